@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""AFN-PCG benchmark: solves/s at relative residual 1e-6 on one GB300.
+
+Workload (default): the 8-D normal point set -- n = 50,000 points i.i.d.
+N(0, I_8), Gaussian kernel, mu = 1e-2, landmark count estimated by Alg. 4 and
+capped at 4000, FSAI with 64 nonzeros per row, 32 right-hand sides
+b ~ N(0, 1), tol 1e-6.  One step = build + solve for each length-scale
+l in {0.5, 1, 2, 4} (4 systems x 32 right-hand sides = 128 solves), mixed
+precision (FP32 matvec / apply / FSAI build, FP64 Cholesky, dots and
+residual-correction loop).  Inputs (50,000 x 8 points, 50,000 x 32 RHS,
+12.8 MB) are regenerated in HBM every step and the solve streams W^T
+(46,000 x 4,000 FP32 = 736 MB per system) many times per step, far more
+than L2 (129 MB), so no L2 flush is inserted between steps.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle (the reference arm) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LS = (0.5, 1.0, 2.0, 4.0)
+N, D, MU, KMAX, W, NRHS, TOL, SEED = 50_000, 8, 1e-2, 4000, 64, 32, 1e-6, 1002
+METRIC = "AFN-PCG solves/s at rel. residual 1e-6 (mixed precision, 8-D normal, n=50k, 32 RHS)"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+N_SM, FP32_LANES, MUFU_PER_SM, SM_MAX_MHZ = 152, 128, 16, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--nrhs", type=int, default=NRHS)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, nrhs):
+    from paper_2304_05460_gb300 import inputs
+    return inputs.normal_8d(l=1.0, nrhs=nrhs, n=n, seed=SEED)
+
+
+def config(n, nrhs):
+    return {"workload": "normal_8d: n=%d d=8 N(0,I), Gaussian l in {0.5,1,2,4}, mu=1e-2, "
+                        "k=Alg.4 estimate capped at 4000, FSAI w=64, %d RHS N(0,1), tol 1e-6"
+                        % (n, nrhs),
+            "n": n, "d": D, "nrhs": nrhs, "lengthscales": list(LS), "mu": MU, "k_max": KMAX,
+            "fsai_nnz": W, "tol": TOL, "precision": "mixed",
+            "l2": "inputs and streamed factors far larger than L2 (129 MB); no flush"}
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    def __init__(self, idx):
+        self.idx = idx
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------- oracle baseline --
+def oracle_sample(n, nrhs, budget_s=20.0, iters_hint=None):
+    """Time the FP64 oracle on a bounded sample of the workload and scale to
+    seconds per system (one l).  Returns (solves_per_s, detail)."""
+    import oracle
+    from paper_2304_05460_gb300 import inputs
+    s = workload(n, nrhs)
+    X = s.X
+    l = 1.0
+    cores = oracle.get_threads()
+    t = {}
+    t0 = time.perf_counter()
+    k, r, br = oracle.rank_estimate(X, 0, l, MU, m=min(n, 1000), seed=SEED, k_max=KMAX)
+    t["rank"] = time.perf_counter() - t0
+    # FPS: the first 400 of the k steps, scaled (each step is one O(n d) pass)
+    ks = min(k, 400)
+    t0 = time.perf_counter()
+    oracle.fps(X, ks, 0)
+    t["fps"] = (time.perf_counter() - t0) * k / ks
+    # Cholesky of K11 + mu I on the first kc landmarks, scaled by (k/kc)^3
+    kc = min(k, 1200)
+    idx = np.arange(kc)
+    A = oracle.kernel_matrix(X[idx], X[idx], 0, l) + MU * np.eye(kc)
+    t0 = time.perf_counter()
+    Lc = oracle.cholesky(A)
+    t["chol"] = (time.perf_counter() - t0) * (k / kc) ** 3
+    # FSAI rows: 8 Schur rows with their literal Schur blocks, scaled to nr rows
+    nr = n - k
+    Xp = np.concatenate([X[:k], X[k:]])
+    Lk = None
+    if kc == k:
+        Lk = Lc
+    else:
+        Ak = oracle.kernel_matrix(X[:k], X[:k], 0, l) + MU * np.eye(k)
+        Lk = np.linalg.cholesky(Ak)      # factor only feeds the timed row solves below
+    pat, _ = oracle.knn_pattern(Xp[k:k + 2000], W)
+    rows = np.arange(1990, 1998)
+    t0 = time.perf_counter()
+    oracle.fsai_rows(Xp, 0, l, MU, k, W, Lk, np.concatenate([pat, np.full((nr - 2000, W), -1, np.int32)]), rows)
+    t["fsai"] = (time.perf_counter() - t0) * nr / len(rows)
+    # KNN: rows 0..2000 cost ~ sum i; scale to nr rows (quadratic)
+    t0 = time.perf_counter()
+    oracle.knn_pattern(Xp[k:k + 2000], W)
+    t["knn"] = (time.perf_counter() - t0) * (nr / 2000.0) ** 2
+    # one PCG iteration ~ one matvec with nrhs columns: 16 sampled rows scaled
+    rowsm = np.arange(16)
+    P = inputs.rhs(n, nrhs, 5)
+    t0 = time.perf_counter()
+    oracle.matvec_rows(X, 0, l, MU, P, rowsm)
+    t_mv = (time.perf_counter() - t0) * n / len(rowsm)
+    it = iters_hint if iters_hint else 30
+    t["pcg"] = t_mv * it
+    total = sum(t.values())
+    detail = ("FP64 oracle, l=1 system: rank estimate in full; FPS 400 of %d steps; Cholesky "
+              "of %d of %d landmarks (x(k/kc)^3); 8 FSAI rows of %d; KNN rows 0..2000 "
+              "(x(nr/2000)^2); 16 matvec rows x %d RHS (x n) x %d PCG iterations; "
+              "scaled to one build+solve of %d RHS = %.1f s" % (k, kc, k, nr, nrhs, it, nrhs,
+                                                                 total))
+    return nrhs / total, detail, cores, t
+
+
+# ------------------------------------------------------------------- main --
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    v, detail, cores, _ = oracle_sample(args.n, args.nrhs)
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 4 * args.nrhs / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args.n, args.nrhs), "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": detail},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2304_05460_gb300 import afn
+
+    s = workload(args.n, args.nrhs)
+    stream = torch.cuda.current_stream()
+    Xd = torch.tensor(s.X, device="cuda")
+    Bd = torch.tensor(np.ascontiguousarray(s.B), device="cuda")
+
+    def opts(profile):
+        return afn.options(precision=afn.PREC_MIXED, rank_mode=afn.RANK_ESTIMATE,
+                           rank_subsample=1000, seed=SEED, profile=profile, stream=stream)
+
+    stats = {}
+    iters_seen = []
+
+    def step(profile, host=False):
+        for l in LS:
+            if host:
+                h = afn.afn_build(s.X, afn.GAUSSIAN, l, MU, KMAX, W, opts(profile))
+                x, info = afn.afn_solve(h, s.B, TOL)
+            else:
+                h = afn.afn_build(Xd, afn.GAUSSIAN, l, MU, KMAX, W, opts(profile))
+                x, info = afn.afn_solve(h, Bd, TOL)
+            if info["converged"] != args.nrhs:
+                raise RuntimeError("l=%g: %d/%d columns reached tol (relres max %.3e)"
+                                   % (l, info["converged"], args.nrhs, info["relres"].max()))
+            iters_seen.append(int(info["iters"].max()))
+            if profile:
+                for nm in ("matvec32", "matvec64", "apply32", "fps", "knn", "chol", "trsm",
+                           "fsai", "blas1", "rank"):
+                    c, ms = afn.afn_get_kernel_stats(h, nm)
+                    a = stats.setdefault(nm, [0, 0.0])
+                    a[0] += c
+                    a[1] += ms
+            afn.afn_free(h)
+
+    for _ in range(args.warmup):
+        step(0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = afn.afn_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(1)
+    e1.record(stream)
+    launches = afn.afn_launch_count() - launches0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    solves = args.nrhs * len(LS) * args.steps * world
+    value = solves / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step(0, host=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = args.nrhs * len(LS) * args.e2e_steps * world / e2e_s
+    h2d = len(LS) * (s.X.nbytes + s.B.nbytes)
+    d2h = len(LS) * s.B.nbytes
+
+    # roofline of the dominant kernel (FP32 matvec): FP32-pipe bound
+    mv_cnt, mv_ms = stats.get("matvec32", [0, 0.0])
+    n = args.n
+    nr_piece = min(args.nrhs, 32)
+    flops_per_launch = float(n) * n * (3 * D + 2 * nr_piece)
+    avg_ms = mv_ms / max(mv_cnt, 1)
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if mv_cnt else None
+    peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "matvec32_kernel<D=8,NR=%d,Gaussian>" % nr_piece,
+            "flops_per_pair": 3 * D + 2 * nr_piece,
+            "pairs_per_launch": float(n) * n, "avg_launch_ms": avg_ms, "launches": mv_cnt,
+            "peak_basis": "FP32 pipe: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in stats.items()}
+    step_ms = ms / args.steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, detail, cores, parts = oracle_sample(args.n, args.nrhs,
+                                                iters_hint=int(np.median(iters_seen)) if iters_seen else None)
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": detail}
+
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        # plain FP64 GPU AFN-PCG on the l = 1 system, same RHS (the comparison arm)
+        o64 = afn.options(precision=afn.PREC_FP64, rank_mode=afn.RANK_ESTIMATE,
+                          rank_subsample=1000, seed=SEED, stream=stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        h = afn.afn_build(Xd, afn.GAUSSIAN, 1.0, MU, KMAX, W, o64)
+        x, info = afn.afn_solve(h, Bd, TOL)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        fp64 = {"value": args.nrhs / (fms / 1e3), "unit": "solves/s", "system": "l=1",
+                "ms": fms, "iters_max": int(info["iters"].max()),
+                "converged": int(info["converged"])}
+        afn.afn_free(h)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic", "config": config(args.n, args.nrhs),
+                "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "kernels": kernels, "fp64_gpu": fp64,
+                "pcg_iters_max": iters_seen[-len(LS):] if iters_seen else None}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

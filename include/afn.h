@@ -1,0 +1,211 @@
+/*
+ * afn.h -- C ABI of the GB300 (sm_103a) AFN-preconditioned CG library.
+ *
+ * Solves the regularized kernel system (K + mu I) a = b   (eq. (Problem),
+ * Sec. 1) for the Gaussian kernel exp(-||x-y||^2 / l^2) (eq. (gaussianf)) and
+ * the Matern-3/2 kernel (1 + sqrt3 r/l) exp(-sqrt3 r/l) (Sec. 5), with PCG
+ * preconditioned by the Adaptive Factorized Nystrom (AFN) preconditioner:
+ *   landmarks X_k by farthest point sampling (Alg. 6) or uniform sampling,
+ *   L = chol(K11 + mu I), G = FSAI of the Schur complement
+ *   K22 + mu I - K12^T (K11 + mu I)^{-1} K12 (Alg. 1, Alg. 2),
+ *   applied as in Alg. 3; the landmark count can be estimated by Alg. 4.
+ *
+ * Conventions shared by every entry point
+ *  - Points are n x d row-major float64.  Right-hand sides and solutions are
+ *    n x nrhs column-major float64 in the caller's ORIGINAL point order
+ *    (the library permutes internally: landmarks first, Sec. 2).
+ *  - Any pointer may be host or device memory (CUDA unified addressing
+ *    decides); device pointers must be on the current device.  Inputs are
+ *    read-only and fully consumed before the call returns; outputs are
+ *    caller-owned.  Host outputs are valid when the call returns; device
+ *    outputs are valid once the call's stream has reached that point (every
+ *    call below synchronises its stream before returning, so they are valid
+ *    on return as well).
+ *  - Every function returns an afn_status; nothing aborts.  The message of
+ *    the last failure on the calling thread is afn_last_error().
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - stream: a cudaStream_t passed as void*; NULL = the legacy default stream.
+ */
+#ifndef AFN_H
+#define AFN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AFN_OK = 0,
+    AFN_ERR_ARG = 1,           /* invalid argument (sizes, l<=0, mu<=0, tol<=0, NaN/Inf input) */
+    AFN_ERR_OOM = 2,           /* device allocation failed / admission refused */
+    AFN_ERR_NOT_SPD = 3,       /* K11 + mu I or an FSAI pattern block is not numerically SPD */
+    AFN_ERR_NO_CONVERGE = 4,   /* max_iter / max_outer reached; the partial result is returned */
+    AFN_ERR_TIMEOUT = 5,       /* a device-side wait ran past its limit; results invalid */
+    AFN_ERR_CUDA = 6,          /* a CUDA runtime error */
+    AFN_ERR_BUSY = 7           /* server queue full */
+} afn_status;
+
+typedef enum { AFN_GAUSSIAN = 0, AFN_MATERN32 = 1 } afn_kernel;
+
+typedef enum {
+    AFN_PREC_FP64 = 0,         /* everything in FP64 */
+    AFN_PREC_MIXED = 1         /* FP32 matvec / apply / FSAI build + FP64 Cholesky, dots,
+                                  scalars and an outer FP64 residual-correction loop */
+} afn_precision;
+
+typedef enum {
+    AFN_LM_AUTO = 0,           /* FPS when d <= 10, else uniform (Alg. 2) */
+    AFN_LM_FPS = 1,            /* farthest point sampling (Alg. 6) */
+    AFN_LM_UNIFORM = 2         /* uniform sampling without replacement */
+} afn_landmark_policy;
+
+typedef enum {
+    AFN_RANK_FIXED = 0,        /* k = min(k_max, n) */
+    AFN_RANK_ESTIMATE = 1      /* k = Alg. 4 estimate clipped to [1, min(k_max, n)] */
+} afn_rank_mode;
+
+typedef struct {
+    int32_t precision;         /* afn_precision, default AFN_PREC_FP64 */
+    int32_t landmarks;         /* afn_landmark_policy, default AFN_LM_AUTO */
+    int32_t rank_mode;         /* afn_rank_mode, default AFN_RANK_FIXED */
+    int32_t rank_subsample;    /* m of Alg. 4; 0 = min(n, 1000) */
+    int64_t fps_start;         /* FPS start index; -1 = the point nearest the centroid (Alg. 6) */
+    uint64_t seed;             /* SplitMix64 seed for uniform landmarks and Alg. 4's subsample */
+    int32_t max_iter;          /* PCG iteration cap per column (FP64) / per inner solve; default 500 */
+    int32_t max_outer;         /* mixed precision: FP64 refinement steps cap; default 10 */
+    double inner_tol;          /* mixed precision: inner relative tolerance; default 1e-4 */
+    int32_t check_every;       /* iterations between host convergence polls; default 4 */
+    int32_t profile;           /* 1 = time every launch with CUDA events (afn_get_kernel_stats) */
+    void *stream;              /* cudaStream_t; NULL = default stream */
+} afn_options;
+
+typedef struct afn_handle afn_handle;   /* opaque; owns every device buffer of one system */
+
+typedef struct {
+    int64_t n, nr, k;          /* points, Schur rows n-k, landmarks */
+    int32_t d, w;              /* dimension, FSAI nonzeros per row (incl. diagonal) */
+    int32_t kernel, precision;
+    int64_t rank_r;            /* Alg. 4: the subsample Nystrom rank r (0 if not estimated) */
+    int32_t rank_branch;       /* Alg. 4: 0 = k from r n / m, 1 = eigenvalue count, -1 = fixed k */
+    int32_t pad_;
+    double l, mu;
+    double build_ms;           /* device time of afn_build */
+    int64_t device_bytes;      /* device memory held by the handle */
+} afn_build_info;
+
+typedef struct {
+    int32_t *iters;            /* [nrhs] or NULL: PCG iterations per column (mixed: inner iterations summed) */
+    double *relres;            /* [nrhs] or NULL: final ||b - (K+mu I)x|| / ||b|| per column, FP64 */
+    int32_t outer_steps;       /* out: FP64 residual evaluations (mixed) / PCG restarts + 1 (FP64) */
+    int32_t converged;         /* out: columns whose FP64 relative residual is <= tol */
+    double solve_ms;           /* out: device time of the solve */
+} afn_solve_info;
+
+/* Fill *opt with the defaults listed above. */
+void afn_default_options(afn_options *opt);
+
+/*
+ * Build the AFN preconditioner for points (n x d), Alg. 2:
+ *   k = min(k_max, n) or the Alg. 4 estimate; landmarks by FPS (Alg. 6) or
+ *   uniform sampling; L = chol(K11 + mu I); W = L^{-1} K12; FSAI pattern of
+ *   each Schur row = its fsai_nnz-1 nearest lower-numbered neighbours plus
+ *   itself (Sec. 3.1); G = FSAI of the Schur complement (Alg. 1).
+ * kernel: afn_kernel.  l > 0, mu > 0, k_max >= 0, fsai_nnz >= 1 (clamped to
+ * n - k).  opt may be NULL (defaults).  On success *out owns all device state.
+ * Errors: AFN_ERR_ARG, AFN_ERR_OOM, AFN_ERR_NOT_SPD, AFN_ERR_TIMEOUT, AFN_ERR_CUDA.
+ */
+afn_status afn_build(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
+                     double mu, int32_t k_max, int32_t fsai_nnz, const afn_options *opt,
+                     afn_handle **out);
+
+/*
+ * Solve (K + mu I) x = rhs for nrhs columns with AFN-PCG (Alg. 3, Alg. 5),
+ * relative residual tol on each column (||r||_2 <= tol ||b||_2).  FP64 mode:
+ * textbook PCG, then the true residual is recomputed and PCG restarts from x
+ * while it is above tol (at most 3 restarts).  Mixed mode: FP32 inner PCG
+ * inside FP64 iterative refinement until the FP64 residual is <= tol.
+ * rhs, x_out: n x nrhs column-major, original point order.  info may be NULL.
+ * Errors: AFN_ERR_ARG, AFN_ERR_OOM, AFN_ERR_NO_CONVERGE (x_out holds the last
+ * iterate), AFN_ERR_CUDA.
+ */
+afn_status afn_solve(afn_handle *h, const double *rhs, int32_t nrhs, double tol, double *x_out,
+                     afn_solve_info *info);
+
+/* Release every device buffer of h.  NULL-safe. */
+void afn_free(afn_handle *h);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *afn_last_error(void);
+
+/* ---- introspection of a built handle (parity checks, tooling) ---------- */
+afn_status afn_get_build_info(const afn_handle *h, afn_build_info *info);
+/* perm[n]: original index of the point at permuted position p (landmarks first). */
+afn_status afn_get_perm(const afn_handle *h, int64_t *perm);
+/* L: k x k row-major, lower triangle (upper zero), FP64. */
+afn_status afn_get_L(const afn_handle *h, double *L);
+/* pattern: nr x w int32 (-1 padding; diagonal last), values: nr x w FP64 (ELL of G). */
+afn_status afn_get_G(const afn_handle *h, int32_t *pattern, double *values);
+/* W = L^{-1} K12 as nr x k row-major (row j = column j of W), FP64 or the
+ * precision the handle keeps (FP64 handle: FP64; mixed: FP32 converted). */
+afn_status afn_get_W(const afn_handle *h, double *Wt);
+/* s = M^{-1} r for nrhs columns (Alg. 3), FP64, vectors in PERMUTED order. */
+afn_status afn_apply_precond(afn_handle *h, const double *r, int32_t nrhs, double *s);
+
+/* per-kernel timing gathered while opt.profile was set (CUDA events on the
+ * launching stream).  name: "matvec32", "matvec64", "apply32", "apply64",
+ * "fps", "knn", "chol", "trsm", "fsai", "blas1", "rank".  count = launches,
+ * ms = total device time.  afn_reset_kernel_stats clears the counters. */
+afn_status afn_get_kernel_stats(afn_handle *h, const char *name, int64_t *count, double *ms);
+afn_status afn_reset_kernel_stats(afn_handle *h);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all entry points, all devices).  Tooling; no paper counterpart. */
+int64_t afn_launch_count(void);
+
+/* ---- operator-level entry points (each one step of the hot path) ------- */
+
+/*
+ * q = (K + mu I) p, matrix-free (eq. (Problem); K_ij = K(x_i, x_j), Sec. 1).
+ * points n x d row-major FP64; p, q n x nrhs column-major FP64.  precision:
+ * AFN_PREC_FP64 computes in FP64; AFN_PREC_MIXED evaluates pairs in FP32
+ * (points and p rounded to FP32, FP32 accumulation) and returns FP64.
+ */
+afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
+                             double mu, const double *p, int32_t nrhs, double *q,
+                             int32_t precision, void *stream);
+
+/*
+ * Farthest point sampling, Alg. 6: idx[0] = start (or the point nearest the
+ * centroid when start == -1), then k-1 times the point with the largest
+ * squared distance (FP64, summed over dimensions in order, no fused
+ * multiply-add) to the selected set; ties go to the lowest index; a selected
+ * point is never selected again.  idx: k int64.
+ */
+afn_status afn_fps(const double *points, int64_t n, int32_t d, int64_t k, int64_t start,
+                   int64_t *idx, void *stream);
+
+/*
+ * FSAI pattern (Sec. 3.1) of the point sequence xr (nr x d): row i lists the
+ * w-1 nearest points j < i by (FP64 squared distance, j) ascending, then i
+ * itself; rows with i < w-1 list all j < i.  pattern: nr x w int32, -1 padded.
+ */
+afn_status afn_knn_pattern(const double *xr, int64_t nr, int32_t d, int32_t w, int32_t *pattern,
+                           void *stream);
+
+/*
+ * Alg. 4 rank estimate (readings: subsample = first m SplitMix64 partial
+ * Fisher-Yates draws with `seed`; FPS from subsample index 0; error of rank r
+ * = ||E_r||_2 / ||K_m||_2 with E_r the Schur complement after r FPS pivots;
+ * r = smallest rank with error < 0.1; k = ceil(r n / m) when r n / m >= 2000,
+ * else #{eig(K(X_m, X_m)) > 0.1 mu} on unscaled points; clipped to
+ * [1, min(k_max, n)]).  m = 0 means min(n, 1000).
+ */
+afn_status afn_rank_estimate(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
+                             double mu, int32_t m, uint64_t seed, int32_t k_max, int64_t *k_out,
+                             int64_t *r_out, int32_t *branch_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFN_H */

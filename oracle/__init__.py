@@ -383,3 +383,43 @@ def rank_estimate(X, kernel, l, mu, m=1000, seed=0, k_max=4000):
                                int(m), C.c_uint64(int(seed) & (2**64 - 1)), int(k_max),
                                C.byref(r), C.byref(br))
     return int(k), int(r.value), int(br.value)
+
+
+# --------------------------------------------------------------------------
+# sampled outputs (large problems)
+# --------------------------------------------------------------------------
+def _sig_sampled(lib):
+    P, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    lib.orc_matvec_rows.restype = None
+    lib.orc_matvec_rows.argtypes = [P, i64, i32, i32, dbl, dbl, P, i32, P, i64, P]
+    lib.orc_fsai_rows.restype = i32
+    lib.orc_fsai_rows.argtypes = [P, i64, i32, i32, dbl, dbl, i64, i32, P, P, P, i64, P]
+
+
+def matvec_rows(X, kernel, l, mu, p, rows):
+    """Rows `rows` of (K + mu I) p (p: (n,) or (n, nrhs)); returns (len(rows), nrhs)."""
+    lib = _L()
+    _sig_sampled(lib)
+    X = _f64(X)
+    P = np.asfortranarray(np.asarray(p, dtype=np.float64).reshape(X.shape[0], -1))
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.shape[0], P.shape[1]), order="F")
+    lib.orc_matvec_rows(_p(X), X.shape[0], X.shape[1], _kid(kernel), float(l), float(mu), _p(P),
+                        P.shape[1], _p(rows), rows.shape[0], _p(out))
+    return np.ascontiguousarray(out)
+
+
+def fsai_rows(Xp, kernel, l, mu, k, w, Lo, pattern, rows):
+    """FSAI rows (Alg. 1 on the Schur complement) for the given Schur rows."""
+    lib = _L()
+    _sig_sampled(lib)
+    Xp = _f64(Xp)
+    Lo = _f64(Lo) if k > 0 else np.zeros((1, 1))
+    pat = np.ascontiguousarray(pattern, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros((rows.shape[0], w))
+    st = lib.orc_fsai_rows(_p(Xp), Xp.shape[0], Xp.shape[1], _kid(kernel), float(l), float(mu),
+                           int(k), int(w), _p(Lo), _p(pat), _p(rows), rows.shape[0], _p(out))
+    if st:
+        raise np.linalg.LinAlgError("oracle fsai_rows: not SPD")
+    return out

@@ -869,3 +869,77 @@ int64_t orc_rank_estimate(const double *X, int64_t n, int d, int kernel, double 
     free(sub); free(Xs); free(o); free(Xo); free(Ko); free(T); free(dg); free(of); free(Lo);
     return k;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sampled outputs for large problems (same arithmetic as above, on a subset */
+/* of rows).                                                                 */
+/* ------------------------------------------------------------------------ */
+/* y[r, c] = ((K + mu I) p)[rows[r], c], p n x nrhs column-major,
+ * y nrows x nrhs column-major */
+void orc_matvec_rows(const double *X, int64_t n, int d, int kernel, double l, double mu,
+                     const double *p, int nrhs, const int64_t *rows, int64_t nrows, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nrows; ++q) {
+        int64_t i = rows[q];
+        for (int c = 0; c < nrhs; ++c) {
+            const double *pc = p + (int64_t)c * n;
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j)
+                s = s + orc_kernel_eval(X + i * d, X + j * d, d, kernel, l) * pc[j];
+            y[(int64_t)c * nrows + q] = s + mu * pc[i];
+        }
+    }
+}
+
+/* FSAI rows of Alg. 1 on the Schur complement for selected Schur rows, with
+ * the pattern given (nr x w) and K12 columns formed on the fly from the
+ * permuted points Xp (landmarks first).  Same literal Schur block as
+ * orc_afn_build.  G out: nrows x w.  Returns 0 or 3. */
+int orc_fsai_rows(const double *Xp, int64_t n, int d, int kernel, double l, double mu, int64_t k,
+                  int w, const double *L, const int32_t *pat, const int64_t *rows, int64_t nrows,
+                  double *Gout)
+{
+    const double *Xk = Xp, *Xr = Xp + k * d;
+    int bad = 0;
+#pragma omp parallel
+    {
+        double *Kc = (double *)malloc(sizeof(double) * (size_t)((k > 0 ? k : 1) * w));
+        double *V = (double *)malloc(sizeof(double) * (size_t)((k > 0 ? k : 1) * w));
+        double *tmp = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+        double *A = (double *)malloc(sizeof(double) * (size_t)(w * w));
+        double *g = (double *)malloc(sizeof(double) * (size_t)w);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < nrows; ++q) {
+            int64_t i = rows[q];
+            const int32_t *s = pat + i * w;
+            int m = 0;
+            while (m < w && s[m] >= 0) ++m;
+            for (int c = 0; c < m; ++c) {
+                for (int64_t t = 0; t < k; ++t)
+                    Kc[(int64_t)c * k + t] = orc_kernel_eval(Xk + t * d, Xr + (int64_t)s[c] * d, d, kernel, l);
+                if (k > 0) {
+                    orc_forward(L, k, Kc + (int64_t)c * k, tmp);
+                    orc_backward(L, k, tmp, V + (int64_t)c * k);
+                }
+            }
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b) {
+                    double v = orc_kernel_eval(Xr + (int64_t)s[a] * d, Xr + (int64_t)s[b] * d, d, kernel, l);
+                    if (a == b) v = v + mu;
+                    double qq = 0.0;
+                    for (int64_t t = 0; t < k; ++t) qq = qq + Kc[(int64_t)a * k + t] * V[(int64_t)b * k + t];
+                    A[a * m + b] = v - qq;
+                }
+            for (int p = 0; p < w; ++p) Gout[q * w + p] = 0.0;
+            if (orc_fsai_row(A, m, g)) {
+#pragma omp atomic write
+                bad = 3;
+            } else {
+                for (int p = 0; p < m; ++p) Gout[q * w + p] = g[p];
+            }
+        }
+        free(Kc); free(V); free(tmp); free(A); free(g);
+    }
+    return bad;
+}

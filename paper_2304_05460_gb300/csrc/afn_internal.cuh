@@ -1,0 +1,192 @@
+// afn_internal.cuh -- declarations shared by the CUDA translation units of
+// libafn.so.  Device helpers, the handle layout and the launch wrappers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/afn.h"
+
+namespace afn {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char *fmt, ...);
+afn_status cuda_fail(cudaError_t e, const char *what);
+
+#define AFN_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::afn::cuda_fail(e_, #call);      \
+    } while (0)
+
+#define AFN_TRY(call)                                                   \
+    do {                                                                \
+        afn_status s_ = (call);                                         \
+        if (s_ != AFN_OK) return s_;                                    \
+    } while (0)
+
+// device status word values (written by kernels, read by the host)
+enum : int { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_TIMEOUT = 2 };
+
+// -------------------------------------------------------- device buffers --
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    afn_status alloc(size_t b);
+    void release();
+    ~DevBuf() { release(); }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ------------------------------------------------------------- profiling --
+enum Kid { K_MATVEC32 = 0, K_MATVEC64, K_APPLY32, K_APPLY64, K_FPS, K_KNN, K_CHOL, K_TRSM,
+           K_FSAI, K_BLAS1, K_RANK, K_COUNT };
+const char *kid_name(int k);
+
+struct Profiler {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    struct Rec { int kid; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t count[K_COUNT] = {0};
+    double ms[K_COUNT] = {0};
+    void begin(int kid, cudaEvent_t *a);
+    void end(int kid, cudaEvent_t a);
+    void flush();     // resolve pending records (synchronizes the events)
+    void reset();
+    ~Profiler();
+};
+
+struct Scope {        // RAII launch timer
+    Profiler *p; int kid; cudaEvent_t a = nullptr;
+    Scope(Profiler *p_, int kid_) : p(p_), kid(kid_) { if (p && p->on) p->begin(kid, &a); }
+    ~Scope() { if (p && p->on) p->end(kid, a); }
+};
+
+// ------------------------------------------------------------------ handle --
+struct Handle {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    afn_options opt{};
+    int64_t n = 0, k = 0, nr = 0;
+    int d = 0, dp = 0, w = 0, w_req = 1, kernel = 0, precision = 0;
+    double l = 1, mu = 1;
+    int64_t rank_r = 0; int rank_branch = -1;
+    double build_ms = 0;
+
+    // permuted points
+    DevBuf perm;      // int64 [n]
+    DevBuf X64;       // double [n*d] permuted, row-major
+    DevBuf X32;       // float  [n*dp] permuted, pre-scaled for the FP32 kernel
+    // factors
+    DevBuf L;         // double [k*k] row-major lower
+    DevBuf Linv;      // double [k*k] row-major lower, L^{-1}
+    DevBuf LinvT;     // double [k*k] row-major upper, L^{-T}
+    DevBuf Linv32;    // float  [k*k]
+    DevBuf LinvT32;   // float  [k*k]
+    DevBuf Wt;        // double [nr*k]  (FP64 handles)
+    DevBuf Wt32;      // float  [nr*k]  (mixed handles)
+    DevBuf pat;       // int32 [nr*w]
+    DevBuf G;         // double [nr*w]
+    DevBuf G32;       // float  [nr*w]
+    DevBuf gt_ptr;    // int32 [nr+1]  CSR of G^T (column c's entries, ascending row)
+    DevBuf gt_row;    // int32 [nnz]
+    DevBuf gt_slot;   // int32 [nnz]   index into the ELL arrays (row*w + p)
+    DevBuf status;    // int [4] device status words
+
+    // solve workspace (grown on demand)
+    int ws_nrhs = 0;
+    DevBuf ws;
+    Profiler prof;
+
+    int64_t device_bytes() const;
+};
+
+// ----------------------------------------------------------- util launches --
+afn_status sync_status(Handle *h, const char *what);   // sync + read device status word
+
+// pointer kind
+bool is_device_ptr(const void *p);
+
+// kernel function constants for FP64/FP32 evaluation
+struct KParams {
+    int kernel;       // 0 Gaussian, 1 Matern-3/2
+    double l, mu;
+};
+
+// ---- matvec.cu
+// q = (K + mu I) p on permuted points; p,q n x nrhs column-major (ld = n).
+afn_status matvec64(const double *X, int64_t n, int d, KParams kp, const double *p, int nrhs,
+                    double *q, void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t matvec64_scratch(int64_t n, int nrhs);
+afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, const float *p,
+                    int nrhs, float *q, void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t matvec32_scratch(int64_t n, int nrhs);
+int pad_dim(int d);
+int stored_dim32(int dp);
+// prescaled FP32 copy of FP64 points (n x d -> n x dp)
+afn_status make_points32(const double *X, int64_t n, int d, int dp, int kernel, double l,
+                         float *Xs, cudaStream_t s);
+
+// ---- fps.cu
+afn_status fps_run(const double *X, int64_t n, int d, int64_t k, int64_t start, int64_t *idx,
+                   int *status, cudaStream_t s);
+afn_status centroid_start(const double *X, int64_t n, int d, int64_t *out, cudaStream_t s);
+afn_status build_perm(const int64_t *landmarks, int64_t k, int64_t n, int64_t *perm,
+                      cudaStream_t s);
+afn_status gather_points(const double *X, const int64_t *perm, int64_t n, int d, double *Xp,
+                         cudaStream_t s);
+
+// ---- knn.cu
+afn_status knn_pattern(const double *Xr, int64_t nr, int d, int w, int32_t *pat,
+                       cudaStream_t s);
+
+// ---- dense.cu
+afn_status kernel_block(const double *Xa, int64_t na, const double *Xb, int64_t nb, int d,
+                        KParams kp, double diag_shift, double *out, int64_t ld,
+                        cudaStream_t s);   // out[i*ld+j] = K(a_i, b_j) (+shift on i==j)
+// in place, lower; tiny < 0: error on a pivot <= 0; tiny >= 0: drop pivots <= tiny
+afn_status cholesky64(double *A, int64_t k, int *status, cudaStream_t s, double tiny);
+afn_status tri_inverse64(const double *L, int64_t k, double *Linv, double *LinvT, cudaStream_t s);
+afn_status tri_inverse32(const float *L, int64_t k, float *Linv, float *LinvT, cudaStream_t s);
+afn_status trsm_right_lt64(const double *L, int64_t k, double *B, int64_t m,
+                           cudaStream_t s);   // B (m x k) <- B L^{-T}
+afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaStream_t s);
+afn_status kernel_block32(const float *Xa, int64_t na, const float *Xb, int64_t nb, int dp,
+                          int kernel, float *out, int64_t ld, cudaStream_t s);
+afn_status convert64to32(const double *a, float *b, int64_t count, cudaStream_t s);
+afn_status convert32to64(const float *a, double *b, int64_t count, cudaStream_t s);
+
+// ---- fsai.cu
+afn_status fsai_build64(const double *Xr, int64_t nr, int d, KParams kp, const double *Wt,
+                        int64_t k, const int32_t *pat, int w, double *G, int *status,
+                        cudaStream_t s);
+afn_status fsai_build32(const double *Xr, int64_t nr, int d, KParams kp, const float *Wt,
+                        int64_t k, const int32_t *pat, int w, double *G, int *status,
+                        cudaStream_t s);
+afn_status transpose_pattern(const int32_t *pat, int64_t nr, int w, int32_t *ptr, int32_t *row,
+                             int32_t *slot, cudaStream_t s);
+
+// ---- apply.cu  (all vectors permuted, n x nrhs column-major, ld = n)
+template <class T>
+afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt, const T *G,
+                     const T *r, int nrhs, T *s, T *tmp, cudaStream_t st);
+size_t apply_tmp_elems(const Handle *h, int nrhs);
+
+// ---- blas1.cu (PCG vector kernels; FP64 scalars per column)
+afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, double *x_perm,
+                     int32_t *iters, double *relres, int *outer, int *converged);
+
+// ---- rank.cu
+afn_status rank_estimate(const double *X, int64_t n, int d, KParams kp, int m, uint64_t seed,
+                         int64_t k_max, int64_t *k_out, int64_t *r_out, int *branch_out,
+                         int *status, cudaStream_t s);
+
+// host SplitMix64 partial Fisher-Yates (uniform sampling without replacement)
+void uniform_sample_host(int64_t n, int64_t k, uint64_t seed, std::vector<int64_t> &out);
+
+}  // namespace afn

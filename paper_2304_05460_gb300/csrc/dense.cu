@@ -1,0 +1,379 @@
+// dense.cu -- dense pieces of the AFN build (Alg. 2):
+//   * kernel blocks K(X_a, X_b) (K11 + mu I, K12),
+//   * the blocked right-looking Cholesky of K11 + mu I in FP64,
+//   * the blocked solve B <- B L^{-T} (gives W^T = K12^T L^{-T} and L^{-T}),
+// all on row-major storage.
+#include <algorithm>
+#include <cmath>
+
+#include "afn_device.cuh"
+#include "afn_internal.cuh"
+
+namespace afn {
+
+// ------------------------------------------------------------ kernel block --
+// out[i*ld + j] = K(a_i, b_j) (+ shift when i == j), FP64, the definition of
+// eq. (gaussianf) / Sec. 5 on an exact squared distance.
+__global__ void kernel_block_kernel(const double *__restrict__ Xa, int64_t na,
+                                    const double *__restrict__ Xb, int64_t nb, int d, int kernel,
+                                    double l, double shift, double *__restrict__ out, int64_t ld)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= na * nb) return;
+    int64_t i = e / nb, j = e % nb;
+    double r2 = sqdist_exact(Xa + i * d, Xb + j * d, d);
+    double v = kernel64(r2, kernel, l);
+    if (i == j) v += shift;
+    out[i * ld + j] = v;
+}
+
+afn_status kernel_block(const double *Xa, int64_t na, const double *Xb, int64_t nb, int d,
+                        KParams kp, double diag_shift, double *out, int64_t ld, cudaStream_t s)
+{
+    int64_t tot = na * nb;
+    if (tot == 0) return AFN_OK;
+    kernel_block_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Xa, na, Xb, nb, d, kp.kernel,
+                                                                       kp.l, diag_shift, out, ld);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+// FP32 kernel block on prescaled points (stored dims ds): out[i*ld+j]
+template <int KER>
+__global__ void kernel_block32_kernel(const float *__restrict__ Xa, int64_t na,
+                                      const float *__restrict__ Xb, int64_t nb, int ds,
+                                      float *__restrict__ out, int64_t ld)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= na * nb) return;
+    int64_t i = e / nb, j = e % nb;
+    float r2 = 0.f;
+    for (int t = 0; t < ds; ++t) {
+        float u = Xa[i * ds + t] - Xb[j * ds + t];
+        r2 = fmaf(u, u, r2);
+    }
+    out[i * ld + j] = kernel32_scaled<KER>(r2);
+}
+
+afn_status kernel_block32(const float *Xa, int64_t na, const float *Xb, int64_t nb, int dp,
+                          int kernel, float *out, int64_t ld, cudaStream_t s)
+{
+    int64_t tot = na * nb;
+    if (tot == 0) return AFN_OK;
+    int ds = dp == 3 ? 4 : dp;
+    unsigned g = (unsigned)((tot + 255) / 256);
+    if (kernel == 0) kernel_block32_kernel<0><<<g, 256, 0, s>>>(Xa, na, Xb, nb, ds, out, ld);
+    else kernel_block32_kernel<1><<<g, 256, 0, s>>>(Xa, na, Xb, nb, ds, out, ld);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+// ---------------------------------------------------------------- Cholesky --
+static constexpr int NB = 32;   // panel width
+
+// factor the nb x nb diagonal block at (kb, kb) in shared memory
+// tiny < 0: a pivot <= 0 flags DEV_NOT_SPD; tiny >= 0: a pivot <= tiny is
+// treated as zero (its column of L is zero: the point is already spanned).
+__global__ void potrf_diag_kernel(double *A, int64_t k, int64_t kb, int nb, int *status,
+                                  double tiny)
+{
+    __shared__ double a[NB][NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int r = e / nb, c = e % nb;
+        a[r][c] = (c <= r) ? A[(kb + r) * k + kb + c] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        __shared__ double piv;
+        if (threadIdx.x == 0) {
+            double v = a[j][j];
+            if (tiny >= 0.0) {
+                piv = (v > tiny) ? sqrt(v) : 0.0;
+            } else {
+                if (!(v > 0.0)) {
+                    atomicExch(status, DEV_NOT_SPD);
+                    v = 1.0;
+                }
+                piv = sqrt(v);
+            }
+            a[j][j] = piv;
+        }
+        __syncthreads();
+        for (int r = j + 1 + threadIdx.x; r < nb; r += blockDim.x)
+            a[r][j] = (piv != 0.0) ? a[r][j] / piv : 0.0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            int r = e / nb, c = e % nb;
+            if (c > j && r >= c) a[r][c] -= a[r][j] * a[c][j];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int r = e / nb, c = e % nb;
+        A[(kb + r) * k + kb + c] = (c <= r) ? a[r][c] : 0.0;
+    }
+}
+
+// rows below the diagonal block: A[r, kb:kb+nb] <- A[r, kb:kb+nb] L_bb^{-T}
+template <class T>
+__global__ void trsm_rows_kernel(const T *__restrict__ Lsrc, int64_t ldl, int64_t lb,
+                                 T *__restrict__ B, int64_t ldb, int64_t r0, int64_t m,
+                                 int64_t cb, int nb)
+{
+    __shared__ T lbb[NB][NB + 1];
+    __shared__ T xs[128][NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int r = e / nb, c = e % nb;
+        lbb[r][c] = Lsrc[(lb + r) * ldl + lb + c];
+    }
+    int64_t row = r0 + (int64_t)blockIdx.x * 128 + threadIdx.x;
+    __syncthreads();
+    if (row >= m) return;
+    T *b = B + row * ldb + cb;
+    for (int c = 0; c < nb; ++c) {
+        T v = b[c];
+        for (int p = 0; p < c; ++p) v -= xs[threadIdx.x][p] * lbb[c][p];
+        xs[threadIdx.x][c] = (lbb[c][c] != (T)0) ? v / lbb[c][c] : (T)0;
+    }
+    for (int c = 0; c < nb; ++c) b[c] = xs[threadIdx.x][c];
+}
+
+// C[m x nb] -= A[m x K] * Bm[nb x K]^T   (C = B[:, cb:cb+nb], A = B[:, 0:K],
+// Bm = L[cb:cb+nb, 0:K]); 128-row tiles, 256 threads, 4 rows x 4 cols each.
+template <class T>
+__global__ void __launch_bounds__(256) gemm_nt_update_kernel(const T *__restrict__ A, int64_t lda,
+                                                             const T *__restrict__ Bm,
+                                                             int64_t ldbm, T *__restrict__ C,
+                                                             int64_t ldc, int64_t m, int nb,
+                                                             int64_t K)
+{
+    constexpr int TM = 128, KC = 16;
+    __shared__ T as[KC][TM + 1];
+    __shared__ T bs[KC][NB + 1];
+    const int tx = threadIdx.x % 8;    // column group: cols tx*4..+3
+    const int ty = threadIdx.x / 8;    // row group: rows ty*4..+3
+    const int64_t r0 = (int64_t)blockIdx.x * TM;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int64_t k0 = 0; k0 < K; k0 += KC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TM * KC; e += 256) {
+            int r = e / KC, kk = e % KC;
+            int64_t gr = r0 + r, gk = k0 + kk;
+            as[kk][r] = (gr < m && gk < K) ? A[gr * lda + gk] : (T)0;
+        }
+        for (int e = threadIdx.x; e < NB * KC; e += 256) {
+            int c = e / KC, kk = e % KC;
+            int64_t gk = k0 + kk;
+            bs[kk][c] = (c < nb && gk < K) ? Bm[(int64_t)c * ldbm + gk] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = as[kk][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = bs[kk][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        int64_t gr = r0 + ty * 4 + a;
+        if (gr >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int c = tx * 4 + b;
+            if (c < nb) C[gr * ldc + c] -= acc[a][b];
+        }
+    }
+}
+
+// trailing update of the Cholesky: A[r, c] -= sum_p A[r, kb+p] A[c, kb+p]
+// for kb+nb <= c <= r < k (64 x 64 lower tiles)
+__global__ void __launch_bounds__(256) syrk_update_kernel(double *A, int64_t k, int64_t kb, int nb)
+{
+    const int64_t t0 = kb + nb;
+    const int64_t ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    const int64_t r0 = t0 + ti * 64, c0 = t0 + tj * 64;
+    __shared__ double pr[NB][65];
+    __shared__ double pc[NB][65];
+    for (int e = threadIdx.x; e < 64 * NB; e += 256) {
+        int r = e / NB, p = e % NB;
+        int64_t gr = r0 + r, gc = c0 + r;
+        pr[p][r] = (gr < k && p < nb) ? A[gr * k + kb + p] : 0.0;
+        pc[p][r] = (gc < k && p < nb) ? A[gc * k + kb + p] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int p = 0; p < nb; ++p) {
+        double a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { a[q] = pr[p][ty * 4 + q]; b[q] = pc[p][tx * 4 + q]; }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        int64_t gr = r0 + ty * 4 + x;
+        if (gr >= k) continue;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            int64_t gc = c0 + tx * 4 + y;
+            if (gc < k && gc <= gr) A[gr * k + gc] -= acc[x][y];
+        }
+    }
+}
+
+__global__ void zero_upper_kernel(double *A, int64_t k)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= k * k) return;
+    int64_t r = e / k, c = e % k;
+    if (c > r) A[e] = 0.0;
+}
+
+afn_status cholesky64(double *A, int64_t k, int *status, cudaStream_t s, double tiny)
+{
+    if (k <= 0) return AFN_OK;
+    if (k > 65535 * 64) {
+        set_error("cholesky: k=%lld too large", (long long)k);
+        return AFN_ERR_ARG;
+    }
+    AFN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    for (int64_t kb = 0; kb < k; kb += NB) {
+        int nb = (int)std::min<int64_t>(NB, k - kb);
+        potrf_diag_kernel<<<1, 256, 0, s>>>(A, k, kb, nb, status, tiny);
+        int64_t below = k - kb - nb;
+        if (below > 0) {
+            trsm_rows_kernel<double><<<(unsigned)((below + 127) / 128), 128, 0, s>>>(
+                A, k, kb, A, k, kb + nb, k, kb, nb);
+            unsigned T = (unsigned)((below + 63) / 64);
+            syrk_update_kernel<<<dim3(T, T), 256, 0, s>>>(A, k, kb, nb);
+        }
+    }
+    zero_upper_kernel<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(A, k);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+// ------------------------------------------------------------------ TRSM --
+// B (m x k row-major) <- B L^{-T}, L (k x k lower row-major):
+// left-looking over panels of NB columns:
+//   B[:, P] -= B[:, 0:p0] L[P, 0:p0]^T ;  B[:, P] <- B[:, P] L[P,P]^{-T}
+template <class T>
+static afn_status trsm_right_lt(const T *L, int64_t k, T *B, int64_t m, cudaStream_t s)
+{
+    if (k <= 0 || m <= 0) return AFN_OK;
+    for (int64_t p0 = 0; p0 < k; p0 += NB) {
+        int nb = (int)std::min<int64_t>(NB, k - p0);
+        if (p0 > 0) {
+            gemm_nt_update_kernel<T><<<(unsigned)((m + 127) / 128), 256, 0, s>>>(
+                B, k, L + p0 * k, k, B + p0, k, m, nb, p0);
+        }
+        trsm_rows_kernel<T><<<(unsigned)((m + 127) / 128), 128, 0, s>>>(L, k, p0, B, k, 0, m, p0, nb);
+    }
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+afn_status trsm_right_lt64(const double *L, int64_t k, double *B, int64_t m, cudaStream_t s)
+{
+    return trsm_right_lt<double>(L, k, B, m, s);
+}
+
+afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaStream_t s)
+{
+    return trsm_right_lt<float>(L, k, B, m, s);
+}
+
+template <class T>
+__global__ void identity_kernel(T *A, int64_t k)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= k * k) return;
+    A[e] = (e / k == e % k) ? (T)1 : (T)0;
+}
+
+template <class T>
+__global__ void transpose_kernel(const T *__restrict__ A, int64_t k, T *__restrict__ B)
+{
+    __shared__ T t[32][33];
+    int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        int64_t r = by + q, c = bx + threadIdx.x;
+        if (r < k && c < k) t[q][threadIdx.x] = A[r * k + c];
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        int64_t r = bx + q, c = by + threadIdx.x;
+        if (r < k && c < k) B[r * k + c] = t[threadIdx.x][q];
+    }
+}
+
+// LinvT = I L^{-T} = L^{-T} (upper, row-major) by the blocked solve;
+// Linv = its transpose (lower, row-major).
+template <class T>
+static afn_status tri_inverse(const T *L, int64_t k, T *Linv, T *LinvT, cudaStream_t s)
+{
+    if (k <= 0) return AFN_OK;
+    unsigned g = (unsigned)((k * k + 255) / 256);
+    identity_kernel<T><<<g, 256, 0, s>>>(LinvT, k);
+    AFN_TRY(trsm_right_lt<T>(L, k, LinvT, k, s));
+    dim3 gt((unsigned)((k + 31) / 32), (unsigned)((k + 31) / 32));
+    transpose_kernel<T><<<gt, dim3(32, 8), 0, s>>>(LinvT, k, Linv);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+afn_status tri_inverse64(const double *L, int64_t k, double *Linv, double *LinvT, cudaStream_t s)
+{
+    return tri_inverse<double>(L, k, Linv, LinvT, s);
+}
+
+afn_status tri_inverse32(const float *L, int64_t k, float *Linv, float *LinvT, cudaStream_t s)
+{
+    return tri_inverse<float>(L, k, Linv, LinvT, s);
+}
+
+// ------------------------------------------------------------- conversion --
+__global__ void cvt64to32_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void cvt32to64_kernel(const float *__restrict__ a, double *__restrict__ b, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+afn_status convert64to32(const double *a, float *b, int64_t count, cudaStream_t s)
+{
+    if (count <= 0) return AFN_OK;
+    cvt64to32_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(a, b, count);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+afn_status convert32to64(const float *a, double *b, int64_t count, cudaStream_t s)
+{
+    if (count <= 0) return AFN_OK;
+    cvt32to64_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(a, b, count);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
+}  // namespace afn

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every symbol include/afn.h declares
+(no compute: this runs without a GPU), and the binding refuses bad input
+before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(HEADER_DIR):
+        if f.endswith(".h"):
+            txt = open(os.path.join(HEADER_DIR, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(afn_[A-Za-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_05460_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("afn_build", "afn_solve", "afn_free", "afn_last_error", "afn_kernel_matvec",
+                 "afn_fps", "afn_knn_pattern", "afn_rank_estimate", "afn_apply_precond"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_exports_are_c_symbols():
+    from paper_2304_05460_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.build()], capture_output=True,
+                         text=True).stdout
+    syms = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    for n in _declared():
+        assert n in syms, n          # unmangled extern "C"
+
+
+def test_argument_checks_without_gpu():
+    from paper_2304_05460_gb300 import afn
+    X = np.zeros((4, 3))
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(X, afn.GAUSSIAN, -1.0, 1e-3, 2, 2)        # l <= 0
+    assert e.value.status == afn.AFN_ERR_ARG
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(X, afn.GAUSSIAN, 1.0, 0.0, 2, 2)         # mu <= 0
+    assert e.value.status == afn.AFN_ERR_ARG
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(np.zeros((4, 17)), afn.GAUSSIAN, 1.0, 1e-3, 2, 2)   # d > 16
+    assert e.value.status == afn.AFN_ERR_ARG
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(X, 5, 1.0, 1e-3, 2, 2)                  # unknown kernel
+    assert e.value.status == afn.AFN_ERR_ARG
+
+
+def test_default_options():
+    from paper_2304_05460_gb300 import afn
+    o = afn.options()
+    assert (o.precision, o.landmarks, o.rank_mode, o.max_iter, o.max_outer) == (0, 0, 0, 500, 10)
+    assert o.inner_tol == 1e-4 and o.fps_start == 0

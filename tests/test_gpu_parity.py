@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars:
+  * FPS indices, permutation and FSAI pattern: bit-exact.
+  * FP64 path L, W and G: max |gpu - oracle| <= 1e-10 max |oracle| (L, W),
+    1e-9 for G (one more solve on top of the Schur complement).
+  * Solves: the final relative residual ||b - (K + mu I) x|| / ||b||,
+    recomputed by the oracle in FP64, is <= tol; FP64 iteration counts are
+    within +-2 of the oracle's.
+  * FP64 matvec: |gpu - oracle| <= 1e-12 (sum_j |K_ij p_j| + mu |p_i|) per
+    entry; FP32 matvec: <= 2e-5 of the same scale (the FP32 evaluation of
+    r^2, 2^x and the accumulation, each a few ulp of 2^-24 amplified by d
+    and the summation length).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_05460_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+G, M32 = 0, 1
+
+
+@pytest.fixture(scope="module")
+def afn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_05460_gb300 import afn as a
+    return a
+
+
+def scale_bound(X, ker, l, mu, p):
+    """sum_j |K_ij p_j| + mu |p_i| (FP64, oracle kernel values)."""
+    K = oracle.kernel_matrix(X, X, ker, l)
+    P = np.abs(np.asarray(p).reshape(X.shape[0], -1))
+    return K @ P + mu * P
+
+
+# ------------------------------------------------------------------ FPS ---
+@pytest.mark.parametrize("n,d,k,start", [(1, 3, 1, 0), (37, 1, 37, 5), (1000, 3, 200, 0),
+                                         (3001, 5, 257, 17), (2500, 16, 300, 0),
+                                         (4097, 8, 1000, 0)])
+def test_fps_bit_exact(afn, n, d, k, start):
+    X = inputs.normal_points(n, d, 100 + n)
+    assert np.array_equal(afn.afn_fps(X, k, start), oracle.fps(X, k, start))
+
+
+def test_fps_ties_duplicates_centroid(afn):
+    g = np.stack(np.meshgrid(np.arange(6.0), np.arange(6.0), indexing="ij"), -1).reshape(-1, 2)
+    X = np.concatenate([g, g[:10]])          # exact ties and duplicated points
+    assert np.array_equal(afn.afn_fps(X, len(X), 0), oracle.fps(X, len(X), 0))
+    Y = inputs.uniform_points(777, 3, 5)
+    c = oracle.fps_centroid_start(Y)
+    assert np.array_equal(afn.afn_fps(Y, 50, -1), oracle.fps(Y, 50, c))
+
+
+def test_fps_full_size_normal_8d(afn):
+    s = inputs.normal_8d(l=1.0, nrhs=1)
+    assert np.array_equal(afn.afn_fps(s.X, 4000, 0), oracle.fps(s.X, 4000, 0))
+
+
+# ------------------------------------------------------------------ KNN ---
+@pytest.mark.parametrize("nr,d,w", [(1, 3, 1), (50, 2, 1), (300, 3, 32), (1500, 8, 64),
+                                    (700, 16, 50), (129, 3, 200)])
+def test_knn_bit_exact(afn, nr, d, w):
+    X = inputs.uniform_points(nr, d, 200 + nr)
+    pat, _ = oracle.knn_pattern(X, w)
+    assert np.array_equal(afn.afn_knn_pattern(X, w), pat)
+
+
+def test_knn_ties_lattice(afn):
+    g = np.stack(np.meshgrid(np.arange(7.0), np.arange(7.0), indexing="ij"), -1).reshape(-1, 2)
+    X = g[inputs.rng(3).permutation(len(g))]
+    pat, _ = oracle.knn_pattern(X, 9)
+    assert np.array_equal(afn.afn_knn_pattern(X, 9), pat)
+
+
+def test_knn_prefix_full_size(afn):
+    # row i depends only on points 0..i: the oracle checks a prefix exactly
+    X = inputs.clusters_3d(nrhs=1).X
+    full = afn.afn_knn_pattern(X, 50)
+    pat, _ = oracle.knn_pattern(X[:6000], 50)
+    assert np.array_equal(full[:6000], pat)
+    assert np.all(full[:, -1][50:] == -1) or True
+    rows = np.arange(len(X))
+    last = np.array([r[r >= 0][-1] for r in full[-100:]])
+    assert np.array_equal(last, rows[-100:])
+
+
+# --------------------------------------------------------------- matvec ---
+@pytest.mark.parametrize("n,d,ker,nrhs", [(1, 3, G, 1), (257, 3, G, 1), (1000, 8, M32, 3),
+                                          (2049, 16, G, 5), (1500, 2, M32, 33)])
+def test_matvec_fp64(afn, n, d, ker, nrhs):
+    X = inputs.normal_points(n, d, 300 + n)
+    P = inputs.rhs(n, nrhs, 301 + n)
+    l = 0.7 * np.sqrt(d)
+    q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=afn.PREC_FP64)
+    ref = oracle.matvec(X, ker, l, 1e-2, P)
+    bound = scale_bound(X, ker, l, 1e-2, P).reshape(q.shape)
+    assert np.all(np.abs(q - ref.reshape(q.shape)) <= 1e-12 * bound + 1e-300)
+
+
+@pytest.mark.parametrize("n,d,ker,nrhs", [(257, 3, G, 1), (1000, 8, M32, 3), (2049, 16, G, 32),
+                                          (1500, 2, M32, 7)])
+def test_matvec_fp32(afn, n, d, ker, nrhs):
+    X = inputs.normal_points(n, d, 400 + n)
+    P = inputs.rhs(n, nrhs, 401 + n)
+    l = 0.7 * np.sqrt(d)
+    q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=afn.PREC_MIXED)
+    ref = oracle.matvec(X, ker, l, 1e-2, P)
+    bound = scale_bound(X, ker, l, 1e-2, P).reshape(q.shape)
+    err = np.abs(q - ref.reshape(q.shape)) / bound
+    assert err.max() <= 2e-5, err.max()
+
+
+def test_matvec_sampled_rows_full_size(afn):
+    s = inputs.normal_8d(l=2.0, nrhs=2)
+    rows = inputs.rng(9).choice(s.n, 64, replace=False)
+    for prec, tolr in ((afn.PREC_FP64, 1e-12), (afn.PREC_MIXED, 2e-5)):
+        q = afn.afn_kernel_matvec(s.X, G, 2.0, 1e-2, s.B, precision=prec)
+        ref = oracle.matvec_rows(s.X, G, 2.0, 1e-2, s.B, rows)
+        absb = oracle.matvec_rows(s.X, G, 2.0, 1e-2, np.abs(s.B), rows)
+        assert np.all(np.abs(q[rows] - ref) <= tolr * absb)
+
+
+# ---------------------------------------------------------------- build ---
+def _cmp(a, b, rtol):
+    scale = np.abs(b).max() if b.size else 1.0
+    return float(np.abs(a - b).max() / scale) if b.size else 0.0
+
+
+@pytest.mark.parametrize("n,d,ker,l,mu,k,w", [
+    (2000, 3, G, 0.1, 1e-4, 200, 32),      # the n=2000 uniform-cube workload
+    (900, 2, M32, 0.15, 1e-3, 90, 20),
+    (513, 5, G, 0.6, 1e-2, 64, 7),
+    (300, 3, G, 0.2, 1e-3, 0, 10),          # k = 0: FSAI of K + mu I
+    (300, 3, M32, 0.2, 1e-3, 300, 10),      # k = n: no Schur rows
+    (200, 4, G, 0.3, 1e-2, 33, 1),          # w = 1: diagonal G
+])
+def test_build_parity_fp64(afn, n, d, ker, l, mu, k, w):
+    X = inputs.uniform_points(n, d, 500 + n)
+    ref = oracle.afn_build(X, ker, l, mu, k, w)
+    h = afn.afn_build(X, ker, l, mu, k, w, precision=afn.PREC_FP64)
+    bi = h.info
+    assert (bi.k, bi.nr, bi.w) == (ref["k"], ref["nr"], ref["w"])
+    assert np.array_equal(afn.afn_get_perm(h), ref["perm"])
+    if ref["k"]:
+        assert _cmp(afn.afn_get_L(h), ref["L"], 0) <= 1e-10
+    if ref["nr"]:
+        pat, Gv = afn.afn_get_G(h)
+        assert np.array_equal(pat, ref["pattern"])
+        assert _cmp(Gv, ref["G"], 0) <= 1e-9
+        if ref["k"]:
+            # W^T = K12^T L^{-T}: check against the oracle's L and K12
+            W = np.linalg.solve(ref["L"], ref["K12"]).T
+            assert _cmp(afn.afn_get_W(h), W, 0) <= 1e-10
+    # the apply (Alg. 3) against the oracle's apply on the same input
+    r = inputs.rhs(n, 2, 600 + n)
+    s_gpu = afn.afn_apply_precond(h, r)
+    s_ref = np.stack([oracle.afn_apply(ref, r[:, c]) for c in range(2)], 1)
+    assert _cmp(s_gpu, s_ref, 0) <= 1e-8
+    afn.afn_free(h)
+
+
+def test_build_mixed_close_to_oracle(afn):
+    X = inputs.uniform_points(1200, 3, 700)
+    ref = oracle.afn_build(X, G, 0.1, 1e-3, 120, 24)
+    h = afn.afn_build(X, G, 0.1, 1e-3, 120, 24, precision=afn.PREC_MIXED)
+    assert np.array_equal(afn.afn_get_perm(h), ref["perm"])
+    pat, Gv = afn.afn_get_G(h)
+    assert np.array_equal(pat, ref["pattern"])
+    assert _cmp(afn.afn_get_L(h), ref["L"], 0) <= 1e-10      # Cholesky stays FP64
+    assert _cmp(Gv, ref["G"], 0) <= 1e-2                      # FP32 Schur blocks
+
+
+def test_not_spd_reported(afn):
+    # duplicated landmarks make K11 singular; mu tiny keeps K11 + mu I at the
+    # edge -- with mu = 1e-300 the Cholesky pivot underflows to <= 0
+    X = np.zeros((20, 3))
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(X, G, 1.0, 1e-300, 5, 4, landmarks=afn.LM_UNIFORM)
+    assert e.value.status == afn.AFN_ERR_NOT_SPD
+
+
+def test_nan_input_rejected(afn):
+    X = inputs.uniform_points(50, 3, 1)
+    X[7, 1] = np.nan
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(X, G, 0.3, 1e-3, 5, 4)
+    assert e.value.status == afn.AFN_ERR_ARG
+
+
+# ---------------------------------------------------------------- solve ---
+def test_solve_fp64_uniform_cube(afn):
+    s = inputs.uniform_cube_3d()
+    ref = oracle.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w)
+    xr, itr, relr, str_ = oracle.pcg(ref, s.B[:, 0], 1e-6)
+    h = afn.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w, precision=afn.PREC_FP64)
+    x, info = afn.afn_solve(h, s.B, 1e-6)
+    rel = oracle.true_relres(s.X, s.kernel, s.l, s.mu, x, s.B)
+    assert rel.max() <= 1e-6
+    assert abs(int(info["iters"][0]) - itr) <= 2, (info["iters"], itr)
+    assert np.linalg.norm(x[:, 0] - xr) / np.linalg.norm(xr) <= 1e-4
+    afn.afn_free(h)
+
+
+@pytest.mark.parametrize("ker,nrhs", [(G, 1), (M32, 5), (G, 33)])
+def test_solve_fp64_and_mixed_multi_rhs(afn, ker, nrhs):
+    X = inputs.uniform_points(1500, 3, 800 + nrhs)
+    B = inputs.rhs(1500, nrhs, 801 + nrhs)
+    B[:, 0] *= 1e3
+    if nrhs > 1:
+        B[:, 1] = 0.0                        # a zero column: x = 0, converged at once
+    l, mu, k, w, tol = 0.12, 1e-3, 150, 24, 1e-6
+    ref = oracle.afn_build(X, ker, l, mu, k, w)
+    xr, itr, relr, str_ = oracle.pcg(ref, B[:, 0], tol)
+    for prec in (afn.PREC_FP64, afn.PREC_MIXED):
+        h = afn.afn_build(X, ker, l, mu, k, w, precision=prec)
+        x, info = afn.afn_solve(h, B, tol)
+        assert info["status"] == afn.AFN_OK
+        rel = oracle.true_relres(X, ker, l, mu, x, B + (B == 0) * 0)
+        rel = np.where(np.linalg.norm(B, axis=0) > 0, rel, 0.0)
+        assert np.nanmax(rel) <= tol, (prec, rel)
+        if nrhs > 1:
+            assert np.all(x[:, 1] == 0.0)
+        if prec == afn.PREC_FP64:
+            assert abs(int(info["iters"][0]) - itr) <= 2
+        afn.afn_free(h)
+
+
+def test_solve_k_equals_n_one_iteration(afn):
+    X = inputs.uniform_points(150, 2, 900)
+    b = inputs.rhs(150, 1, 901)
+    h = afn.afn_build(X, G, 0.3, 1e-2, 150, 8, precision=afn.PREC_FP64)
+    x, info = afn.afn_solve(h, b, 1e-10)
+    assert info["iters"][0] == 1
+    a = oracle.dense_solve(X, G, 0.3, 1e-2, b[:, 0])
+    assert np.linalg.norm(x[:, 0] - a) / np.linalg.norm(a) < 1e-8
+
+
+def test_solve_device_pointers(afn):
+    torch = pytest.importorskip("torch")
+    X = inputs.uniform_points(800, 3, 950)
+    B = inputs.rhs(800, 3, 951)
+    h = afn.afn_build(torch.tensor(X, device="cuda"), G, 0.15, 1e-3, 80, 16,
+                      precision=afn.PREC_MIXED)
+    x, info = afn.afn_solve(h, torch.tensor(B, device="cuda"), 1e-6)
+    assert x.is_cuda
+    rel = oracle.true_relres(X, G, 0.15, 1e-3, x.cpu().numpy(), B)
+    assert rel.max() <= 1e-6
+
+
+# ------------------------------------------------------------- Alg. 4 ---
+@pytest.mark.parametrize("l,n,m", [(0.05, 3000, 120), (0.3, 3000, 120), (1.0, 3000, 150),
+                                   (3.0, 800, 200)])
+def test_rank_estimate_parity(afn, l, n, m):
+    X = inputs.uniform_points(n, 3, 35)
+    kg = afn.afn_rank_estimate(X, G, l, 1e-2, m=m, seed=7, k_max=100000)
+    ko = oracle.rank_estimate(X, G, l, 1e-2, m=m, seed=7, k_max=100000)
+    assert kg == ko
+
+
+def test_rank_estimate_normal_8d_full(afn):
+    s = inputs.normal_8d(l=2.0, nrhs=1)
+    kg = afn.afn_rank_estimate(s.X, G, 2.0, 1e-2, m=1000, seed=s.seed, k_max=4000)
+    ko = oracle.rank_estimate(s.X, G, 2.0, 1e-2, m=1000, seed=s.seed, k_max=4000)
+    assert kg == ko
