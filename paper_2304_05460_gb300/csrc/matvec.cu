@@ -105,9 +105,12 @@ __global__ void __launch_bounds__(NT) matvec32_kernel(const float *__restrict__ 
     float xi[D];
 #pragma unroll
     for (int t = 0; t < D; ++t) xi[t] = (i < n) ? Xs[i * DS + t] : 0.f;
-    float acc[NR];
+    // two-level accumulation: a tile partial (TJ/JG terms) is folded into the
+    // running sum with Kahan compensation, so the FP32 rounding of a row sum
+    // grows like sqrt(TJ/JG) instead of sqrt(n / (JG * chunks)).
+    float acc[NR], cmp[NR];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) acc[c] = 0.f;
+    for (int c = 0; c < NR; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
 
     for (int64_t jt = j0; jt < j1; jt += TJ) {
         __syncthreads();
@@ -121,6 +124,9 @@ __global__ void __launch_bounds__(NT) matvec32_kernel(const float *__restrict__ 
             ps[c * TJ + jj] = (j < j1) ? P[c * ldp + j] : 0.f;
         }
         __syncthreads();
+        float tac[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) tac[c] = 0.f;
 #pragma unroll 4
         for (int jj = g * (TJ / JG); jj < (g + 1) * (TJ / JG); ++jj) {
             const float *xj = xs + jj * DS;
@@ -132,7 +138,14 @@ __global__ void __launch_bounds__(NT) matvec32_kernel(const float *__restrict__ 
             }
             float kv = kernel32_scaled<KER>(r2);
 #pragma unroll
-            for (int c = 0; c < NR; ++c) acc[c] = fmaf(kv, ps[c * TJ + jj], acc[c]);
+            for (int c = 0; c < NR; ++c) tac[c] = fmaf(kv, ps[c * TJ + jj], tac[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            float y = tac[c] - cmp[c];
+            float t = acc[c] + y;
+            cmp[c] = (t - acc[c]) - y;
+            acc[c] = t;
         }
     }
     __syncthreads();

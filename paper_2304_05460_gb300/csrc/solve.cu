@@ -31,7 +31,7 @@ enum DotMode { M_STORE = 0, M_ALPHA, M_RR, M_BETA, M_RHO0, M_NORM };
 
 struct Cols {                 // device arrays, one entry per column
     double *rho, *alpha, *beta, *val, *bnorm, *tolabs, *part;
-    int *active, *iters, *conv;
+    int *active, *iters, *conv, *base;   // base: iters at the start of this inner solve
     unsigned int *cnt;
     int *nactive;
 };
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(DB) dot_kernel(T *a, const T *b, T *x, const T
         }
         break;
     case M_RR:
-        if (act && (sqrt(v) <= cs.tolabs[c] || cs.iters[c] >= maxit)) {
+        if (act && (sqrt(v) <= cs.tolabs[c] || cs.iters[c] - cs.base[c] >= maxit)) {
             cs.active[c] = 0;
             cs.conv[c] = sqrt(v) <= cs.tolabs[c] ? 1 : 0;
         }
@@ -173,7 +173,7 @@ template <class T> static T *carve(char *&p, size_t count)
 
 static size_t cols_bytes(int nrhs)
 {
-    return (size_t)nrhs * (8 * 7 + 4 * 3 + 4) + (size_t)nrhs * DMAXB * 8 + 8 * 256 + 4096;
+    return (size_t)nrhs * (8 * 7 + 4 * 4 + 4) + (size_t)nrhs * DMAXB * 8 + 8 * 256 + 8192;
 }
 
 static void carve_cols(char *&p, int nrhs, Cols &cs)
@@ -188,6 +188,7 @@ static void carve_cols(char *&p, int nrhs, Cols &cs)
     cs.active = carve<int>(p, nrhs);
     cs.iters = carve<int>(p, nrhs);
     cs.conv = carve<int>(p, nrhs);
+    cs.base = carve<int>(p, nrhs);
     cs.cnt = carve<unsigned int>(p, nrhs);
     cs.nactive = carve<int>(p, 1);
 }
@@ -357,6 +358,7 @@ __global__ void set_cols_kernel(Cols cs, int nrhs, double tol, const double *bn,
     cs.conv[c] = bn[c] > 0.0 ? 0 : 1;
     cs.alpha[c] = cs.beta[c] = 0.0;
     if (reset_iters) cs.iters[c] = 0;
+    cs.base[c] = 0;   // FP64 PCG: max_iter caps all iterations, restarts included
 }
 
 // columns whose true relative residual is above tol become active again
@@ -396,6 +398,7 @@ __global__ void outer_prep_kernel(Cols in, Cols out, int nrhs, double tol, doubl
     out.conv[c] = rel <= tol ? 1 : 0;
     in.active[c] = act;
     in.cnt[c] = 0;
+    in.base[c] = in.iters[c];   // max_iter caps each inner solve
     in.alpha[c] = in.beta[c] = 0.0;
     // inner target: the requested inner tolerance, relaxed so that the last
     // outer step does not over-solve past what the FP64 test asks for
