@@ -176,6 +176,31 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
                              int32_t precision, void *stream);
 
 /*
+ * afn_kernel_matvec_noalloc: the FP64 q = (K + mu I) p of afn_kernel_matvec
+ * for callers that cannot allocate device memory (code running while a stream
+ * is captured into a CUDA graph, services with a pre-planned device pool,
+ * plug-ins that must not grow the process's device footprint).  The paper has
+ * no counterpart; this is an interface convenience.
+ *  - points (n x d row-major), p and q (n x nrhs column-major) must all be
+ *    device memory on the current device; nothing is staged or allocated.
+ *  - The split-K partial sums live in a fixed 16 MiB __device__ array built
+ *    into the library (held by every GPU that loads it until exit).  Columns
+ *    are processed in groups of up to 8 that fit it; a size whose single
+ *    column does not fit (n above roughly 2 million) is rejected with
+ *    AFN_ERR_ARG and a message naming the bytes needed.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make it before any
+ *    stream capture.
+ *  - All calls share the array: calls whose kernels overlap on the GPU (on
+ *    streams with no ordering between them) race.  Calls in order on one
+ *    stream are safe; nothing needs zeroing between calls.
+ * Synchronises `stream` before returning.  Errors: AFN_ERR_ARG, AFN_ERR_CUDA.
+ */
+afn_status afn_kernel_matvec_noalloc(const double *points, int64_t n, int32_t d, int32_t kernel,
+                                     double l, double mu, const double *p, int32_t nrhs,
+                                     double *q, void *stream);
+
+/*
  * Farthest point sampling, Alg. 6: idx[0] = start (or the point nearest the
  * centroid when start == -1), then k-1 times the point with the largest
  * squared distance (FP64, summed over dimensions in order, no fused

@@ -79,6 +79,7 @@ def _load():
         "afn_rank_estimate": (i32, [P, i64, i32, i32, dbl, dbl, i32, u64, i32, C.POINTER(i64),
                                     C.POINTER(i64), C.POINTER(i32), P]),
         "afn_launch_count": (i64, []),
+        "afn_kernel_matvec_noalloc": (i32, [P, i64, i32, i32, dbl, dbl, P, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -301,6 +302,18 @@ def afn_kernel_matvec(points, kernel, l, mu, p, precision=PREC_FP64, stream=None
     _check(_lib.afn_kernel_matvec(px, n, d, int(kernel), float(l), float(mu), pp, nrhs, po,
                                   int(precision), _stream_ptr(stream)))
     return out.T if out.ndim == 2 else out
+
+
+def afn_kernel_matvec_noalloc(points, kernel, l, mu, p, q, stream=None):
+    """FP64 (K + mu I) p into q without any device allocation.  points (n x d),
+    p and q (n x nrhs) must be contiguous CUDA float64 tensors; p and q are
+    passed as their transposes' storage (column-major n x nrhs)."""
+    n, d = int(points.shape[0]), int(points.shape[1])
+    nrhs = 1 if p.dim() == 1 else int(p.shape[0])
+    _check(_lib.afn_kernel_matvec_noalloc(C.c_void_p(points.data_ptr()), n, d, int(kernel),
+                                          float(l), float(mu), C.c_void_p(p.data_ptr()), nrhs,
+                                          C.c_void_p(q.data_ptr()), _stream_ptr(stream)))
+    return q
 
 
 def afn_fps(points, k, start=0, stream=None):
