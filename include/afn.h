@@ -73,8 +73,10 @@ typedef struct {
     int64_t fps_start;         /* FPS start index; -1 = the point nearest the centroid (Alg. 6) */
     uint64_t seed;             /* SplitMix64 seed for uniform landmarks and Alg. 4's subsample */
     int32_t max_iter;          /* PCG iteration cap per column (FP64) / per inner solve; default 500 */
-    int32_t max_outer;         /* mixed precision: FP64 refinement steps cap; default 10 */
-    double inner_tol;          /* mixed precision: inner relative tolerance; default 1e-4 */
+    int32_t max_outer;         /* mixed precision, restarted refinement only (AFN_REFINE=restart):
+                                  FP64 refinement steps cap; default 10 */
+    double inner_tol;          /* mixed precision: drop of the FP32 recursive residual between
+                                  two FP64 residual replacements (delta); default 0.01 */
     int32_t check_every;       /* iterations between host convergence polls; default 4 */
     int32_t profile;           /* 1 = time every launch with CUDA events (afn_get_kernel_stats) */
     void *stream;              /* cudaStream_t; NULL = default stream */
@@ -123,8 +125,11 @@ afn_status afn_build(const double *points, int64_t n, int32_t d, int32_t kernel,
  * Solve (K + mu I) x = rhs for nrhs columns with AFN-PCG (Alg. 3, Alg. 5),
  * relative residual tol on each column (||r||_2 <= tol ||b||_2).  FP64 mode:
  * textbook PCG, then the true residual is recomputed and PCG restarts from x
- * while it is above tol (at most 3 restarts).  Mixed mode: FP32 inner PCG
- * inside FP64 iterative refinement until the FP64 residual is <= tol.
+ * while it is above tol (at most 3 restarts).  Mixed mode: one FP32 PCG
+ * sequence (FP32 matvec, apply and vectors; FP64 dots and scalars) whose
+ * residual is replaced by the FP64 residual b - (K + mu I) x (x kept in FP64)
+ * each time the recursive residual has dropped by inner_tol; a column stops
+ * when its FP64 residual is <= tol.
  * rhs, x_out: n x nrhs column-major, original point order.  info may be NULL.
  * Errors: AFN_ERR_ARG, AFN_ERR_OOM, AFN_ERR_NO_CONVERGE (x_out holds the last
  * iterate), AFN_ERR_CUDA.

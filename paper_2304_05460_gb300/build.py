@@ -32,8 +32,9 @@ def nvcc() -> str:
 
 
 def _flags():
+    extra = os.environ.get("AFN_NVCC_FLAGS", "").split()   # tuning: e.g. -DAFN_TC_FOLD=2
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                   "-Xptxas", "-warn-spills"]
+                   "-Xptxas", "-warn-spills"] + extra
 
 
 def _stale(obj, deps):

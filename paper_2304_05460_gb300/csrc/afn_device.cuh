@@ -67,6 +67,44 @@ __device__ __forceinline__ float kernel32_scaled(float r2)
     return (1.0f + t) * ex2_approx(t * -1.4426950408889634f);
 }
 
+// Packed FP32 pairs (two floats in one 64-bit register, low = first):
+// Blackwell's f32x2 add / sub / fma issue one instruction for two lanes of
+// work.  Rounding is the same as the scalar .rn operations.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
+{
+    f2_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 // Lexicographic "better" for argmax with lowest-index tie-break.
 __device__ __forceinline__ bool better_max(double v1, int64_t i1, double v2, int64_t i2)
 {

@@ -168,6 +168,223 @@ __global__ void spmv_gt_kernel(const T *__restrict__ G, const int32_t *__restric
     out[c * ldo + j] = s;
 }
 
+// Row-major forms of the two sparse products for many right-hand sides: one
+// warp per row, lanes over columns; the pattern index and value of each
+// nonzero are one broadcast load, the gathered row is one coalesced read.
+template <class T>
+__global__ void spmv_ell_rm_kernel(const T *__restrict__ G, const int32_t *__restrict__ pat,
+                                   int64_t nr, int w, int nrhs, const T *__restrict__ trm,
+                                   T *__restrict__ yrm)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (i >= nr) return;
+    for (int cb = 0; cb < nrhs; cb += 32) {
+        const int c = cb + lane;
+        T s = 0;
+        for (int p = 0; p < w; ++p) {
+            const int32_t j = pat[i * w + p];
+            if (j < 0) break;
+            const T g = G[i * w + p];
+            if (c < nrhs) s += g * trm[(int64_t)j * nrhs + c];
+        }
+        if (c < nrhs) yrm[i * nrhs + c] = s;
+    }
+}
+
+template <class T>
+__global__ void spmv_gt_rm_kernel(const T *__restrict__ G, const int32_t *__restrict__ ptr,
+                                  const int32_t *__restrict__ row,
+                                  const int32_t *__restrict__ slot, int64_t nr, int nrhs,
+                                  const T *__restrict__ yrm, T *__restrict__ orm)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= nr) return;
+    const int32_t q0 = ptr[j], q1 = ptr[j + 1];
+    for (int cb = 0; cb < nrhs; cb += 32) {
+        const int c = cb + lane;
+        T s = 0;
+        for (int32_t q = q0; q < q1; ++q) {
+            const int32_t r = row[q];
+            const T g = G[slot[q]];
+            if (c < nrhs) s += g * yrm[(int64_t)r * nrhs + c];
+        }
+        if (c < nrhs) orm[j * nrhs + c] = s;
+    }
+}
+
+// out[i*cols + c] = in[c*ldin + i]  (column-major -> row-major), 32x32 tiles
+template <class T>
+__global__ void cm_to_rm_kernel(const T *__restrict__ in, int64_t ldin, int64_t rows, int cols,
+                                T *__restrict__ out)
+{
+    __shared__ T t[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        int c = c0 + q;
+        int64_t i = i0 + threadIdx.x;
+        if (c < cols && i < rows) t[q][threadIdx.x] = in[c * ldin + i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        int64_t i = i0 + q;
+        int c = c0 + threadIdx.x;
+        if (c < cols && i < rows) out[i * cols + c] = t[threadIdx.x][q];
+    }
+}
+
+// out[c*ldout + i] = in[i*cols + c]  (row-major -> column-major)
+template <class T>
+__global__ void rm_to_cm_kernel(const T *__restrict__ in, int64_t rows, int cols,
+                                T *__restrict__ out, int64_t ldout)
+{
+    __shared__ T t[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        int64_t i = i0 + q;
+        int c = c0 + threadIdx.x;
+        if (c < cols && i < rows) t[q][threadIdx.x] = in[i * cols + c];
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        int c = c0 + q;
+        int64_t i = i0 + threadIdx.x;
+        if (c < cols && i < rows) out[c * ldout + i] = t[threadIdx.x][q];
+    }
+}
+
+// --------------------------------------------------------------------------
+// Tiled product for many right-hand sides (NC in {8, 16, 32}):
+//   TA == false: out = A X,   A row-major M x K        (A[i,p] = A[i*lda+p])
+//   TA == true : out = A^T X, A row-major K x M        (A^T[i,p] = A[p*lda+i])
+// X is K x NC column-major (ldx).  A CTA owns GM = 128 output rows and one
+// K-chunk; 256 threads each hold an RM x 4 register tile.  TRI = 1 keeps only
+// p <= i (lower), TRI = 2 only p >= i (upper).  With one K-chunk the epilogue
+// writes O = beta Y + alpha acc directly; otherwise per-chunk partials go to
+// `part` (chunk-major) and gemm_finish sums them in order.
+// --------------------------------------------------------------------------
+static constexpr int GM = 128;     // output rows per CTA
+static constexpr int GK = 16;      // K per shared-memory stage
+
+template <class T, int NC, bool TA, int TRI>
+__global__ void __launch_bounds__(256) gemm_kernel(const T *__restrict__ A, int64_t lda, int64_t M,
+                                                   int64_t K, const T *__restrict__ X,
+                                                   int64_t ldx, int64_t chunk,
+                                                   T *__restrict__ part, const T *__restrict__ Y,
+                                                   int64_t ldy, T *__restrict__ O, int64_t ldo,
+                                                   T alpha, T beta)
+{
+    constexpr int TC = NC / 4;             // threads along columns
+    constexpr int TR = 256 / TC;           // threads along rows
+    constexpr int RM = GM / TR;            // rows per thread
+    __shared__ __align__(16) T as[GK][GM + 4];
+    __shared__ __align__(16) T xs[GK][NC + 4];
+    const int tc = threadIdx.x % TC, tr = threadIdx.x / TC;
+    const int64_t r0 = (int64_t)blockIdx.x * GM;
+    int64_t k0 = (int64_t)blockIdx.y * chunk;
+    int64_t k1 = min(K, k0 + chunk);
+    if (TRI == 1) k1 = min(k1, r0 + GM);          // p <= i <= r0 + GM - 1
+    if (TRI == 2) k0 = max(k0, r0);               // p >= i >= r0
+    T acc[RM][4];
+#pragma unroll
+    for (int a = 0; a < RM; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    // register prefetch: the next stage's global loads are issued before the
+    // current stage is computed
+    constexpr int LA = GM * GK / 256;                        // A elements per thread
+    constexpr int LX = (GK * NC + 255) / 256;                // X elements per thread
+    T ra[LA], rx[LX];
+    auto fetch = [&](int64_t kk0) {
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            int e = threadIdx.x + u * 256;
+            int r, q;
+            if (TA) { q = e / GM; r = e % GM; }       // coalesced along i
+            else { r = e / GK; q = e % GK; }          // coalesced along p
+            int64_t gi = r0 + r, gp = kk0 + q;
+            T v = 0;
+            if (gi < M && gp < k1) {
+                bool keep = (TRI == 0) || (TRI == 1 && gp <= gi) || (TRI == 2 && gp >= gi);
+                if (keep) v = TA ? A[gp * lda + gi] : A[gi * lda + gp];
+            }
+            ra[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < LX; ++u) {
+            int e = threadIdx.x + u * 256;
+            int c = e / GK, q = e % GK;
+            int64_t gp = kk0 + q;
+            rx[u] = (e < GK * NC && gp < k1) ? X[c * ldx + gp] : (T)0;
+        }
+    };
+    if (k0 < k1) fetch(k0);
+    for (int64_t kk0 = k0; kk0 < k1; kk0 += GK) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            int e = threadIdx.x + u * 256;
+            int r, q;
+            if (TA) { q = e / GM; r = e % GM; }
+            else { r = e / GK; q = e % GK; }
+            as[q][r] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < LX; ++u) {
+            int e = threadIdx.x + u * 256;
+            if (e < GK * NC) xs[e % GK][e / GK] = rx[u];
+        }
+        __syncthreads();
+        if (kk0 + GK < k1) fetch(kk0 + GK);
+#pragma unroll
+        for (int q = 0; q < GK; ++q) {
+            T av[RM], xv[4];
+#pragma unroll
+            for (int a = 0; a < RM; ++a) av[a] = as[q][tr * RM + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) xv[b] = xs[q][tc * 4 + b];
+#pragma unroll
+            for (int a = 0; a < RM; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * xv[b];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+        int64_t gi = r0 + tr * RM + a;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int c = tc * 4 + b;
+            if (gridDim.y == 1) {
+                T base = (beta != (T)0) ? beta * Y[c * ldy + gi] : (T)0;
+                O[c * ldo + gi] = base + alpha * acc[a][b];
+            } else {
+                part[((int64_t)blockIdx.y * NC + c) * M + gi] = acc[a][b];
+            }
+        }
+    }
+}
+
+// O[i,c] = beta Y[i,c] + alpha sum_q part[q][c][i]
+template <class T>
+__global__ void gemm_finish(const T *__restrict__ part, int js, int nc, int64_t M,
+                            const T *__restrict__ Y, int64_t ldy, T *__restrict__ O, int64_t ldo,
+                            T alpha, T beta)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * nc) return;
+    int c = (int)(e / M);
+    int64_t i = e % M;
+    T s = 0;
+    for (int q = 0; q < js; ++q) s += part[((int64_t)q * nc + c) * M + i];
+    T base = (beta != (T)0) ? beta * Y[c * ldy + i] : (T)0;
+    O[c * ldo + i] = base + alpha * s;
+}
+
 template <class T>
 __global__ void copy_cols_kernel(const T *__restrict__ a, int64_t lda, T *__restrict__ b,
                                  int64_t ldb, int64_t rows, int nrhs)
@@ -219,12 +436,80 @@ static int colmul_js(int64_t nrows, int64_t ncols)
     return (int)std::max<int64_t>(1, std::min<int64_t>(js, 128));
 }
 
+static constexpr int GEMM_JS_MAX = 64;
+
 size_t apply_tmp_elems(const Handle *h, int nrhs)
 {
     int64_t k = h->k, nr = h->nr;
-    int js = colmul_js(nr, k);
-    int piece_max = 16;
-    return (size_t)(2 * k * nrhs + 2 * nr * nrhs) + (size_t)js * piece_max * (size_t)std::max<int64_t>(k, 1) + 64;
+    int js = std::max(colmul_js(nr, k), GEMM_JS_MAX);
+    // zp, u (k x nrhs), t, y (nr x nrhs), GEMM partials, row-major copy (nr x nrhs)
+    return (size_t)(2 * k * nrhs + 3 * nr * nrhs) + (size_t)js * 32 * (size_t)std::max<int64_t>(k, 1) + 64;
+}
+
+static int gemm_js(int64_t M, int64_t K)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t mb = (M + GM - 1) / GM;
+    int64_t js = (4 * (int64_t)sms + mb - 1) / mb;
+    js = std::min<int64_t>(js, std::max<int64_t>(1, K / 256));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(js, GEMM_JS_MAX));
+}
+
+// out = beta Y + alpha op(A) X for nrhs columns (op(A) = A or A^T, TRI as in
+// gemm_kernel); part holds GEMM_JS_MAX * 32 * M elements of scratch.
+template <class T, bool TA, int TRI>
+static void prod(const T *A, int64_t lda, int64_t M, int64_t K, const T *X, int64_t ldx,
+                 const T *Y, int64_t ldy, T *O, int64_t ldo, T alpha, T beta, int nrhs, T *part,
+                 size_t part_cap, cudaStream_t s)
+{
+    for (int c0 = 0; c0 < nrhs;) {
+        int left = nrhs - c0;
+        const T *x = X + c0 * ldx;
+        const T *y = Y ? Y + c0 * ldy : nullptr;
+        T *o = O + c0 * ldo;
+        if (left >= 8) {
+            int b = left >= 32 ? 32 : (left >= 16 ? 16 : 8);
+            int js = gemm_js(M, K);
+            js = (int)std::max<int64_t>(1, std::min<int64_t>(js, (int64_t)(part_cap / ((size_t)b * M))));
+            int64_t chunk = (K + js - 1) / js;
+            chunk = (chunk + GK - 1) / GK * GK;
+            js = (int)std::max<int64_t>(1, (K + chunk - 1) / chunk);
+            dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)js);
+#define GL(NC) gemm_kernel<T, NC, TA, TRI><<<grid, 256, 0, s>>>(A, lda, M, K, x, ldx, chunk, part, \
+                                                                 y, ldy, o, ldo, alpha, beta)
+            if (b == 32) GL(32); else if (b == 16) GL(16); else GL(8);
+#undef GL
+            if (js > 1) {
+                int64_t tot = M * b;
+                gemm_finish<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, js, b, M, y, ldy,
+                                                                            o, ldo, alpha, beta);
+            }
+            c0 += b;
+            continue;
+        }
+        int b = piece(left, 4);
+        if (!TA) {
+            rowmul<T, TRI>(A, lda, M, K, x, ldx, y, ldy, o, ldo, alpha, beta, b, s);
+        } else {
+            // transposed tail: split-K column kernel, then o = y - sum (alpha = -1, beta = 1)
+            int js = colmul_js(K, M);
+            js = (int)std::max<int64_t>(1, std::min<int64_t>(js, (int64_t)(part_cap / ((size_t)b * M))));
+            int64_t chunk = (K + js - 1) / js;
+            js = (int)((K + chunk - 1) / chunk);
+            dim3 grid((unsigned)((M + CT - 1) / CT), (unsigned)js);
+            switch (b) {
+            case 1: colmul_kernel<T, 1><<<grid, CT, 0, s>>>(A, lda, K, M, x, ldx, part, chunk); break;
+            case 2: colmul_kernel<T, 2><<<grid, CT, 0, s>>>(A, lda, K, M, x, ldx, part, chunk); break;
+            default: colmul_kernel<T, 4><<<grid, CT, 0, s>>>(A, lda, K, M, x, ldx, part, chunk); break;
+            }
+            int64_t tot = M * b;
+            colmul_finish<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, js, b, M, y, ldy, o,
+                                                                           ldo);
+        }
+        c0 += b;
+    }
 }
 
 template <class T>
@@ -237,48 +522,44 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
     T *u = zp + k * nrhs;              // k x nrhs
     T *t = u + k * nrhs;               // nr x nrhs
     T *y = t + nr * nrhs;              // nr x nrhs
-    T *part = y + nr * nrhs;           // js x 16 x k
+    T *part = y + nr * nrhs;           // GEMM_JS_MAX x 32 x k
+    const size_t pcap = (size_t)std::max(colmul_js(nr, k), GEMM_JS_MAX) * 32 *
+                        (size_t)std::max<int64_t>(k, 1);
     const T *r1 = r, *r2 = r + k;
     T *s1 = s, *s2 = s + k;
-    if (k > 0) rowmul<T, 1>(Linv, k, k, k, r1, n, nullptr, 0, zp, k, (T)1, (T)0, nrhs, st);
+    if (k > 0) prod<T, false, 1>(Linv, k, k, k, r1, n, nullptr, 0, zp, k, (T)1, (T)0, nrhs, part, pcap, st);
     if (nr > 0) {
-        if (k > 0) rowmul<T, 0>(Wt, k, nr, k, zp, k, r2, n, t, nr, (T)-1, (T)1, nrhs, st);
+        if (k > 0) prod<T, false, 0>(Wt, k, nr, k, zp, k, r2, n, t, nr, (T)-1, (T)1, nrhs, part, pcap, st);
         else {
             int64_t tot = nr * nrhs;
             copy_cols_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r2, n, t, nr, nr, nrhs);
         }
         int64_t tot = nr * nrhs;
-        unsigned g = (unsigned)((tot + 255) / 256);
-        spmv_ell_kernel<T><<<g, 256, 0, st>>>(G, h->pat.as<int32_t>(), nr, w, nrhs, t, nr, y, nr);
-        spmv_gt_kernel<T><<<g, 256, 0, st>>>(G, h->gt_ptr.as<int32_t>(), h->gt_row.as<int32_t>(),
-                                             h->gt_slot.as<int32_t>(), nr, nrhs, y, nr, s2, n);
+        if (nrhs >= 8) {
+            // row-major copies: t -> trm, G trm -> y (row-major), G^T y -> trm -> s2
+            T *trm = part + pcap;
+            dim3 tb(32, 8), tg((unsigned)((nr + 31) / 32), (unsigned)((nrhs + 31) / 32));
+            unsigned gw = (unsigned)((nr + 7) / 8);
+            cm_to_rm_kernel<T><<<tg, tb, 0, st>>>(t, nr, nr, nrhs, trm);
+            spmv_ell_rm_kernel<T><<<gw, 256, 0, st>>>(G, h->pat.as<int32_t>(), nr, w, nrhs, trm, y);
+            spmv_gt_rm_kernel<T><<<gw, 256, 0, st>>>(G, h->gt_ptr.as<int32_t>(), h->gt_row.as<int32_t>(),
+                                                     h->gt_slot.as<int32_t>(), nr, nrhs, y, trm);
+            rm_to_cm_kernel<T><<<tg, tb, 0, st>>>(trm, nr, nrhs, s2, n);
+        } else {
+            unsigned g = (unsigned)((tot + 255) / 256);
+            spmv_ell_kernel<T><<<g, 256, 0, st>>>(G, h->pat.as<int32_t>(), nr, w, nrhs, t, nr, y, nr);
+            spmv_gt_kernel<T><<<g, 256, 0, st>>>(G, h->gt_ptr.as<int32_t>(), h->gt_row.as<int32_t>(),
+                                                 h->gt_slot.as<int32_t>(), nr, nrhs, y, nr, s2, n);
+        }
     }
     if (k > 0) {
         if (nr > 0) {
-            int js = colmul_js(nr, k);
-            int64_t chunk = (nr + js - 1) / js;
-            js = (int)((nr + chunk - 1) / chunk);
-            for (int c0 = 0; c0 < nrhs;) {
-                int b = piece(nrhs - c0, 16);
-                dim3 grid((unsigned)((k + CT - 1) / CT), (unsigned)js);
-                const T *x = s2 + c0 * n;
-                switch (b) {
-                case 1: colmul_kernel<T, 1><<<grid, CT, 0, st>>>(Wt, k, nr, k, x, n, part, chunk); break;
-                case 2: colmul_kernel<T, 2><<<grid, CT, 0, st>>>(Wt, k, nr, k, x, n, part, chunk); break;
-                case 4: colmul_kernel<T, 4><<<grid, CT, 0, st>>>(Wt, k, nr, k, x, n, part, chunk); break;
-                case 8: colmul_kernel<T, 8><<<grid, CT, 0, st>>>(Wt, k, nr, k, x, n, part, chunk); break;
-                default: colmul_kernel<T, 16><<<grid, CT, 0, st>>>(Wt, k, nr, k, x, n, part, chunk); break;
-                }
-                int64_t tot = k * b;
-                colmul_finish<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-                    part, js, b, k, zp + c0 * k, k, u + c0 * k, k);
-                c0 += b;
-            }
+            prod<T, true, 0>(Wt, k, k, nr, s2, n, zp, k, u, k, (T)-1, (T)1, nrhs, part, pcap, st);
         } else {
             int64_t tot = k * nrhs;
             copy_cols_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(zp, k, u, k, k, nrhs);
         }
-        rowmul<T, 2>(LinvT, k, k, k, u, k, nullptr, 0, s1, n, (T)1, (T)0, nrhs, st);
+        prod<T, false, 2>(LinvT, k, k, k, u, k, nullptr, 0, s1, n, (T)1, (T)0, nrhs, part, pcap, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "apply launch");

@@ -403,7 +403,7 @@ void afn_default_options(afn_options *o)
     o->seed = 0;
     o->max_iter = 500;
     o->max_outer = 10;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 0.01;
     o->check_every = 4;
     o->profile = 0;
     o->stream = nullptr;

@@ -5,9 +5,12 @@
 //    relative residual ||r|| <= tol ||b||, then the true residual is
 //    recomputed and a column that is above tol restarts from its x (at most
 //    3 restarts, iterations counted across restarts).
-//  * Mixed handles: FP64 iterative refinement around an FP32 inner PCG:
-//    r = b - (K + mu I) x in FP64, the inner PCG solves (K + mu I) d = r/||r||
-//    in FP32 vectors (FP64 dots and scalars) to a relative tolerance, x += ||r|| d.
+//  * Mixed handles: one FP32 PCG sequence with reliable updates (see
+//    mixed_reliable): FP32 matvec / apply / vectors, FP64 scalars, x in FP64,
+//    and the residual replaced by the FP64 residual b - (K + mu I) x whenever
+//    the recursive one has dropped by inner_tol.  (AFN_REFINE=restart selects
+//    the earlier restarted refinement: FP32 inner PCG to inner_tol, then
+//    x += d and a new FP64 residual.)
 //
 // Scalars (rho, alpha, beta, norms) live on the device in FP64 per column.
 // Each dot product is a two-level reduction whose last block sums the
@@ -17,6 +20,8 @@
 // the number of active columns every `check_every` iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "afn_device.cuh"
@@ -27,14 +32,27 @@ namespace afn {
 static constexpr int DB = 256;        // threads per dot block
 static constexpr int DMAXB = 512;     // max blocks per column
 
-enum DotMode { M_STORE = 0, M_ALPHA, M_RR, M_BETA, M_RHO0, M_NORM };
+enum DotMode { M_STORE = 0, M_ALPHA, M_RR, M_BETA, M_RHO0, M_NORM, M_RRU };
 
 struct Cols {                 // device arrays, one entry per column
     double *rho, *alpha, *beta, *val, *bnorm, *tolabs, *part;
+    double *rmax2;            // largest ||r||^2 since the last residual replacement
     int *active, *iters, *conv, *base;   // base: iters at the start of this inner solve
+    int *flag;                // residual replacement requested
     unsigned int *cnt;
-    int *nactive;
+    int *nactive, *nflag;
 };
+
+// AFN_LOG=1 in the environment prints the refinement history to stderr
+static bool log_on()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("AFN_LOG");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
 
 static int dot_blocks(int64_t n)
 {
@@ -123,6 +141,16 @@ __global__ void __launch_bounds__(DB) dot_kernel(T *a, const T *b, T *x, const T
     case M_NORM:
         cs.bnorm[c] = sqrt(v);
         break;
+    case M_RRU:
+        // reliable updates: ask for an FP64 residual replacement once the
+        // recursive residual fell by tolabs (= delta) since the last one, or
+        // when the iteration cap is reached
+        if (act) {
+            if (v > cs.rmax2[c]) cs.rmax2[c] = v;
+            const double dl = cs.tolabs[c];
+            if (v <= dl * dl * cs.rmax2[c] || cs.iters[c] - cs.base[c] >= maxit) cs.flag[c] = 1;
+        }
+        break;
     default:
         break;
     }
@@ -143,9 +171,13 @@ __global__ void pupdate_kernel(T *p, const T *z, int64_t n, int64_t ld, Cols cs,
 
 __global__ void count_active_kernel(Cols cs, int nrhs)
 {
-    int s = 0;
-    for (int c = 0; c < nrhs; ++c) s += cs.active[c];
+    int s = 0, f = 0;
+    for (int c = 0; c < nrhs; ++c) {
+        s += cs.active[c];
+        f += cs.active[c] && cs.flag[c];
+    }
     *cs.nactive = s;
+    *cs.nflag = f;
 }
 
 // ---------------------------------------------------------- workspace --
@@ -173,7 +205,7 @@ template <class T> static T *carve(char *&p, size_t count)
 
 static size_t cols_bytes(int nrhs)
 {
-    return (size_t)nrhs * (8 * 7 + 4 * 4 + 4) + (size_t)nrhs * DMAXB * 8 + 8 * 256 + 8192;
+    return (size_t)nrhs * (8 * 8 + 4 * 5 + 4) + (size_t)nrhs * DMAXB * 8 + 8 * 256 + 12288;
 }
 
 static void carve_cols(char *&p, int nrhs, Cols &cs)
@@ -191,6 +223,9 @@ static void carve_cols(char *&p, int nrhs, Cols &cs)
     cs.base = carve<int>(p, nrhs);
     cs.cnt = carve<unsigned int>(p, nrhs);
     cs.nactive = carve<int>(p, 1);
+    cs.rmax2 = carve<double>(p, nrhs);
+    cs.flag = carve<int>(p, nrhs);
+    cs.nflag = carve<int>(p, 1);
 }
 
 static afn_status get_work(Handle *h, int nrhs, Work &wk)
@@ -429,6 +464,160 @@ __global__ void scale_up_kernel(double *x, const float *x32, const double *rn, c
 
 static unsigned g1(int64_t tot) { return (unsigned)((tot + 255) / 256); }
 
+// AFN_REFINE=restart selects the earlier restarted refinement (comparison)
+static bool legacy_refinement()
+{
+    const char *e = getenv("AFN_REFINE");
+    return e && e[0] == 'r';
+}
+
+__global__ void init_rel_kernel(const double *bnorm, double *rel, int nrhs)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nrhs) rel[c] = bnorm[c] > 0.0 ? 1.0 : 0.0;
+}
+
+// ----------------------------------------------- reliable-update kernels --
+__global__ void ru_init_kernel(Cols cs, int nrhs, double delta)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    cs.cnt[c] = 0;
+    cs.tolabs[c] = delta;
+    cs.flag[c] = 0;
+    cs.base[c] = 0;
+    cs.iters[c] = 0;
+    cs.alpha[c] = cs.beta[c] = 0.0;
+    cs.active[c] = cs.bnorm[c] > 0.0 ? 1 : 0;
+    cs.conv[c] = cs.bnorm[c] > 0.0 ? 0 : 1;
+    cs.rmax2[c] = cs.bnorm[c] * cs.bnorm[c];
+}
+
+// x64 += dx32, dx32 = 0 on active columns
+__global__ void ru_accumulate_kernel(double *x, float *dx, const int *active, int64_t n, int nrhs)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nrhs) return;
+    int c = (int)(e / n);
+    if (!active[c]) return;
+    x[e] += (double)dx[e];
+    dx[e] = 0.f;
+}
+
+__global__ void to32_kernel(const double *a, float *b, int64_t count)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < count) b[e] = (float)a[e];
+}
+
+// after a replacement: cs.val = ||b - A x||^2 (FP64); test the true residual
+__global__ void ru_post_kernel(Cols cs, int nrhs, double tol, int maxit, double *relres)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    double bn = cs.bnorm[c];
+    double rel = bn > 0.0 ? sqrt(cs.val[c]) / bn : 0.0;
+    if (!cs.active[c]) return;
+    relres[c] = rel;
+    cs.flag[c] = 0;
+    cs.cnt[c] = 0;
+    if (rel <= tol) {
+        cs.active[c] = 0;
+        cs.conv[c] = 1;
+    } else if (cs.iters[c] >= maxit) {
+        cs.active[c] = 0;
+        cs.conv[c] = 0;
+    } else {
+        cs.rmax2[c] = cs.val[c];
+    }
+}
+
+static afn_status poll_both(const Cols &cs, int nrhs, cudaStream_t s, int *na, int *nf)
+{
+    count_active_kernel<<<1, 1, 0, s>>>(cs, nrhs);
+    int h[2];
+    AFN_CUDA(cudaMemcpyAsync(&h[0], cs.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AFN_CUDA(cudaMemcpyAsync(&h[1], cs.nflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AFN_CUDA(cudaStreamSynchronize(s));
+    *na = h[0];
+    *nf = h[1];
+    return AFN_OK;
+}
+
+// Mixed precision: one FP32 PCG sequence (FP32 matvec, apply and vectors,
+// FP64 dots and scalars) whose residual is replaced by the FP64 true residual
+// b - (K + mu I) x whenever the recursive residual has fallen by `delta`
+// since the last replacement ("reliable updates", Sleijpen & van der Vorst
+// 1996; van der Vorst & Ye 2000).  x is accumulated in FP64.  The search
+// direction is kept across replacements, so the Krylov sequence is not
+// restarted; convergence is declared only on the FP64 residual.
+static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int maxit,
+                                 double *drel, int *steps_out)
+{
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n, tot = n * nrhs;
+    const double delta = h->opt.inner_tol > 0 ? h->opt.inner_tol : 0.05;
+    const Cols &cs = wk.cs;
+    ru_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(cs, nrhs, delta);
+    AFN_CUDA(cudaMemsetAsync(wk.x, 0, sizeof(double) * tot, s));
+    AFN_CUDA(cudaMemsetAsync(wk.x32, 0, sizeof(float) * tot, s));
+    to32_kernel<<<g1(tot), 256, 0, s>>>(wk.b, wk.r32, tot);
+    AFN_TRY(apply32(h, wk.r32, nrhs, wk.z32, wk.tmp));
+    {
+        Scope sc(&h->prof, K_BLAS1);
+        launch_dot<float>(0, wk.r32, wk.z32, nullptr, nullptr, n, nrhs, M_RHO0, cs, maxit, s);
+        launch_pupdate<float>(wk.p32, wk.z32, n, nrhs, cs, 1, s);
+    }
+    const int every = std::max(1, h->opt.check_every);
+    int steps = 0;
+    for (int it = 0; it < maxit + every; ++it) {
+        AFN_TRY(mv32(h, wk.p32, nrhs, wk.q32, wk));
+        {
+            Scope sc(&h->prof, K_BLAS1);
+            launch_dot<float>(0, wk.p32, wk.q32, nullptr, nullptr, n, nrhs, M_ALPHA, cs, maxit, s);
+            launch_dot<float>(1, wk.r32, wk.q32, wk.x32, wk.p32, n, nrhs, M_RRU, cs, maxit, s);
+        }
+        if ((it + 1) % every == 0) {
+            int na = 0, nf = 0;
+            AFN_TRY(poll_both(cs, nrhs, s, &na, &nf));
+            if (na == 0) break;
+            if (nf > 0) {
+                // replacement for every active column: x += dx, r = b - (K + mu I) x
+                ru_accumulate_kernel<<<g1(tot), 256, 0, s>>>(wk.x, wk.x32, cs.active, n, nrhs);
+                AFN_TRY(mv64(h, wk.x, nrhs, wk.q, wk));
+                residual_kernel<<<g1(tot), 256, 0, s>>>(wk.b, wk.q, wk.r, n, nrhs);
+                launch_dot<double>(0, wk.r, wk.r, nullptr, nullptr, n, nrhs, M_STORE, cs, maxit, s);
+                ru_post_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(cs, nrhs, tol, maxit, drel);
+                to32_kernel<<<g1(tot), 256, 0, s>>>(wk.r, wk.r32, tot);
+                ++steps;
+                AFN_TRY(poll_both(cs, nrhs, s, &na, &nf));
+                if (log_on()) {
+                    std::vector<double> hr(nrhs);
+                    std::vector<int> hi(nrhs);
+                    cudaMemcpy(hr.data(), drel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost);
+                    cudaMemcpy(hi.data(), cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost);
+                    double mx = 0;
+                    int itmax = 0;
+                    for (int c = 0; c < nrhs; ++c) { mx = std::max(mx, hr[c]); itmax = std::max(itmax, hi[c]); }
+                    fprintf(stderr, "[afn] replacement %d: max rel. residual %.3e, iterations %d, active %d\n",
+                            steps, mx, itmax, na);
+                }
+                if (na == 0) break;
+            }
+        }
+        AFN_TRY(apply32(h, wk.r32, nrhs, wk.z32, wk.tmp));
+        {
+            Scope sc(&h->prof, K_BLAS1);
+            launch_dot<float>(0, wk.r32, wk.z32, nullptr, nullptr, n, nrhs, M_BETA, cs, maxit, s);
+            launch_pupdate<float>(wk.p32, wk.z32, n, nrhs, cs, 0, s);
+        }
+    }
+    *steps_out = steps;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
+    return AFN_OK;
+}
+
 afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, double *x_perm,
                      int32_t *iters, double *relres, int *outer, int *converged)
 {
@@ -468,6 +657,12 @@ afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, doub
         AFN_CUDA(cudaMemcpyAsync(x_perm, wk.x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
         AFN_CUDA(cudaMemcpyAsync(hrel.data(), drel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         if (iters) AFN_CUDA(cudaMemcpyAsync(iters, wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+    } else if (!legacy_refinement()) {
+        init_rel_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(wk.cs.bnorm, drel, nrhs);
+        AFN_TRY(mixed_reliable(h, wk, nrhs, tol, maxit, drel, &steps));
+        AFN_CUDA(cudaMemcpyAsync(x_perm, wk.x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+        AFN_CUDA(cudaMemcpyAsync(hrel.data(), drel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        if (iters) AFN_CUDA(cudaMemcpyAsync(iters, wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
     } else {
         const int max_outer = h->opt.max_outer > 0 ? h->opt.max_outer : 10;
         const double inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : 1e-4;
@@ -481,6 +676,17 @@ afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, doub
                                                               maxit * max_outer);
             int na = 0;
             AFN_TRY(poll_active(wk.cs_out, nrhs, s, &na));
+            if (log_on()) {
+                std::vector<double> hr(nrhs);
+                std::vector<int> hi(nrhs);
+                cudaMemcpy(hr.data(), drel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost);
+                cudaMemcpy(hi.data(), wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost);
+                double mx = 0;
+                int itmax = 0;
+                for (int c = 0; c < nrhs; ++c) { mx = std::max(mx, hr[c]); itmax = std::max(itmax, hi[c]); }
+                fprintf(stderr, "[afn] outer step %d: max rel. residual %.3e, inner iterations so far %d, active %d\n",
+                        step, mx, itmax, na);
+            }
             if (na == 0) break;
             ++steps;
             scale_down_kernel<<<g1(tot), 256, 0, s>>>(wk.r, wk.rn, wk.cs_out.active, wk.r32, wk.x32,

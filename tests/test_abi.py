@@ -72,4 +72,4 @@ def test_default_options():
     from paper_2304_05460_gb300 import afn
     o = afn.options()
     assert (o.precision, o.landmarks, o.rank_mode, o.max_iter, o.max_outer) == (0, 0, 0, 500, 10)
-    assert o.inner_tol == 1e-4 and o.fps_start == 0
+    assert o.inner_tol == 0.01 and o.fps_start == 0
