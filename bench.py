@@ -50,6 +50,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batched", type=int, default=512,
+                    help="systems of the batched workload (0 = skip)")
+    ap.add_argument("--fp64-sample", type=int, default=24,
+                    help="batched systems solved one at a time in plain FP64 for comparison")
+    ap.add_argument("--serving", type=int, default=64,
+                    help="requests of the serving stream (0 = skip)")
+    ap.add_argument("--serving-rate", type=float, default=0.0,
+                    help="Poisson arrival rate, requests/s (0 = all requests at t = 0)")
     return ap.parse_args()
 
 
@@ -172,6 +180,161 @@ def oracle_sample(n, nrhs, budget_s=20.0, iters_hint=None):
               "scaled to one build+solve of %d RHS = %.1f s" % (k, kc, k, nr, nrhs, it, nrhs,
                                                                  total))
     return nrhs / total, detail, cores, t
+
+
+# ---------------------------------------------------------------- batched --
+def run_batched(afn, count, fp64_sample, stream):
+    """The batched workload: `count` systems (n log-uniform in [256, 8192],
+    d in 2..16, N(0,I) points, Gaussian, l = median distance x log-uniform
+    [0.1, 10], mu log-uniform [1e-4, 1e-1], k = min(n/4, 1000), w = 32, 8 RHS
+    each), built and solved together (mixed precision, grouped kernels under
+    CUDA graphs), against the plain FP64 GPU path run one system at a time on
+    a seeded sample of the systems."""
+    import torch
+    from paper_2304_05460_gb300 import inputs
+    systems = inputs.batched_512(count=count)
+    args_ = [dict(points=torch.tensor(s.X, device="cuda"), kernel=s.kernel, l=s.l, mu=s.mu,
+                  k_max=s.k, fsai_nnz=s.w) for s in systems]
+    rhs = [torch.tensor(np.ascontiguousarray(s.B), device="cuda") for s in systems]
+    cols = sum(s.nrhs for s in systems)
+    opt = dict(seed=1004, max_iter=MAXIT, check_every=4)
+
+    def once():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = afn.afn_build_batched(args_, **opt)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        xs, info = afn.afn_solve_batched(b, rhs, TOL)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        afn.afn_batch_free(b)
+        return t1 - t0, t2 - t1, info
+
+    once()                                   # warm-up (graph capture, pool growth)
+    bt, st, info = once()
+    if info["converged"] != cols:
+        raise RuntimeError("batched: %d/%d columns reached tol" % (info["converged"], cols))
+    # kernel-pair evaluations of the FP32 matvec: per system and column group,
+    # n^2 pairs for every iteration in which one of its columns was active
+    pairs = 0.0
+    for s, its in zip(systems, info["iters"]):
+        for g in range(0, len(its), 8):
+            pairs += float(s.n) ** 2 * int(its[g:g + 8].max())
+    out = {"workload": "batched_512: %d systems, n log-uniform [256, 8192], d in 2..16, N(0,I), "
+                       "Gaussian, l = median dist x logU[0.1, 10], mu logU[1e-4, 1e-1], "
+                       "k = min(n/4, 1000), w = 32, 8 RHS, tol 1e-6" % count,
+           "systems": count, "columns": cols, "build_ms": bt * 1e3, "solve_ms": st * 1e3,
+           "solves_per_s": cols / (bt + st), "solve_only_solves_per_s": cols / st,
+           "iters_max": info["iters_max"], "graph_launches": info["graph_launches"],
+           "matvec_pairs_per_s": pairs / st}
+    if fp64_sample > 0:
+        g = np.random.Generator(np.random.PCG64(7))
+        pick = sorted(g.choice(count, size=min(fp64_sample, count), replace=False).tolist())
+        o64 = afn.options(precision=afn.PREC_FP64, seed=1004, max_iter=MAXIT, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c64 = 0
+        for i in pick:
+            h = afn.afn_build(args_[i]["points"], systems[i].kernel, systems[i].l, systems[i].mu,
+                              systems[i].k, systems[i].w, o64)
+            x, inf = afn.afn_solve(h, rhs[i], TOL)
+            c64 += int(inf["converged"])
+            afn.afn_free(h)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        n2 = sum(float(systems[i].n) ** 2 for i in pick)
+        n2_all = sum(float(s.n) ** 2 for s in systems)
+        # scale the sample's time by the workload's sum of n^2 (the matvec cost)
+        t_all = t64 * n2_all / n2
+        out["fp64_one_at_a_time"] = {
+            "solves_per_s": cols / t_all, "sample_systems": len(pick),
+            "sample_converged_columns": c64, "sample_s": t64,
+            "scaling": "sample time x sum(n^2) of all systems / sum(n^2) of the sample"}
+        out["speedup_vs_fp64"] = out["solves_per_s"] / out["fp64_one_at_a_time"]["solves_per_s"]
+    return out
+
+
+# ---------------------------------------------------------------- serving --
+def run_serving(afn, count, rate, fp64_sample):
+    """The serving workload: `count` requests of the Poisson stream (n
+    log-uniform in [1e3, 1e5], d in {3, 8, 16}, N(0,I) points, Gaussian or
+    Matern-3/2 50/50, l and mu drawn as in the batched workload, k =
+    min(n/4, 1000), w = 32, 1..16 RHS, tol 1e-6) replayed against the serving
+    loop; latency is submit -> result.  rate 0 submits every request at once
+    (saturation throughput).  The plain FP64 GPU path, one request at a time,
+    is timed on a seeded sample and scaled by sum(n^2)."""
+    import threading
+    import torch
+    from paper_2304_05460_gb300 import inputs
+    reqs = inputs.serving_stream(count=count, rate=rate if rate > 0 else 1.0)
+    systems = [inputs.serving_system(r) for r in reqs]
+    args_ = [dict(points=s.X, kernel=s.kernel, l=s.l, mu=s.mu, k_max=s.k, fsai_nnz=s.w)
+             for s in systems]
+    cols = sum(s.nrhs for s in systems)
+    srv = afn.Server(seed=1005, max_iter=MAXIT, build_threads=8)
+    # warm-up request (graph capture, pool growth), not counted
+    wid = srv.submit(args_[0], systems[0].B, TOL)
+    while not srv.poll(wait_ms=100):
+        pass
+    srv.result(wid)
+    ids = {}
+    t0 = time.perf_counter()
+
+    def feeder():
+        for i, r in enumerate(reqs):
+            if rate > 0:
+                dt = r["t"] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            ids[srv.submit(args_[i], systems[i].B, TOL)] = i
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    lat, conv, done = [], 0, 0
+    while done < count:
+        for rid in srv.poll(wait_ms=50):
+            x, info = srv.result(rid)
+            lat.append(info["latency_ms"])
+            conv += int(info["converged"])
+            done += 1
+    span = time.perf_counter() - t0
+    th.join()
+    st = srv.stats()
+    srv.close()
+    lat = np.sort(np.array(lat))
+    out = {"workload": "serving_stream: %d requests, n log-uniform [1e3, 1e5], d in {3,8,16}, "
+                       "N(0,I), Gaussian/Matern-3/2 50/50, l = median dist x logU[0.1, 10], "
+                       "mu logU[1e-4, 1e-1], k = min(n/4, 1000), w = 32, 1-16 RHS, tol 1e-6; "
+                       "arrivals: %s" % (count, "Poisson %.3g/s" % rate if rate > 0 else
+                                         "all at t = 0 (saturation)"),
+           "requests": count, "columns": cols, "converged_columns": conv, "makespan_s": span,
+           "requests_per_s": count / span, "solves_per_s": cols / span,
+           "latency_p50_ms": float(np.percentile(lat, 50)),
+           "latency_p99_ms": float(np.percentile(lat, 99)),
+           "peak_live": st["peak_live"], "graph_launches": st["graph_launches"],
+           "peak_reserved_gb": st["peak_reserved_bytes"] / 2**30}
+    if fp64_sample > 0:
+        g = np.random.Generator(np.random.PCG64(11))
+        pick = sorted(g.choice(count, size=min(fp64_sample, count), replace=False).tolist())
+        o64 = afn.options(precision=afn.PREC_FP64, seed=1005, max_iter=MAXIT)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for i in pick:
+            s = systems[i]
+            h = afn.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w, o64)
+            afn.afn_solve(h, s.B, TOL)
+            afn.afn_free(h)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t1
+        n2 = sum(float(systems[i].n) ** 2 for i in pick)
+        n2_all = sum(float(s.n) ** 2 for s in systems)
+        t_all = t64 * n2_all / n2
+        out["fp64_one_at_a_time"] = {"solves_per_s": cols / t_all, "requests_per_s": count / t_all,
+                                     "sample_requests": len(pick), "sample_s": t64,
+                                     "scaling": "sample time x sum(n^2) / sum(n^2) of the sample"}
+        out["speedup_vs_fp64"] = out["solves_per_s"] / out["fp64_one_at_a_time"]["solves_per_s"]
+    return out
 
 
 # ------------------------------------------------------------------- main --
@@ -319,6 +482,13 @@ def main():
                 "converged": int(info["converged"])}
         afn.afn_free(h)
 
+    batched = None
+    if rank == 0 and args.batched > 0:
+        batched = run_batched(afn, args.batched, args.fp64_sample, stream)
+    serving = None
+    if rank == 0 and args.serving > 0:
+        serving = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
@@ -328,7 +498,8 @@ def main():
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "kernels": kernels, "fp64_gpu": fp64,
-                "pcg_iters_max": iters_seen[-len(LS):] if iters_seen else None}
+                "pcg_iters_max": iters_seen[-len(LS):] if iters_seen else None,
+                "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -174,8 +174,12 @@ int64_t afn_launch_count(void);
  * q = (K + mu I) p, matrix-free (eq. (Problem); K_ij = K(x_i, x_j), Sec. 1).
  * points n x d row-major FP64; p, q n x nrhs column-major FP64.  precision:
  * AFN_PREC_FP64 computes in FP64; AFN_PREC_MIXED evaluates pairs in FP32
- * (points and p rounded to FP32, FP32 accumulation) and returns FP64.
+ * (points and p rounded to FP32, FP32 accumulation) and returns FP64;
+ * AFN_MATVEC_DF computes FP64-accurate values (kernel values to about 1e-14
+ * relative, double-float sums) on the FP32 pipes -- the kernel the mixed
+ * solves use for their FP64 residual b - (K + mu I) x.
  */
+#define AFN_MATVEC_DF 2
 afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
                              double mu, const double *p, int32_t nrhs, double *q,
                              int32_t precision, void *stream);
@@ -234,6 +238,142 @@ afn_status afn_knn_pattern(const double *xr, int64_t nr, int32_t d, int32_t w, i
 afn_status afn_rank_estimate(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
                              double mu, int32_t m, uint64_t seed, int32_t k_max, int64_t *k_out,
                              int64_t *r_out, int32_t *branch_out, void *stream);
+
+/* ---- many systems: batched solves -------------------------------------- */
+
+/* One independent system (K + mu I) a = b: the arguments of afn_build. */
+typedef struct {
+    const double *points;   /* n x d row-major FP64, host or device; read during the build */
+    int64_t n;
+    int32_t d;              /* 1..16 */
+    int32_t kernel;         /* afn_kernel */
+    double l, mu;           /* > 0 */
+    int32_t k_max;          /* landmarks (clamped to [0, n]; Alg. 4 when opt.rank_mode = 1) */
+    int32_t fsai_nnz;       /* w, nonzeros per row of G including the diagonal */
+} afn_system;
+
+typedef struct afn_batch afn_batch;
+
+typedef struct {
+    int32_t converged;      /* columns whose FP64 relative residual reached tol */
+    int32_t columns;        /* sum of nrhs */
+    int32_t graph_launches; /* CUDA graph launches (opt.check_every iterations each) */
+    int32_t iters_max;      /* largest per-column iteration count */
+    double solve_ms;        /* device time of the whole solve */
+} afn_batch_solve_info;
+
+/*
+ * Builds the AFN preconditioners (Alg. 2, the factors of afn_build) of nsys
+ * independent systems, several at a time on separate streams.  The batch
+ * runs the mixed-precision path only: opt->precision must be AFN_PREC_MIXED
+ * (AFN_ERR_ARG otherwise).  opt applies to every system (landmark policy,
+ * rank mode, seed, max_iter, inner_tol = delta of the reliable updates,
+ * check_every = PCG iterations per captured CUDA graph launch, stream for
+ * the solves: NULL creates a private stream).  AFN_BUILD_THREADS in the
+ * environment sets the number of building host threads (default 16).
+ * Errors: those of afn_build, with the failing system's index in the
+ * message; nothing is returned on failure.
+ */
+afn_status afn_build_batched(const afn_system *systems, int32_t nsys, const afn_options *opt,
+                             afn_batch **out);
+
+/*
+ * Solves every system of the batch for its nrhs[s] right-hand sides by the
+ * mixed-precision PCG of afn_solve (Alg. 5 with the apply of Alg. 3; FP32
+ * matvec/apply, FP64 scalars, FP64 residual replacements; stop when the FP64
+ * residual ||b - (K + mu I) x|| <= tol ||b||, at most max_iter iterations a
+ * column), all systems advancing together: each step of an iteration is one
+ * launch over the work of every system that still has an active column.
+ * rhs and x_out (host or device) hold the systems' n_s x nrhs[s] column-major
+ * blocks one after the other, in original point order; iters and relres (host,
+ * may be NULL) get sum(nrhs) entries in the same column order.  A system's
+ * result does not depend on the other systems of the batch.
+ * Returns AFN_ERR_NO_CONVERGE (x_out still written) when a column missed tol.
+ */
+afn_status afn_solve_batched(afn_batch *b, const double *rhs, const int32_t *nrhs, double tol,
+                             double *x_out, int32_t *iters, double *relres,
+                             afn_batch_solve_info *info);
+
+/* build information of system `system` of the batch (as afn_get_build_info) */
+afn_status afn_batch_build_info(const afn_batch *b, int32_t system, afn_build_info *info);
+/* host wall time of afn_build_batched, ms */
+double afn_batch_build_ms(const afn_batch *b);
+void afn_batch_free(afn_batch *b);    /* NULL-safe */
+
+/* ---- many systems: the serving loop ------------------------------------ */
+
+typedef struct afn_server afn_server;
+
+typedef struct {
+    int64_t memory_budget;  /* device bytes for admitted requests; 0 = half the free memory */
+    int32_t max_active;     /* admitted requests at once; 0 = no limit besides memory */
+    int32_t build_threads;  /* host threads (each with a stream) building requests; 0 = 8 */
+    afn_options opt;        /* solve options for every request; precision must be MIXED */
+} afn_server_config;
+
+typedef struct {
+    int32_t status;         /* afn_status of the request */
+    int32_t converged;      /* columns that reached tol */
+    int32_t nrhs;
+    int32_t pad_;
+    double queue_ms;        /* submit -> admitted (memory reserved) */
+    double build_ms;        /* preconditioner build (Alg. 2) on a build thread */
+    double wait_ms;         /* built -> joined the running group */
+    double solve_ms;        /* joined -> all columns stopped and result copied */
+    double latency_ms;      /* submit -> done */
+    int64_t device_bytes;   /* footprint reserved while admitted */
+} afn_request_info;
+
+typedef struct {
+    int64_t submitted, completed, queued;
+    int32_t active;         /* admitted, not finished */
+    int32_t peak_live;      /* most requests advanced by one graph launch */
+    int64_t graph_launches;
+    int64_t reserved_bytes, peak_reserved_bytes, budget_bytes;
+} afn_server_stats;
+
+/* defaults: budget 0 (half the free memory), no count limit, 8 build
+ * threads, afn_default_options with precision = AFN_PREC_MIXED */
+void afn_server_default_config(afn_server_config *cfg);
+
+/*
+ * Starts a serving loop on the current device: one scheduler thread and
+ * cfg->build_threads build threads.  Requests (afn_server_submit) are
+ * admitted in arrival order while the sum of the admitted requests' device
+ * footprints stays within the budget (a request larger than the budget runs
+ * when nothing else is admitted); each is built (Alg. 2) on a build thread's
+ * own stream, then joins the group of running PCG solves (the solve of
+ * afn_solve_batched, one launch per step for all requests) at its next graph
+ * launch and leaves it when its columns have stopped; its device memory is
+ * then released and its result kept in host memory until afn_server_result.
+ * A request's solution is the same whatever other requests run beside it.
+ * Errors: AFN_ERR_ARG (bad config), AFN_ERR_CUDA.
+ */
+afn_status afn_server_create(const afn_server_config *cfg, afn_server **out);
+
+/* Queues one system (points n x d row-major, rhs n x nrhs column-major,
+ * host or device; both are copied before the call returns).  *id identifies
+ * the request.  Errors: AFN_ERR_ARG (bad sizes, NaN/Inf). */
+afn_status afn_server_submit(afn_server *s, const afn_system *sys, const double *rhs,
+                             int32_t nrhs, double tol, int64_t *id);
+
+/* Up to max ids of finished requests (each reported once), waiting up to
+ * wait_ms for the first one; *count = number written. */
+afn_status afn_server_poll(afn_server *s, int64_t *ids, int32_t max, int32_t *count,
+                           int32_t wait_ms);
+
+/* Result of a finished request (x_out n x nrhs column-major, original point
+ * order, host or device; iters/relres host, nrhs entries; any may be NULL),
+ * then forgets the request.  Returns the request's status (AFN_ERR_BUSY when
+ * it has not finished, AFN_ERR_ARG for an unknown id). */
+afn_status afn_server_result(afn_server *s, int64_t id, double *x_out, int32_t *iters,
+                             double *relres, afn_request_info *info);
+
+afn_status afn_server_get_stats(afn_server *s, afn_server_stats *out);
+
+/* Stops the loop (requests not yet finished are dropped) and releases
+ * everything.  NULL-safe. */
+void afn_server_destroy(afn_server *s);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "AFN_OK", 1: "AFN_ERR_ARG", 2: "AFN_ERR_OOM", 3: "AFN_ERR_NOT
                 4: "AFN_ERR_NO_CONVERGE", 5: "AFN_ERR_TIMEOUT", 6: "AFN_ERR_CUDA", 7: "AFN_ERR_BUSY"}
 GAUSSIAN, MATERN32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+MATVEC_DF = 2              # afn_kernel_matvec only: FP64-accurate double-float
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
 
@@ -53,6 +54,17 @@ class afn_solve_info(C.Structure):
                 ("outer_steps", C.c_int32), ("converged", C.c_int32), ("solve_ms", C.c_double)]
 
 
+class afn_system(C.Structure):
+    _fields_ = [("points", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("kernel", C.c_int32),
+                ("l", C.c_double), ("mu", C.c_double), ("k_max", C.c_int32),
+                ("fsai_nnz", C.c_int32)]
+
+
+class afn_batch_solve_info(C.Structure):
+    _fields_ = [("converged", C.c_int32), ("columns", C.c_int32), ("graph_launches", C.c_int32),
+                ("iters_max", C.c_int32), ("solve_ms", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libafn.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
@@ -80,6 +92,13 @@ def _load():
                                     C.POINTER(i64), C.POINTER(i32), P]),
         "afn_launch_count": (i64, []),
         "afn_kernel_matvec_noalloc": (i32, [P, i64, i32, i32, dbl, dbl, P, i32, P, P]),
+        "afn_build_batched": (i32, [C.POINTER(afn_system), i32, C.POINTER(afn_options),
+                                    C.POINTER(P)]),
+        "afn_solve_batched": (i32, [P, P, C.POINTER(i32), dbl, P, P, P,
+                                    C.POINTER(afn_batch_solve_info)]),
+        "afn_batch_build_info": (i32, [P, i32, C.POINTER(afn_build_info)]),
+        "afn_batch_build_ms": (dbl, [P]),
+        "afn_batch_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -350,3 +369,218 @@ def afn_rank_estimate(points, kernel, l, mu, m=0, seed=0, k_max=4000, stream=Non
                                   C.c_uint64(int(seed) & (2**64 - 1)), int(k_max), C.byref(k),
                                   C.byref(r), C.byref(br), _stream_ptr(stream)))
     return int(k.value), int(r.value), int(br.value)
+
+
+# ----------------------------------------------------------------- batches --
+class Batch:
+    """Owns an ``afn_batch*`` (many systems built together)."""
+
+    def __init__(self, ptr, ns, ns_n):
+        self.ptr = ptr
+        self.nsys = ns
+        self.n = ns_n
+
+    def __del__(self):
+        try:
+            afn_batch_free(self)
+        except Exception:
+            pass
+
+
+def afn_build_batched(systems, opt: afn_options | None = None, **kw):
+    """Builds every system of ``systems`` (dicts with keys points, kernel, l,
+    mu, k_max, fsai_nnz) with the mixed-precision options ``opt``."""
+    if opt is None:
+        kw.setdefault("precision", PREC_MIXED)
+        opt = options(**kw)
+    ns = len(systems)
+    arr = (afn_system * ns)()
+    keep = []
+    for i, sy in enumerate(systems):
+        X = _f64_rowmajor(sy["points"])
+        px, kx = _ptr(X)
+        keep.append(kx)
+        arr[i] = afn_system(px, int(X.shape[0]), int(X.shape[1]), int(sy["kernel"]),
+                            float(sy["l"]), float(sy["mu"]), int(sy["k_max"]), int(sy["fsai_nnz"]))
+    b = C.c_void_p()
+    _check(_lib.afn_build_batched(arr, ns, C.byref(opt), C.byref(b)))
+    return Batch(b, ns, [int(sy["points"].shape[0]) for sy in systems])
+
+
+def afn_batch_free(b: Batch):
+    if b is not None and b.ptr:
+        _lib.afn_batch_free(b.ptr)
+        b.ptr = None
+
+
+def afn_batch_build_info(b: Batch, system: int) -> afn_build_info:
+    bi = afn_build_info()
+    _check(_lib.afn_batch_build_info(b.ptr, int(system), C.byref(bi)))
+    return bi
+
+
+def afn_batch_build_ms(b: Batch) -> float:
+    return float(_lib.afn_batch_build_ms(b.ptr))
+
+
+def afn_solve_batched(b: Batch, rhs, tol):
+    """Solves every system of the batch.  rhs: list of (n_s,) or (n_s, nrhs_s)
+    arrays (all numpy, or all torch tensors on one device).  Returns (xs, info)
+    with xs the list of solutions and info = dict(iters, relres (per system
+    arrays), converged, columns, graph_launches, iters_max, solve_ms, status)."""
+    if len(rhs) != b.nsys:
+        raise ValueError("expected %d right-hand-side blocks" % b.nsys)
+    cols = []
+    nr = []
+    for i, r in enumerate(rhs):
+        Bc, m = _f64_colmajor(r)
+        if int(Bc.shape[-1]) != b.n[i]:
+            raise ValueError("rhs %d has %d rows, system has n=%d" % (i, Bc.shape[-1], b.n[i]))
+        cols.append(Bc.reshape(-1))
+        nr.append(m)
+    if _is_torch(cols[0]):
+        import torch
+        flat = torch.cat(cols)
+        out = torch.empty_like(flat)
+    else:
+        flat = np.concatenate(cols)
+        out = np.empty_like(flat)
+    tot = sum(nr)
+    nrhs = (C.c_int32 * b.nsys)(*nr)
+    its = np.zeros(tot, dtype=np.int32)
+    rel = np.zeros(tot, dtype=np.float64)
+    info = afn_batch_solve_info()
+    pf, kf = _ptr(flat)
+    po, ko = _ptr(out)
+    st = _lib.afn_solve_batched(b.ptr, pf, nrhs, float(tol), po, _ptr(its)[0], _ptr(rel)[0],
+                                C.byref(info))
+    if st not in (AFN_OK, AFN_ERR_NO_CONVERGE):
+        _check(st)
+    xs, iters, relres = [], [], []
+    o = c = 0
+    for i in range(b.nsys):
+        n, m = b.n[i], nr[i]
+        blk = out[o:o + n * m].reshape(m, n)
+        xs.append(blk.T if m > 1 or (_is_torch(rhs[i]) and rhs[i].dim() == 2) or
+                  (not _is_torch(rhs[i]) and np.ndim(rhs[i]) == 2) else blk[0])
+        iters.append(its[c:c + m].astype(np.int64))
+        relres.append(rel[c:c + m].copy())
+        o += n * m
+        c += m
+    return xs, dict(iters=iters, relres=relres, converged=info.converged, columns=info.columns,
+                    graph_launches=info.graph_launches, iters_max=info.iters_max,
+                    solve_ms=info.solve_ms, status=st)
+
+
+# ----------------------------------------------------------------- serving --
+class afn_server_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("max_active", C.c_int32),
+                ("build_threads", C.c_int32), ("opt", afn_options)]
+
+
+class afn_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("converged", C.c_int32), ("nrhs", C.c_int32),
+                ("pad_", C.c_int32), ("queue_ms", C.c_double), ("build_ms", C.c_double),
+                ("wait_ms", C.c_double), ("solve_ms", C.c_double), ("latency_ms", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+class afn_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
+                ("active", C.c_int32), ("peak_live", C.c_int32), ("graph_launches", C.c_int64),
+                ("reserved_bytes", C.c_int64), ("peak_reserved_bytes", C.c_int64),
+                ("budget_bytes", C.c_int64)]
+
+
+def _bind_server():
+    P, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    sig = {
+        "afn_server_default_config": (None, [C.POINTER(afn_server_config)]),
+        "afn_server_create": (i32, [C.POINTER(afn_server_config), C.POINTER(P)]),
+        "afn_server_submit": (i32, [P, C.POINTER(afn_system), P, i32, dbl, C.POINTER(i64)]),
+        "afn_server_poll": (i32, [P, P, i32, C.POINTER(i32), i32]),
+        "afn_server_result": (i32, [P, i64, P, P, P, C.POINTER(afn_request_info)]),
+        "afn_server_get_stats": (i32, [P, C.POINTER(afn_server_stats)]),
+        "afn_server_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(_lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+_bind_server()
+
+
+class Server:
+    """A serving loop (``afn_server*``): submit systems at any time, poll for
+    finished ones, fetch results.  Options are those of ``options`` (mixed
+    precision); memory_budget (bytes, 0 = half the free device memory),
+    max_active and build_threads as in afn_server_config."""
+
+    def __init__(self, memory_budget=0, max_active=0, build_threads=8, **kw):
+        cfg = afn_server_config()
+        _lib.afn_server_default_config(C.byref(cfg))
+        cfg.memory_budget = int(memory_budget)
+        cfg.max_active = int(max_active)
+        cfg.build_threads = int(build_threads)
+        kw.setdefault("precision", PREC_MIXED)
+        cfg.opt = options(**kw)
+        self.ptr = C.c_void_p()
+        _check(_lib.afn_server_create(C.byref(cfg), C.byref(self.ptr)))
+        self._shape = {}
+
+    def submit(self, system, rhs, tol):
+        """system: dict(points, kernel, l, mu, k_max, fsai_nnz); rhs (n,) or
+        (n, nrhs).  Returns the request id."""
+        X = _f64_rowmajor(system["points"])
+        Bc, m = _f64_colmajor(rhs)
+        px, kx = _ptr(X)
+        pb, kb = _ptr(Bc)
+        sy = afn_system(px, int(X.shape[0]), int(X.shape[1]), int(system["kernel"]),
+                        float(system["l"]), float(system["mu"]), int(system["k_max"]),
+                        int(system["fsai_nnz"]))
+        rid = C.c_int64(0)
+        _check(_lib.afn_server_submit(self.ptr, C.byref(sy), pb, m, float(tol), C.byref(rid)))
+        self._shape[int(rid.value)] = (int(X.shape[0]), m, np.ndim(rhs) if not _is_torch(rhs)
+                                       else rhs.dim())
+        return int(rid.value)
+
+    def poll(self, max_ids=1024, wait_ms=0):
+        """Ids of requests finished since the last poll."""
+        ids = np.zeros(max(1, int(max_ids)), dtype=np.int64)
+        cnt = C.c_int32(0)
+        _check(_lib.afn_server_poll(self.ptr, _ptr(ids)[0], int(max_ids), C.byref(cnt),
+                                    int(wait_ms)))
+        return [int(v) for v in ids[: cnt.value]]
+
+    def result(self, rid):
+        """(x, info) of a finished request; x (n,) or (n, nrhs) float64 host."""
+        n, m, nd = self._shape.pop(int(rid))
+        x = np.zeros((m, n), dtype=np.float64)
+        its = np.zeros(m, dtype=np.int32)
+        rel = np.zeros(m, dtype=np.float64)
+        inf = afn_request_info()
+        st = _lib.afn_server_result(self.ptr, int(rid), _ptr(x)[0], _ptr(its)[0], _ptr(rel)[0],
+                                    C.byref(inf))
+        if st not in (AFN_OK, AFN_ERR_NO_CONVERGE):
+            _check(st)
+        info = {f: getattr(inf, f) for f, _ in afn_request_info._fields_ if f != "pad_"}
+        info.update(iters=its.astype(np.int64), relres=rel, status=st)
+        return (x.T if nd == 2 else x[0]), info
+
+    def stats(self):
+        s = afn_server_stats()
+        _check(_lib.afn_server_get_stats(self.ptr, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in afn_server_stats._fields_}
+
+    def close(self):
+        if self.ptr:
+            _lib.afn_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

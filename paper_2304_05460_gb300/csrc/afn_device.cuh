@@ -127,6 +127,12 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+__device__ __forceinline__ double warp_max_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
     uint64_t t;

@@ -32,14 +32,28 @@ afn_status cuda_fail(cudaError_t e, const char *what);
 enum : int { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_TIMEOUT = 2 };
 
 // -------------------------------------------------------- device buffers --
+// Device memory comes from a library-owned stream-ordered pool (one per
+// device).  A buffer is allocated on the calling thread's current library
+// stream (StreamGuard) and released on the same stream, so allocation and
+// release never synchronise the device: independent handles built on
+// separate streams run concurrently.  That stream must outlive the buffer.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t s = nullptr;
     afn_status alloc(size_t b);
     void release();
     ~DevBuf() { release(); }
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
+
+cudaStream_t current_stream();          // the calling thread's library stream
+struct StreamGuard {                    // sets it for the scope of an entry point
+    cudaStream_t prev;
+    explicit StreamGuard(cudaStream_t s);
+    ~StreamGuard();
+};
+void trim_pool();                       // return cached pool memory to the device
 
 // ------------------------------------------------------------- profiling --
 enum Kid { K_MATVEC32 = 0, K_MATVEC64, K_APPLY32, K_APPLY64, K_FPS, K_KNN, K_CHOL, K_TRSM,
@@ -82,6 +96,7 @@ struct Handle {
     DevBuf perm;      // int64 [n]
     DevBuf X64;       // double [n*d] permuted, row-major
     DevBuf X32;       // float  [n*dp] permuted, pre-scaled for the FP32 kernel
+    DevBuf Xdf;       // float2 [n*ds] permuted, pre-scaled double-float (mixed handles)
     // factors
     DevBuf L;         // double [k*k] row-major lower
     DevBuf Linv;      // double [k*k] row-major lower, L^{-1}
@@ -112,6 +127,21 @@ afn_status sync_status(Handle *h, const char *what);   // sync + read device sta
 // pointer kind
 bool is_device_ptr(const void *p);
 
+// the body of afn_build: validate, build on stream s, return a new handle
+afn_status create_handle(const double *points, int64_t n, int d, int kernel, double l, double mu,
+                         int k_max, int fsai_nnz, const afn_options &o, cudaStream_t s,
+                         Handle **out);
+// host or device input -> device pointer (copied into tmp when on the host)
+afn_status to_device(const double *src, int64_t count, DevBuf &tmp, const double **out,
+                     cudaStream_t s);
+afn_status check_finite(const double *a, int64_t count, int *dflag, cudaStream_t s,
+                        const char *what);
+// dst[c][i] = src[c][perm[i]] and its inverse, n x nrhs column-major
+void gather_cols(const double *src, const int64_t *perm, int64_t n, int nrhs, double *dst,
+                 cudaStream_t s);
+void scatter_cols(const double *src, const int64_t *perm, int64_t n, int nrhs, double *dst,
+                  cudaStream_t s);
+
 // kernel function constants for FP64/FP32 evaluation
 struct KParams {
     int kernel;       // 0 Gaussian, 1 Matern-3/2
@@ -128,6 +158,13 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
 size_t matvec32_scratch(int64_t n, int nrhs);
 int pad_dim(int d);
 int stored_dim32(int dp);
+// FP64-accurate q = (K + mu I) p on the FP32 pipes (double-float), from
+// prescaled double-float points (make_points_df, n x ds)
+afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
+                     int nrhs, double *q, void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t matvecdf_scratch(int64_t n, int nrhs);
+afn_status make_points_df(const double *X, int64_t n, int d, int ds, int kernel, double l,
+                          float2 *Xd, cudaStream_t s);
 // prescaled FP32 copy of FP64 points (n x d -> n x dp)
 afn_status make_points32(const double *X, int64_t n, int d, int dp, int kernel, double l,
                          float *Xs, cudaStream_t s);
@@ -177,7 +214,17 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
                      const T *r, int nrhs, T *s, T *tmp, cudaStream_t st);
 size_t apply_tmp_elems(const Handle *h, int nrhs);
 
-// ---- blas1.cu (PCG vector kernels; FP64 scalars per column)
+// ---- grouped steps (many systems per launch; group.cuh describes the group)
+struct GDev;
+afn_status group_matvec32(const GDev *gd, cudaStream_t s);
+afn_status group_matvec64(const GDev *gd, cudaStream_t s);
+afn_status group_apply(const GDev *gd, cudaStream_t s);
+int group_mv32_rows();      // rows per tile of the grouped FP32 matvec
+int group_mv64_rows();      // rows per tile of the grouped FP64 matvec
+int group_block_rows();     // rows per block of the grouped dense products
+int group_sparse_rows();    // rows per block of the grouped sparse products
+
+// ---- solve.cu (PCG vector kernels; FP64 scalars per column)
 afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, double *x_perm,
                      int32_t *iters, double *relres, int *outer, int *converged);
 

@@ -12,6 +12,8 @@
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
+#include "gemm_tile.cuh"
+#include "group.cuh"
 
 namespace afn {
 
@@ -257,18 +259,11 @@ __global__ void rm_to_cm_kernel(const T *__restrict__ in, int64_t rows, int cols
 }
 
 // --------------------------------------------------------------------------
-// Tiled product for many right-hand sides (NC in {8, 16, 32}):
-//   TA == false: out = A X,   A row-major M x K        (A[i,p] = A[i*lda+p])
-//   TA == true : out = A^T X, A row-major K x M        (A^T[i,p] = A[p*lda+i])
-// X is K x NC column-major (ldx).  A CTA owns GM = 128 output rows and one
-// K-chunk; 256 threads each hold an RM x 4 register tile.  TRI = 1 keeps only
-// p <= i (lower), TRI = 2 only p >= i (upper).  With one K-chunk the epilogue
-// writes O = beta Y + alpha acc directly; otherwise per-chunk partials go to
-// `part` (chunk-major) and gemm_finish sums them in order.
+// Tiled product for many right-hand sides (NC in {8, 16, 32}), see gemm_rows:
+// a CTA owns GM = 128 output rows and one K-chunk.  With one K-chunk the
+// epilogue writes O = beta Y + alpha acc directly; otherwise per-chunk
+// partials go to `part` (chunk-major) and gemm_finish sums them in order.
 // --------------------------------------------------------------------------
-static constexpr int GM = 128;     // output rows per CTA
-static constexpr int GK = 16;      // K per shared-memory stage
-
 template <class T, int NC, bool TA, int TRI>
 __global__ void __launch_bounds__(256) gemm_kernel(const T *__restrict__ A, int64_t lda, int64_t M,
                                                    int64_t K, const T *__restrict__ X,
@@ -277,81 +272,16 @@ __global__ void __launch_bounds__(256) gemm_kernel(const T *__restrict__ A, int6
                                                    int64_t ldy, T *__restrict__ O, int64_t ldo,
                                                    T alpha, T beta)
 {
-    constexpr int TC = NC / 4;             // threads along columns
-    constexpr int TR = 256 / TC;           // threads along rows
-    constexpr int RM = GM / TR;            // rows per thread
+    constexpr int TC = GemmShape<NC>::TC;
+    constexpr int RM = GemmShape<NC>::RM;
     __shared__ __align__(16) T as[GK][GM + 4];
     __shared__ __align__(16) T xs[GK][NC + 4];
     const int tc = threadIdx.x % TC, tr = threadIdx.x / TC;
     const int64_t r0 = (int64_t)blockIdx.x * GM;
-    int64_t k0 = (int64_t)blockIdx.y * chunk;
-    int64_t k1 = min(K, k0 + chunk);
-    if (TRI == 1) k1 = min(k1, r0 + GM);          // p <= i <= r0 + GM - 1
-    if (TRI == 2) k0 = max(k0, r0);               // p >= i >= r0
+    const int64_t k0 = (int64_t)blockIdx.y * chunk;
+    const int64_t k1 = min(K, k0 + chunk);
     T acc[RM][4];
-#pragma unroll
-    for (int a = 0; a < RM; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-    // register prefetch: the next stage's global loads are issued before the
-    // current stage is computed
-    constexpr int LA = GM * GK / 256;                        // A elements per thread
-    constexpr int LX = (GK * NC + 255) / 256;                // X elements per thread
-    T ra[LA], rx[LX];
-    auto fetch = [&](int64_t kk0) {
-#pragma unroll
-        for (int u = 0; u < LA; ++u) {
-            int e = threadIdx.x + u * 256;
-            int r, q;
-            if (TA) { q = e / GM; r = e % GM; }       // coalesced along i
-            else { r = e / GK; q = e % GK; }          // coalesced along p
-            int64_t gi = r0 + r, gp = kk0 + q;
-            T v = 0;
-            if (gi < M && gp < k1) {
-                bool keep = (TRI == 0) || (TRI == 1 && gp <= gi) || (TRI == 2 && gp >= gi);
-                if (keep) v = TA ? A[gp * lda + gi] : A[gi * lda + gp];
-            }
-            ra[u] = v;
-        }
-#pragma unroll
-        for (int u = 0; u < LX; ++u) {
-            int e = threadIdx.x + u * 256;
-            int c = e / GK, q = e % GK;
-            int64_t gp = kk0 + q;
-            rx[u] = (e < GK * NC && gp < k1) ? X[c * ldx + gp] : (T)0;
-        }
-    };
-    if (k0 < k1) fetch(k0);
-    for (int64_t kk0 = k0; kk0 < k1; kk0 += GK) {
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < LA; ++u) {
-            int e = threadIdx.x + u * 256;
-            int r, q;
-            if (TA) { q = e / GM; r = e % GM; }
-            else { r = e / GK; q = e % GK; }
-            as[q][r] = ra[u];
-        }
-#pragma unroll
-        for (int u = 0; u < LX; ++u) {
-            int e = threadIdx.x + u * 256;
-            if (e < GK * NC) xs[e % GK][e / GK] = rx[u];
-        }
-        __syncthreads();
-        if (kk0 + GK < k1) fetch(kk0 + GK);
-#pragma unroll
-        for (int q = 0; q < GK; ++q) {
-            T av[RM], xv[4];
-#pragma unroll
-            for (int a = 0; a < RM; ++a) av[a] = as[q][tr * RM + a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) xv[b] = xs[q][tc * 4 + b];
-#pragma unroll
-            for (int a = 0; a < RM; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * xv[b];
-        }
-    }
+    gemm_rows<T, NC, TA, TRI>(A, lda, M, r0, k0, k1, X, ldx, as, xs, acc);
 #pragma unroll
     for (int a = 0; a < RM; ++a) {
         int64_t gi = r0 + tr * RM + a;
@@ -572,5 +502,151 @@ template afn_status afn_apply<float>(const Handle *, const float *, const float 
 template afn_status afn_apply<double>(const Handle *, const double *, const double *,
                                       const double *, const double *, const double *, int,
                                       double *, double *, cudaStream_t);
+
+// ------------------------------------------------------- grouped apply --
+// The apply of every member system of a group, one persistent launch per
+// step of Alg. 3 (the same W-form as afn_apply), each over its own tile list:
+//   zp  = L^{-1} r1                       (128-row blocks of k)
+//   t   = r2 - W^T zp                     (128-row blocks of nr; t row-major)
+//   y   = G t,  s2 = G^T y                (32-row blocks of nr, 8 lanes a row)
+//   part_q = W[:, chunk q] s2[chunk q]    (128-row blocks of k x chunks)
+//   u   = zp - sum_q part_q               (128-row blocks of k, chunks in order)
+//   s1  = L^{-T} u
+// r and s are the system's r32 and z32 (n x C column-major); a column group
+// of 8 columns is the unit of every tile.
+
+__device__ __forceinline__ bool group_live_ap(const GSys &S, int cg)
+{
+    const int c0 = cg * GC, c1 = min(S.nrhs, c0 + GC);
+    for (int c = c0; c < c1; ++c)
+        if (S.cs[c].active) return true;
+    return false;
+}
+
+static constexpr int GAP_TR = GemmShape<GC>::TR;   // threads along rows (128)
+
+// MODE 0: zp = L^{-1} r1; 1: t = r2 - W^T zp; 2: W s2 partials; 3: s1 = L^{-T} u
+template <int MODE>
+__global__ void __launch_bounds__(256) gap_gemm_kernel(const GDev *__restrict__ gd)
+{
+    __shared__ __align__(16) float as[GK][GM + 4];
+    __shared__ __align__(16) float xs[GK][GC + 4];
+    const GTile *tiles = MODE == 1 ? gd->wb : (MODE == 2 ? gd->wtb : gd->kb);
+    const int nt = MODE == 1 ? gd->nwb : (MODE == 2 ? gd->nwtb : gd->nkb);
+    const int tc = threadIdx.x % 2, tr = threadIdx.x / 2;   // GemmShape<8>: TC = 2, RM = 1
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const GTile tl = tiles[ti];
+        const GSys &S = gd->sys[tl.sys];
+        if (!group_live_ap(S, tl.cg)) continue;
+        const int64_t n = S.n, k = S.k, nr = S.nr;
+        const int C = S.ncg * GC;
+        float acc[1][4];
+        if (MODE == 0)
+            gemm_rows<float, GC, false, 1>(S.Linv, k, k, tl.r0, 0, k, S.r32 + (int64_t)tl.cg * GC * n, n,
+                                           as, xs, acc);
+        else if (MODE == 1)
+            gemm_rows<float, GC, false, 0>(S.Wt, k, nr, tl.r0, 0, k, S.zp + (int64_t)tl.cg * GC * k, k,
+                                           as, xs, acc);
+        else if (MODE == 2)
+            gemm_rows<float, GC, true, 0>(S.Wt, k, k, tl.r0, (int64_t)tl.aux * S.kch,
+                                          min(nr, (int64_t)(tl.aux + 1) * S.kch),
+                                          S.z32 + (int64_t)tl.cg * GC * n + k, n, as, xs, acc);
+        else
+            gemm_rows<float, GC, false, 2>(S.LinvT, k, k, tl.r0, 0, k, S.u + (int64_t)tl.cg * GC * k, k,
+                                           as, xs, acc);
+        const int64_t gi = tl.r0 + tr;
+        const int64_t M = MODE == 1 ? nr : k;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = tl.cg * GC + tc * 4 + b;
+            const float v = acc[0][b];
+            if (MODE == 0) S.zp[(int64_t)c * k + gi] = v;
+            else if (MODE == 1)
+                S.t[((int64_t)tl.cg * nr + gi) * GC + tc * 4 + b] = S.r32[(int64_t)c * n + k + gi] - v;
+            else if (MODE == 2) S.part[((int64_t)tl.aux * C + c) * k + gi] = v;
+            else S.z32[(int64_t)c * n + gi] = v;
+        }
+    }
+}
+
+// u = zp - sum_q part_q, chunks in order
+__global__ void __launch_bounds__(256) gap_finish_kernel(const GDev *__restrict__ gd)
+{
+    const int nt = gd->nkb;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const GTile tl = gd->kb[ti];
+        const GSys &S = gd->sys[tl.sys];
+        if (!group_live_ap(S, tl.cg)) continue;
+        const int64_t k = S.k;
+        const int C = S.ncg * GC;
+        for (int e = threadIdx.x; e < GM * GC; e += 256) {
+            const int64_t i = tl.r0 + e % GM;
+            const int c = tl.cg * GC + e / GM;
+            if (i >= k) continue;
+            float v = S.zp[(int64_t)c * k + i];
+            for (int q = 0; q < S.js; ++q) v -= S.part[((int64_t)q * C + c) * k + i];
+            S.u[(int64_t)c * k + i] = v;
+        }
+    }
+}
+
+// MODE 0: y = G t (ELL rows); 1: s2 = G^T y (CSR of G^T).  8 lanes per row,
+// lane = column of the group; t and y are row-major [nr][8].
+template <int MODE>
+__global__ void __launch_bounds__(256) gap_sparse_kernel(const GDev *__restrict__ gd)
+{
+    const int nt = gd->nsp;
+    const int c = threadIdx.x % GC;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const GTile tl = gd->sp[ti];
+        const GSys &S = gd->sys[tl.sys];
+        if (!group_live_ap(S, tl.cg)) continue;
+        const int64_t nr = S.nr;
+        const int64_t i = tl.r0 + threadIdx.x / GC;
+        if (i >= nr) continue;
+        float acc = 0.f;
+        if (MODE == 0) {
+            const float *t = S.t + (int64_t)tl.cg * nr * GC;
+            const int w = S.w;
+            for (int p = 0; p < w; ++p) {
+                const int32_t j = S.pat[i * w + p];
+                if (j < 0) break;
+                acc += S.G[i * w + p] * t[(int64_t)j * GC + c];
+            }
+            S.y[((int64_t)tl.cg * nr + i) * GC + c] = acc;
+        } else {
+            const float *y = S.y + (int64_t)tl.cg * nr * GC;
+            const int32_t q0 = S.gptr[i], q1 = S.gptr[i + 1];
+            for (int32_t q = q0; q < q1; ++q) acc += S.G[S.gslot[q]] * y[(int64_t)S.grow[q] * GC + c];
+            S.z32[((int64_t)tl.cg * GC + c) * S.n + S.k + i] = acc;
+        }
+    }
+}
+
+static int sm_count()
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+int group_sparse_rows() { return 256 / GC; }
+int group_block_rows() { return GM; }
+
+afn_status group_apply(const GDev *gd, cudaStream_t s)
+{
+    const int g = sm_count() * 4;
+    gap_gemm_kernel<0><<<g, 256, 0, s>>>(gd);
+    gap_gemm_kernel<1><<<g, 256, 0, s>>>(gd);
+    gap_sparse_kernel<0><<<g, 256, 0, s>>>(gd);
+    gap_sparse_kernel<1><<<g, 256, 0, s>>>(gd);
+    gap_gemm_kernel<2><<<g, 256, 0, s>>>(gd);
+    gap_finish_kernel<<<g, 256, 0, s>>>(gd);
+    gap_gemm_kernel<3><<<g, 256, 0, s>>>(gd);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped apply launch");
+}
 
 }  // namespace afn

@@ -2,6 +2,7 @@
 // argument checks, host/device staging, the build orchestration of Alg. 2,
 // the solve (Alg. 5 with the apply of Alg. 3) and introspection.
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,11 +33,56 @@ afn_status cuda_fail(cudaError_t e, const char *what)
     return AFN_ERR_CUDA;
 }
 
+static thread_local cudaStream_t tl_stream = nullptr;
+
+cudaStream_t current_stream() { return tl_stream; }
+StreamGuard::StreamGuard(cudaStream_t s) : prev(tl_stream) { tl_stream = s; }
+StreamGuard::~StreamGuard() { tl_stream = prev; }
+
+// one pool per device; up to 8 GiB of released memory stays cached in it
+static constexpr int MAX_DEV = 64;
+static cudaMemPool_t g_pool[MAX_DEV];
+static std::once_flag g_pool_once[MAX_DEV];
+
+static cudaMemPool_t pool_for(int dev)
+{
+    if (dev < 0 || dev >= MAX_DEV) return nullptr;
+    std::call_once(g_pool_once[dev], [dev]() {
+        cudaMemPoolProps pr;
+        memset(&pr, 0, sizeof(pr));
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        if (cudaMemPoolCreate(&mp, &pr) != cudaSuccess) {
+            cudaGetLastError();
+            mp = nullptr;
+        } else {
+            uint64_t keep = 8ull << 30;
+            cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        g_pool[dev] = mp;
+    });
+    return g_pool[dev];
+}
+
+void trim_pool()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t mp = pool_for(dev);
+    if (mp) cudaMemPoolTrimTo(mp, 0);
+}
+
 afn_status DevBuf::alloc(size_t b)
 {
     release();
     if (b == 0) return AFN_OK;
-    cudaError_t e = cudaMalloc(&p, b);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t mp = pool_for(dev);
+    s = tl_stream;
+    cudaError_t e = mp ? cudaMallocFromPoolAsync(&p, b, mp, s) : cudaMallocAsync(&p, b, s);
     if (e != cudaSuccess) {
         p = nullptr;
         cudaGetLastError();
@@ -49,7 +95,7 @@ afn_status DevBuf::alloc(size_t b)
 
 void DevBuf::release()
 {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
 }
@@ -109,7 +155,7 @@ Profiler::~Profiler()
 
 int64_t Handle::device_bytes() const
 {
-    const DevBuf *b[] = {&perm, &X64, &X32, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32,
+    const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32,
                          &pat, &G, &G32, &gt_ptr, &gt_row, &gt_slot, &status, &ws};
     int64_t s = 0;
     for (auto x : b) s += (int64_t)x->bytes;
@@ -132,7 +178,8 @@ afn_status sync_status(Handle *h, const char *what)
 {
     AFN_CUDA(cudaStreamSynchronize(h->stream));
     int st = 0;
-    AFN_CUDA(cudaMemcpy(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    AFN_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AFN_CUDA(cudaStreamSynchronize(h->stream));
     if (st == DEV_NOT_SPD) {
         set_error("%s: matrix not numerically SPD", what);
         return AFN_ERR_NOT_SPD;
@@ -170,7 +217,7 @@ __global__ void finite_kernel(const double *a, int64_t n, int *flag)
     if (i < n && !isfinite(a[i])) atomicExch(flag, 1);
 }
 
-static afn_status check_finite(const double *a, int64_t count, int *dflag, cudaStream_t s,
+afn_status check_finite(const double *a, int64_t count, int *dflag, cudaStream_t s,
                                const char *what)
 {
     if (count <= 0) return AFN_OK;
@@ -187,7 +234,7 @@ static afn_status check_finite(const double *a, int64_t count, int *dflag, cudaS
 }
 
 // stage a caller buffer (host or device) as a device buffer
-static afn_status to_device(const double *src, int64_t count, DevBuf &tmp, const double **out,
+afn_status to_device(const double *src, int64_t count, DevBuf &tmp, const double **out,
                             cudaStream_t s)
 {
     if (is_device_ptr(src)) {
@@ -217,6 +264,22 @@ __global__ void scatter_cols_kernel(const double *__restrict__ src, const int64_
     if (e >= n * nrhs) return;
     int64_t c = e / n, p = e % n;
     dst[c * n + perm[p]] = src[e];
+}
+
+void gather_cols(const double *src, const int64_t *perm, int64_t n, int nrhs, double *dst,
+                 cudaStream_t s)
+{
+    int64_t tot = n * nrhs;
+    if (tot > 0)
+        gather_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, perm, n, nrhs, dst);
+}
+
+void scatter_cols(const double *src, const int64_t *perm, int64_t n, int nrhs, double *dst,
+                  cudaStream_t s)
+{
+    int64_t tot = n * nrhs;
+    if (tot > 0)
+        scatter_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, perm, n, nrhs, dst);
 }
 
 // ------------------------------------------------------------------- build --
@@ -264,7 +327,8 @@ static afn_status build_impl(Handle *h, const double *points)
                 DevBuf ds;
                 AFN_TRY(ds.alloc(sizeof(int64_t)));
                 AFN_TRY(centroid_start(X0, n, d, ds.as<int64_t>(), s));
-                AFN_CUDA(cudaMemcpy(&start, ds.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
+                AFN_CUDA(cudaMemcpyAsync(&start, ds.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                AFN_CUDA(cudaStreamSynchronize(s));
             }
             if (start >= n) {
                 set_error("fps_start %lld out of range", (long long)start);
@@ -290,6 +354,8 @@ static afn_status build_impl(Handle *h, const double *points)
         int ds = stored_dim32(h->dp);
         AFN_TRY(h->X32.alloc(sizeof(float) * (size_t)(n * ds)));
         AFN_TRY(make_points32(h->X64.as<double>(), n, d, h->dp, h->kernel, h->l, h->X32.as<float>(), s));
+        AFN_TRY(h->Xdf.alloc(sizeof(float2) * (size_t)(n * ds)));
+        AFN_TRY(make_points_df(h->X64.as<double>(), n, d, ds, h->kernel, h->l, h->Xdf.as<float2>(), s));
     }
 
     if (k > 0) {
@@ -359,6 +425,58 @@ static afn_status build_impl(Handle *h, const double *points)
     return AFN_OK;
 }
 
+// Validates the arguments, builds the AFN factors on stream s and returns a
+// new handle (the body of afn_build; also used by the batched build).
+afn_status create_handle(const double *points, int64_t n, int d, int kernel, double l, double mu,
+                         int k_max, int fsai_nnz, const afn_options &o, cudaStream_t s,
+                         Handle **out)
+{
+    *out = nullptr;
+    if (!points || n < 1 || d < 1 || d > 16 || (kernel != 0 && kernel != 1) || !(l > 0) ||
+        !std::isfinite(l) || !(mu > 0) || !std::isfinite(mu) || k_max < 0 || fsai_nnz < 1) {
+        set_error("afn_build: invalid argument (n=%lld d=%d kernel=%d l=%g mu=%g k_max=%d w=%d)",
+                  (long long)n, d, kernel, l, mu, k_max, fsai_nnz);
+        return AFN_ERR_ARG;
+    }
+    if (o.precision != 0 && o.precision != 1) { set_error("bad precision"); return AFN_ERR_ARG; }
+    Handle *h = new Handle();
+    cudaGetDevice(&h->dev);
+    h->opt = o;
+    h->stream = s;
+    h->prof.on = o.profile != 0;
+    h->prof.s = h->stream;
+    StreamGuard sg(h->stream);
+    h->n = n;
+    h->d = d;
+    h->kernel = kernel;
+    h->l = l;
+    h->mu = mu;
+    h->precision = o.precision;
+    h->k = std::min<int64_t>(k_max, n);
+    h->w_req = fsai_nnz;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, h->stream);
+    afn_status st = build_impl(h, points);
+    if (st == AFN_OK) {
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->build_ms = ms;
+        h->prof.flush();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != AFN_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AFN_OK;
+}
+
 }  // namespace afn
 
 using namespace afn;
@@ -368,6 +486,10 @@ using namespace afn;
 // cudaLaunchCooperativeKernel; the link step wraps both (-Wl,--wrap) so that
 // the library can report how many kernels it launched.
 static std::atomic<long long> g_launches{0};
+
+namespace afn {
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace afn
 
 extern "C" cudaError_t __real___cudaLaunchKernel(cudaKernel_t f, dim3 g, dim3 b, void **a,
                                                  size_t sm, cudaStream_t s);
@@ -418,51 +540,14 @@ afn_status afn_build(const double *points, int64_t n, int32_t d, int32_t kernel,
     g_err[0] = 0;
     if (!out) { set_error("out is NULL"); return AFN_ERR_ARG; }
     *out = nullptr;
-    if (!points || n < 1 || d < 1 || d > 16 || (kernel != 0 && kernel != 1) || !(l > 0) ||
-        !std::isfinite(l) || !(mu > 0) || !std::isfinite(mu) || k_max < 0 || fsai_nnz < 1) {
-        set_error("afn_build: invalid argument (n=%lld d=%d kernel=%d l=%g mu=%g k_max=%d w=%d)",
-                  (long long)n, d, kernel, l, mu, k_max, fsai_nnz);
-        return AFN_ERR_ARG;
-    }
     afn_options o;
     afn_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != 0 && o.precision != 1) { set_error("bad precision"); return AFN_ERR_ARG; }
-    Handle *h = new Handle();
-    cudaGetDevice(&h->dev);
-    h->opt = o;
-    h->stream = static_cast<cudaStream_t>(o.stream);
-    h->prof.on = o.profile != 0;
-    h->prof.s = h->stream;
-    h->n = n;
-    h->d = d;
-    h->kernel = kernel;
-    h->l = l;
-    h->mu = mu;
-    h->precision = o.precision;
-    h->k = std::min<int64_t>(k_max, n);
-    h->w_req = fsai_nnz;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, h->stream);
-    afn_status st = build_impl(h, points);
-    if (st == AFN_OK) {
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        h->build_ms = ms;
-        h->prof.flush();
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != AFN_OK) {
-        delete h;
-        return st;
-    }
-    *out = reinterpret_cast<afn_handle *>(h);
-    return AFN_OK;
+    Handle *h = nullptr;
+    afn_status st = create_handle(points, n, d, kernel, l, mu, k_max, fsai_nnz, o,
+                                  static_cast<cudaStream_t>(o.stream), &h);
+    if (st == AFN_OK) *out = reinterpret_cast<afn_handle *>(h);
+    return st;
 }
 
 void afn_free(afn_handle *hh)
@@ -484,6 +569,7 @@ afn_status afn_solve(afn_handle *hh, const double *rhs, int32_t nrhs, double tol
         return AFN_ERR_ARG;
     }
     cudaStream_t s = h->stream;
+    StreamGuard sg(s);
     const int64_t n = h->n, tot = n * nrhs;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -600,6 +686,7 @@ afn_status afn_get_W(const afn_handle *hh, double *Wt)
     int64_t cnt = h->nr * h->k;
     if (cnt == 0) return AFN_OK;
     if (h->precision != AFN_PREC_MIXED) return copy_out(Wt, h->Wt.p, sizeof(double) * cnt);
+    StreamGuard sg(h->stream);
     DevBuf tmp;
     AFN_TRY(tmp.alloc(sizeof(double) * cnt));
     AFN_TRY(convert32to64(h->Wt32.as<float>(), tmp.as<double>(), cnt, h->stream));
@@ -616,6 +703,7 @@ afn_status afn_apply_precond(afn_handle *hh, const double *r, int32_t nrhs, doub
         return AFN_ERR_ARG;
     }
     cudaStream_t s = h->stream;
+    StreamGuard sg(s);
     int64_t tot = h->n * nrhs;
     DevBuf rin, sd, tmp;
     const double *R = nullptr;
@@ -663,6 +751,7 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
         return AFN_ERR_ARG;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StreamGuard sg(s);
     int64_t tot = n * nrhs;
     DevBuf xin, pin, qd, scratch;
     const double *X = nullptr, *P = nullptr;
@@ -679,6 +768,15 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
         AFN_TRY(scratch.alloc(sb));
         KParams kp{kernel, l, mu};
         AFN_TRY(matvec64(X, n, d, kp, P, nrhs, Q, scratch.p, sb, s));
+    } else if (precision == AFN_MATVEC_DF) {
+        const int ds = stored_dim32(pad_dim(d));
+        DevBuf xd;
+        AFN_TRY(xd.alloc(sizeof(float2) * n * ds));
+        AFN_TRY(make_points_df(X, n, d, ds, kernel, l, xd.as<float2>(), s));
+        size_t sb = matvecdf_scratch(n, nrhs);
+        AFN_TRY(scratch.alloc(sb));
+        AFN_TRY(matvec_df(xd.as<float2>(), n, ds, kernel, mu, P, nrhs, Q, scratch.p, sb, s));
+        AFN_CUDA(cudaStreamSynchronize(s));
     } else {
         int dp = pad_dim(d);
         int ds = stored_dim32(dp);
@@ -710,6 +808,7 @@ afn_status afn_fps(const double *points, int64_t n, int32_t d, int64_t k, int64_
     }
     if (k == 0) return AFN_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StreamGuard sg(s);
     DevBuf xin, id, stt;
     const double *X = nullptr;
     AFN_TRY(to_device(points, n * d, xin, &X, s));
@@ -719,7 +818,8 @@ afn_status afn_fps(const double *points, int64_t n, int32_t d, int64_t k, int64_
         DevBuf ds;
         AFN_TRY(ds.alloc(sizeof(int64_t)));
         AFN_TRY(centroid_start(X, n, d, ds.as<int64_t>(), s));
-        AFN_CUDA(cudaMemcpy(&start, ds.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        AFN_CUDA(cudaMemcpyAsync(&start, ds.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AFN_CUDA(cudaStreamSynchronize(s));
     }
     AFN_TRY(fps_run(X, n, d, k, start, id.as<int64_t>(), stt.as<int>(), s));
     return copy_out(idx, id.p, sizeof(int64_t) * k);
@@ -734,6 +834,7 @@ afn_status afn_knn_pattern(const double *xr, int64_t nr, int32_t d, int32_t w, i
         return AFN_ERR_ARG;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StreamGuard sg(s);
     DevBuf xin, pd;
     const double *X = nullptr;
     AFN_TRY(to_device(xr, nr * d, xin, &X, s));
@@ -754,6 +855,7 @@ afn_status afn_rank_estimate(const double *points, int64_t n, int32_t d, int32_t
         return AFN_ERR_ARG;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StreamGuard sg(s);
     DevBuf xin, stt;
     const double *X = nullptr;
     AFN_TRY(to_device(points, n * d, xin, &X, s));

@@ -183,7 +183,8 @@ afn_status fps_run(const double *X, int64_t n, int d, int64_t k, int64_t start, 
     // the temporaries are released at scope exit: make sure the kernel is done
     AFN_CUDA(cudaStreamSynchronize(s));
     int hs = 0;
-    AFN_CUDA(cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost));
+    AFN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AFN_CUDA(cudaStreamSynchronize(s));
     if (hs == DEV_TIMEOUT) {
         set_error("fps: grid barrier wait exceeded its limit");
         return AFN_ERR_TIMEOUT;

@@ -4,12 +4,18 @@
 //
 // One thread per row; a CTA of 128 consecutive rows streams the points
 // j < (its last row) through shared memory tiles and every lane reads the
-// same x_j (broadcast).  Distances are exact FP64 (no FMA, dimensions in
-// order), so the selection is identical to a sequential scan.  Each thread
-// keeps an unsorted candidate list in local memory and the position of its
-// worst entry; a new j replaces the worst only when strictly closer (j grows,
-// so an equal distance never wins).  The heaviest CTAs (largest i) start
-// first.
+// same x_j (broadcast).  The selection uses exact FP64 distances (no FMA,
+// dimensions in order), so it is identical to a sequential scan.  Each
+// thread keeps an unsorted candidate list and the position of its worst
+// entry; a new j replaces the worst only when strictly closer (j grows, so an
+// equal distance never wins).  Once the list is full, a j is first tested in
+// FP32: with every coordinate of magnitude <= M, the FP32 squared distance
+// z of a pair whose exact one is r2 satisfies |z - r2| <=
+// z <= (1 + gamma) (r2 + delta (2 sqrt(d r2) + d delta)) with delta about
+// 2^-22 M (the rounded coordinates and their rounded difference) and gamma <
+// (d + 2) 2^-24 (d + 1 roundings of the squares and the running sum), so a j
+// whose z exceeds that bound at r2 = wv cannot be strictly closer and is
+// skipped without computing its FP64 distance.  The heaviest CTAs (largest i) start first.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -22,52 +28,88 @@ namespace afn {
 static constexpr int KR = 128;    // rows per CTA
 static constexpr int KTJ = 128;   // points per tile
 
+// largest |coordinate| (as the bits of a non-negative double, whose integer
+// order is its numeric order)
+__global__ void maxabs_kernel(const double *__restrict__ X, int64_t count,
+                              unsigned long long *__restrict__ out)
+{
+    double m = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(X[e]));
+    m = warp_max_d(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 template <int CAP>
 __global__ void __launch_bounds__(KR) knn_kernel(const double *__restrict__ X, int64_t nr, int d,
-                                                 int w, int32_t *__restrict__ pat)
+                                                 int w, const unsigned long long *__restrict__ maxabs,
+                                                 int32_t *__restrict__ pat)
 {
     __shared__ double xs[KTJ * 16];
+    __shared__ float xf[KTJ * 16];
     const int64_t rb = (int64_t)gridDim.x - 1 - blockIdx.x;   // heavy blocks first
     const int64_t i = rb * KR + threadIdx.x;
     const int64_t ilast = min(nr - 1, rb * KR + KR - 1);
+    // error bound of the FP32 pre-test (see the file comment)
+    const double M = __longlong_as_double((long long)*maxabs);
+    const double delta = M * 0x1p-22 * (1.0 + 0x1p-20);
+    const double rel = (d + 2) * 0x1p-24;
     double xi[16];
-    for (int t = 0; t < d; ++t) xi[t] = (i < nr) ? X[i * d + t] : 0.0;
+    float xif[16];
+    for (int t = 0; t < d; ++t) {
+        xi[t] = (i < nr) ? X[i * d + t] : 0.0;
+        xif[t] = (float)xi[t];
+    }
     double bd[CAP];
     int32_t bj[CAP];
     const int64_t m = (i < nr) ? min(i, (int64_t)(w - 1)) : 0;
     int cnt = 0, worst = 0;
     double wv = (double)INFINITY;
+    float zcut = INFINITY;          // skip j when its FP32 distance exceeds this
     for (int64_t jt = 0; jt < ilast; jt += KTJ) {
         __syncthreads();
         for (int e = threadIdx.x; e < KTJ * d; e += KR) {
             int64_t j = jt + e / d;
-            xs[e] = (j < nr) ? X[jt * d + e] : 0.0;
+            const double v = (j < nr) ? X[jt * d + e] : 0.0;
+            xs[e] = v;
+            xf[e] = (float)v;
         }
         __syncthreads();
         const int64_t jend = min((int64_t)KTJ, i - jt);   // only j < i
         for (int jj = 0; jj < jend && m > 0; ++jj) {
+            if (cnt == m) {
+                float z = 0.f;
+                for (int t = 0; t < d; ++t) {
+                    const float u = __fsub_rn(xif[t], xf[jj * d + t]);
+                    z = __fadd_rn(z, __fmul_rn(u, u));
+                }
+                if (z > zcut) continue;
+            }
             double r2 = 0.0;
             for (int t = 0; t < d; ++t) {
                 double u = __dsub_rn(xi[t], xs[jj * d + t]);
                 r2 = __dadd_rn(r2, __dmul_rn(u, u));
             }
+            bool changed = false;
             if (cnt < m) {
                 bd[cnt] = r2;
                 bj[cnt] = (int32_t)(jt + jj);
                 ++cnt;
-                if (cnt == m) {
-                    worst = 0;
-                    for (int q = 1; q < cnt; ++q)
-                        if (bd[q] > bd[worst] || (bd[q] == bd[worst] && bj[q] > bj[worst])) worst = q;
-                    wv = bd[worst];
-                }
+                changed = cnt == m;
             } else if (r2 < wv) {
                 bd[worst] = r2;
                 bj[worst] = (int32_t)(jt + jj);
+                changed = true;
+            }
+            if (changed) {
                 worst = 0;
                 for (int q = 1; q < cnt; ++q)
                     if (bd[q] > bd[worst] || (bd[q] == bd[worst] && bj[q] > bj[worst])) worst = q;
                 wv = bd[worst];
+                // z > wv + bound(wv) implies r2 > wv
+                const double cut = (wv + delta * (2.0 * sqrt((double)d * wv) + d * delta)) / (1.0 - rel);
+                zcut = (float)(cut * (1.0 + 0x1p-22));
             }
         }
     }
@@ -98,12 +140,20 @@ afn_status knn_pattern(const double *Xr, int64_t nr, int d, int w, int32_t *pat,
         set_error("knn: unsupported d=%d or w=%d (1<=d<=16, 1<=w<=256)", d, w);
         return AFN_ERR_ARG;
     }
+    DevBuf mx;
+    AFN_TRY(mx.alloc(sizeof(unsigned long long)));
+    AFN_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
+    const int64_t cnt = nr * d;
+    maxabs_kernel<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, s>>>(
+        Xr, cnt, mx.as<unsigned long long>());
+    const unsigned long long *M = mx.as<unsigned long long>();
     unsigned grid = (unsigned)((nr + KR - 1) / KR);
-    if (w <= 32) knn_kernel<31><<<grid, KR, 0, s>>>(Xr, nr, d, w, pat);
-    else if (w <= 64) knn_kernel<63><<<grid, KR, 0, s>>>(Xr, nr, d, w, pat);
-    else if (w <= 128) knn_kernel<127><<<grid, KR, 0, s>>>(Xr, nr, d, w, pat);
-    else knn_kernel<255><<<grid, KR, 0, s>>>(Xr, nr, d, w, pat);
+    if (w <= 32) knn_kernel<31><<<grid, KR, 0, s>>>(Xr, nr, d, w, M, pat);
+    else if (w <= 64) knn_kernel<63><<<grid, KR, 0, s>>>(Xr, nr, d, w, M, pat);
+    else if (w <= 128) knn_kernel<127><<<grid, KR, 0, s>>>(Xr, nr, d, w, M, pat);
+    else knn_kernel<255><<<grid, KR, 0, s>>>(Xr, nr, d, w, M, pat);
     AFN_CUDA(cudaGetLastError());
+    // mx is released on stream s after the kernels that read it
     return AFN_OK;
 }
 

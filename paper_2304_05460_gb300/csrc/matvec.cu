@@ -13,6 +13,9 @@
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
+#include "matvec_tc.cuh"
+#include "matvec_df.cuh"
+#include "group.cuh"
 
 namespace afn {
 
@@ -302,175 +305,25 @@ __global__ void __launch_bounds__(NT) matvec32p_kernel(const float *__restrict__
     }
 }
 
-// --------------------------------------------------------------------------
-// Tensor-core variant for 8, 16 or 32 right-hand sides.  The kernel-matrix
-// block K[i, j] (16 rows x 8 points) is evaluated on the FP32 pipes directly
-// into the A-fragment registers of mma.m16n8k8 (tf32), and the contraction
-// with the p tile runs on the tensor cores in three tf32 passes
-// (K_hi p_hi + K_hi p_lo + K_lo p_hi, each operand split as x = hi + lo with
-// hi = tf32(x), lo = tf32(x - hi)), which keeps single-precision accuracy.
-// A warp owns 16 rows; a CTA owns 128 rows and one j-chunk; point and p
-// tiles (64 points) are staged in shared memory with bank-conflict-free
-// strides.  Fragment layouts (PTX ISA, mma.m16n8k8 .tf32): with g = lane/4,
-// t = lane%4, A holds (g,t) (g+8,t) (g,t+4) (g+8,t+4); B holds (t,g) (t+4,g);
-// C holds (g,2t) (g,2t+1) (g+8,2t) (g+8,2t+1).
-// --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tf32_bits(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-#ifndef AFN_TC_MINB
-#define AFN_TC_MINB 3
-#endif
-#ifndef AFN_TC_FOLD
-#define AFN_TC_FOLD 2
-#endif
-#ifndef AFN_TC_KAHAN
-#define AFN_TC_KAHAN 1
-#endif
-static constexpr int TC_FOLD = AFN_TC_FOLD;        // blocks of 8 points per accumulator fold
-static constexpr bool TC_KAHAN = AFN_TC_KAHAN != 0;
-
-// x = hi + lo with hi, lo tf32 (10-bit mantissa) values, each rounded to
-// nearest (ties away from zero): adding half a unit of the 13 dropped bits
-// and masking them is that rounding for finite inputs.
-__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
-{
-#ifdef AFN_TC_CVT_SPLIT
-    hi = tf32_bits(x);
-    lo = tf32_bits(x - __uint_as_float(hi));
-#else
-    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
-    lo = (__float_as_uint(x - __uint_as_float(hi)) + 0x1000u) & 0xffffe000u;
-#endif
-}
-
-__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, "
-                 "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-static constexpr int TCR = 128;   // rows per CTA (8 warps x 16)
-static constexpr int TCJ = 64;    // points per staged tile
-
+// Single-system tensor-core kernel: CTA = 128 rows x one j-chunk, one
+// partial per (chunk, column), summed in order by matvec_finish.
 template <int DS, int NB, int KER>
 __global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MINB : 2)
     matvec32tc_kernel(const float *__restrict__ Xs, int64_t n, const float *__restrict__ P,
                       int64_t ldp, float *__restrict__ part, int64_t chunk)
 {
     constexpr int NR = NB * 8;
-    constexpr int PS = (NR == 8) ? 8 : (NR == 16 ? 24 : 40);   // t*PS distinct mod 32 by 8s
-    constexpr int DSP = DS + 2;                                 // f2 stride of a point row
-    __shared__ __align__(16) f2_t xsd[TCJ * DSP];               // (x, x) duplicated coordinates
-    __shared__ __align__(16) uint32_t phi[TCJ * PS];
-    __shared__ __align__(16) uint32_t plo[TCJ * PS];
+    __shared__ __align__(16) f2_t xsd[TCJ * (DS + 2)];
+    __shared__ __align__(16) uint32_t phi[TCJ * TcPS<NB>::v];
+    __shared__ __align__(16) uint32_t plo[TCJ * TcPS<NB>::v];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int64_t ia = (int64_t)blockIdx.x * TCR + warp * 16 + g;
     const int64_t ib = ia + 8;
     const int64_t j0 = (int64_t)blockIdx.y * chunk;
     const int64_t j1 = min(n, j0 + chunk);
-
-    f2_t xi[DS];   // (x_ia[q], x_ib[q])
-#pragma unroll
-    for (int q = 0; q < DS; ++q)
-        xi[q] = f2_pack(ia < n ? Xs[ia * DS + q] : 0.f, ib < n ? Xs[ib * DS + q] : 0.f);
-    float acc[NB][4], cmp[TC_KAHAN ? NB : 1][4];
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[b][r] = 0.f;
-#pragma unroll
-    for (int b = 0; b < (TC_KAHAN ? NB : 1); ++b)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) cmp[b][r] = 0.f;
-
-    for (int64_t jt = j0; jt < j1; jt += TCJ) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < TCJ * DS; e += 256) {
-            int jj = e / DS, q = e % DS;
-            int64_t j = jt + jj;
-            float v = (j < j1) ? Xs[j * DS + q] : 0.f;
-            xsd[jj * DSP + q] = f2_pack(v, v);
-        }
-        for (int e = threadIdx.x; e < TCJ * NR / 4; e += 256) {
-            int jj = e % TCJ, c4 = e / TCJ;
-            int64_t j = jt + jj;
-            uint4 h4, l4;
-            tf32_split(j < j1 ? P[(4 * c4 + 0) * ldp + j] : 0.f, h4.x, l4.x);
-            tf32_split(j < j1 ? P[(4 * c4 + 1) * ldp + j] : 0.f, h4.y, l4.y);
-            tf32_split(j < j1 ? P[(4 * c4 + 2) * ldp + j] : 0.f, h4.z, l4.z);
-            tf32_split(j < j1 ? P[(4 * c4 + 3) * ldp + j] : 0.f, h4.w, l4.w);
-            *reinterpret_cast<uint4 *>(phi + jj * PS + 4 * c4) = h4;
-            *reinterpret_cast<uint4 *>(plo + jj * PS + 4 * c4) = l4;
-        }
-        __syncthreads();
-        float tac[NB][4];
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) tac[b][r] = 0.f;
-#pragma unroll
-        for (int kb = 0; kb < TCJ / 8; ++kb) {
-            const f2_t *xa = xsd + (kb * 8 + t) * DSP;
-            const f2_t *xb = xsd + (kb * 8 + t + 4) * DSP;
-            f2_t ra = 0ull, rb = 0ull;
-#pragma unroll
-            for (int q = 0; q < DS; ++q) {
-                f2_t u = f2_sub(xi[q], xa[q]);
-                ra = f2_fma(u, u, ra);
-                u = f2_sub(xi[q], xb[q]);
-                rb = f2_fma(u, u, rb);
-            }
-            float r_aa, r_ba, r_ab, r_bb;   // (row ia|ib, column t|t+4)
-            f2_unpack(ra, r_aa, r_ba);
-            f2_unpack(rb, r_ab, r_bb);
-            uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3;
-            tf32_split(kernel32_scaled<KER>(r_aa), ah0, al0);   // (g,   t)
-            tf32_split(kernel32_scaled<KER>(r_ba), ah1, al1);   // (g+8, t)
-            tf32_split(kernel32_scaled<KER>(r_ab), ah2, al2);   // (g,   t+4)
-            tf32_split(kernel32_scaled<KER>(r_bb), ah3, al3);   // (g+8, t+4)
-            const uint32_t *ph0 = phi + (kb * 8 + t) * PS + g;
-            const uint32_t *ph1 = phi + (kb * 8 + t + 4) * PS + g;
-            const uint32_t *pl0 = plo + (kb * 8 + t) * PS + g;
-            const uint32_t *pl1 = plo + (kb * 8 + t + 4) * PS + g;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const uint32_t bh0 = ph0[b * 8], bh1 = ph1[b * 8];
-                const uint32_t bl0 = pl0[b * 8], bl1 = pl1[b * 8];
-                // small cross terms first, then the leading product
-                mma_tf32(tac[b], al0, al1, al2, al3, bh0, bh1);
-                mma_tf32(tac[b], ah0, ah1, ah2, ah3, bl0, bl1);
-                mma_tf32(tac[b], ah0, ah1, ah2, ah3, bh0, bh1);
-            }
-            // The tensor-core accumulator is not rounded to nearest; folding
-            // it into the FP32 running sum every TC_FOLD blocks of 8 points
-            // keeps its error from growing over the whole j range.
-            if ((kb + 1) % TC_FOLD == 0) {
-#pragma unroll
-                for (int b = 0; b < NB; ++b)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        if constexpr (TC_KAHAN) {
-                            float y = tac[b][r] - cmp[b][r];
-                            float s = acc[b][r] + y;
-                            cmp[b][r] = (s - acc[b][r]) - y;
-                            acc[b][r] = s;
-                        } else {
-                            acc[b][r] += tac[b][r];
-                        }
-                        tac[b][r] = 0.f;
-                    }
-            }
-        }
-    }
+    float acc[NB][4];
+    mv32tc_rows<DS, NB, KER>(Xs, n, P, ldp, (int64_t)blockIdx.x * TCR, j0, j1, xsd, phi, plo, acc);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int c = b * 8 + 2 * t;
@@ -480,6 +333,7 @@ __global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MI
         if (ib < n) { p0[ib] = acc[b][2]; p1[ib] = acc[b][3]; }
     }
 }
+
 
 size_t matvec32_scratch(int64_t n, int nrhs)
 {
@@ -566,27 +420,32 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
 }
 
 // ------------------------------------------------------------------ FP64 --
+// FP64 tile: a 256-thread CTA = TI rows x JG j-groups.  Each thread sums
+// K(x_i, x_j) p_j over its j-group of every staged tile of [j0, j1) for row
+// i = row0 + threadIdx.x % TI; the j-groups are then reduced in shared memory
+// in a fixed order, and on return threads with threadIdx.x < TI hold the
+// row's sums in acc.  sm holds max(TJ*D + NR*TJ, (JG-1)*TI*NR) doubles.
 template <int D, int NR>
-__global__ void __launch_bounds__(NT) matvec64_kernel(const double *__restrict__ X, int d,
-                                                      int64_t n, int kernel, double l,
-                                                      const double *__restrict__ P, int64_t ldp,
-                                                      double *__restrict__ part, int64_t chunk)
+struct Mv64Smem {
+    static constexpr int TILE = TJ * D + NR * TJ;
+    static constexpr int RED = (JG - 1) * TI * NR;
+    static constexpr int v = TILE > RED ? TILE : RED;
+};
+
+template <int D, int NR>
+__device__ __forceinline__ void mv64_rows(const double *__restrict__ X, int d, int64_t n,
+                                          int kernel, double l, const double *__restrict__ P,
+                                          int64_t ldp, int64_t row0, int64_t j0, int64_t j1,
+                                          double *sm, double (&acc)[NR])
 {
-    constexpr int TILE = TJ * D + NR * TJ;
-    constexpr int RED = (JG - 1) * TI * NR;
-    constexpr int SM = TILE > RED ? TILE : RED;
-    __shared__ double sm[SM];
     double *xs = sm;
     double *ps = sm + TJ * D;
     const int ti = threadIdx.x % TI;
     const int g = threadIdx.x / TI;
-    const int64_t i = (int64_t)blockIdx.x * TI + ti;
-    const int64_t j0 = (int64_t)blockIdx.y * chunk;
-    const int64_t j1 = min(n, j0 + chunk);
+    const int64_t i = row0 + ti;
     double xi[D];
 #pragma unroll
     for (int t = 0; t < D; ++t) xi[t] = (i < n && t < d) ? X[i * d + t] : 0.0;
-    double acc[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[c] = 0.0;
     const double inv_l2 = 1.0 / (l * l);
@@ -629,13 +488,28 @@ __global__ void __launch_bounds__(NT) matvec64_kernel(const double *__restrict__
         for (int c = 0; c < NR; ++c) sm[((g - 1) * NR + c) * TI + ti] = acc[c];
     }
     __syncthreads();
-    if (g == 0 && i < n) {
+    if (g == 0) {
 #pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            double s = acc[c];
-            for (int q = 1; q < JG; ++q) s += sm[((q - 1) * NR + c) * TI + ti];
-            part[((int64_t)blockIdx.y * NR + c) * n + i] = s;
-        }
+        for (int c = 0; c < NR; ++c)
+            for (int q = 1; q < JG; ++q) acc[c] += sm[((q - 1) * NR + c) * TI + ti];
+    }
+}
+
+template <int D, int NR>
+__global__ void __launch_bounds__(NT) matvec64_kernel(const double *__restrict__ X, int d,
+                                                      int64_t n, int kernel, double l,
+                                                      const double *__restrict__ P, int64_t ldp,
+                                                      double *__restrict__ part, int64_t chunk)
+{
+    __shared__ double sm[Mv64Smem<D, NR>::v];
+    const int64_t i = (int64_t)blockIdx.x * TI + threadIdx.x % TI;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk;
+    const int64_t j1 = min(n, j0 + chunk);
+    double acc[NR];
+    mv64_rows<D, NR>(X, d, n, kernel, l, P, ldp, (int64_t)blockIdx.x * TI, j0, j1, sm, acc);
+    if (threadIdx.x < TI && i < n) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c) part[((int64_t)blockIdx.y * NR + c) * n + i] = acc[c];
     }
 }
 
@@ -692,6 +566,203 @@ afn_status matvec64(const double *X, int64_t n, int d, KParams kp, const double 
     return AFN_OK;
 }
 
+// ----------------------------------------------------- double-float --
+// FP64-accurate matvec for the residual replacements of the mixed solve,
+// computed in double-float on the FP32 pipes (matvec_df.cuh).  Same CTA
+// shape and split-K partials as the FP64 kernel: TI rows x JG j-groups,
+// TJ-point tiles of the prescaled double-float points and of p (split into
+// double-float) in shared memory, partial sums per j-chunk in FP64.
+__device__ __forceinline__ void df_table_init(DfExpTable &T)
+{
+    if (threadIdx.x < 64) {
+        const double v = exp2((double)threadIdx.x / 64.0);
+        const float h = (float)v;
+        T.t_h[threadIdx.x] = h;
+        T.t_l[threadIdx.x] = (float)(v - (double)h);
+    }
+    if (threadIdx.x == 64) {
+        const double ln2 = 0.6931471805599453094, log2e = 1.4426950408889634074;
+        T.ln2_h = (float)ln2;
+        T.ln2_l = (float)(ln2 - (double)T.ln2_h);
+        T.log2e_h = (float)log2e;
+        T.log2e_l = (float)(log2e - (double)T.log2e_h);
+    }
+}
+
+template <int DS, int NR>
+struct MvDfSmem {
+    static constexpr int TILE = TJ * DS * 2 + NR * TJ * 2;   // floats
+    static constexpr int RED = (JG - 1) * TI * NR * 2;       // floats (doubles x 2)
+    static constexpr int v = TILE > RED ? TILE : RED;
+};
+
+// On return threads with threadIdx.x < TI hold row (row0 + threadIdx.x)'s
+// sums over [j0, j1) in acc.
+template <int DS, int NR, int KER>
+__device__ __forceinline__ void mvdf_rows(const float2 *__restrict__ Xd, int64_t n,
+                                          const double *__restrict__ P, int64_t ldp,
+                                          int64_t row0, int64_t j0, int64_t j1, float *sm,
+                                          const DfExpTable &T, double (&acc)[NR])
+{
+    float2 *xs = reinterpret_cast<float2 *>(sm);
+    float2 *ps = xs + TJ * DS;
+    const int ti = threadIdx.x % TI;
+    const int g = threadIdx.x / TI;
+    const int64_t i = row0 + ti;
+    dfl xi[DS];
+#pragma unroll
+    for (int q = 0; q < DS; ++q) {
+        const float2 v = i < n ? Xd[i * DS + q] : make_float2(0.f, 0.f);
+        xi[q] = dfl{v.x, v.y};
+    }
+    float S[NR], Cc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) S[c] = Cc[c] = 0.f;
+    for (int64_t jt = j0; jt < j1; jt += TJ) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TJ * DS; e += NT) {
+            const int64_t j = jt + e / DS;
+            xs[e] = j < j1 ? Xd[jt * DS + e] : make_float2(0.f, 0.f);
+        }
+        for (int e = threadIdx.x; e < NR * TJ; e += NT) {
+            const int c = e / TJ, jj = e % TJ;
+            const int64_t j = jt + jj;
+            const double v = j < j1 ? P[c * ldp + j] : 0.0;
+            const float h = (float)v;
+            ps[e] = make_float2(h, (float)(v - (double)h));
+        }
+        __syncthreads();
+        for (int jj = g * (TJ / JG); jj < (g + 1) * (TJ / JG); ++jj) {
+            const dfl z = df_dist2<DS>(xi, xs + jj * DS);
+            const dfl kv = df_kernel<KER>(z, T);
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const float2 x = ps[c * TJ + jj];
+                const float p = __fmul_rn(kv.h, x.x);
+                float e = __fmaf_rn(kv.h, x.x, -p);
+                e = __fmaf_rn(kv.h, x.y, e);
+                e = __fmaf_rn(kv.l, x.x, e);
+                float t;
+                two_sum(S[c], p, S[c], t);
+                Cc[c] = __fadd_rn(Cc[c], __fadd_rn(t, e));
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = (double)S[c] + (double)Cc[c];
+    __syncthreads();
+    double *red = reinterpret_cast<double *>(sm);
+    if (g > 0) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c) red[((g - 1) * NR + c) * TI + ti] = acc[c];
+    }
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            for (int q = 1; q < JG; ++q) acc[c] += red[((q - 1) * NR + c) * TI + ti];
+    }
+}
+
+template <int DS, int NR, int KER>
+__global__ void __launch_bounds__(NT) matvecdf_kernel(const float2 *__restrict__ Xd, int64_t n,
+                                                      const double *__restrict__ P, int64_t ldp,
+                                                      double *__restrict__ part, int64_t chunk)
+{
+    __shared__ __align__(16) float sm[MvDfSmem<DS, NR>::v];
+    __shared__ DfExpTable T;
+    df_table_init(T);
+    const int64_t i = (int64_t)blockIdx.x * TI + threadIdx.x % TI;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk;
+    const int64_t j1 = min(n, j0 + chunk);
+    double acc[NR];
+    mvdf_rows<DS, NR, KER>(Xd, n, P, ldp, (int64_t)blockIdx.x * TI, j0, j1, sm, T, acc);
+    if (threadIdx.x < TI && i < n) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c) part[((int64_t)blockIdx.y * NR + c) * n + i] = acc[c];
+    }
+}
+
+template <int DS, int KER>
+static void launchdf_nr(int nr, const float2 *Xd, int64_t n, const double *P, double *part,
+                        int js, int64_t chunk, cudaStream_t s)
+{
+    dim3 grid((unsigned)((n + TI - 1) / TI), (unsigned)js);
+    switch (nr) {
+    case 1: matvecdf_kernel<DS, 1, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
+    case 2: matvecdf_kernel<DS, 2, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
+    case 4: matvecdf_kernel<DS, 4, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
+    case 8: matvecdf_kernel<DS, 8, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
+    default: matvecdf_kernel<DS, 16, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
+    }
+}
+
+size_t matvecdf_scratch(int64_t n, int nrhs)
+{
+    return sizeof(double) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 16) *
+               (size_t)n + 256;
+}
+
+afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
+                     int nrhs, double *q, void *scratch, size_t scratch_bytes, cudaStream_t s)
+{
+    if (n <= 0 || nrhs <= 0) return AFN_OK;
+    if (scratch_bytes < matvecdf_scratch(n, nrhs)) {
+        set_error("matvec_df: scratch too small");
+        return AFN_ERR_ARG;
+    }
+    int js;
+    int64_t chunk;
+    chunking(n, js, chunk);
+    double *part = static_cast<double *>(scratch);
+    for (int c0 = 0; c0 < nrhs;) {
+        const int b = piece(nrhs - c0, 16);
+        const double *pp = p + (int64_t)c0 * n;
+        const int key = ds * 2 + kernel;
+        switch (key) {
+        case 8: launchdf_nr<4, 0>(b, Xd, n, pp, part, js, chunk, s); break;
+        case 9: launchdf_nr<4, 1>(b, Xd, n, pp, part, js, chunk, s); break;
+        case 16: launchdf_nr<8, 0>(b, Xd, n, pp, part, js, chunk, s); break;
+        case 17: launchdf_nr<8, 1>(b, Xd, n, pp, part, js, chunk, s); break;
+        case 32: launchdf_nr<16, 0>(b, Xd, n, pp, part, js, chunk, s); break;
+        default: launchdf_nr<16, 1>(b, Xd, n, pp, part, js, chunk, s); break;
+        }
+        const int64_t tot = n * b;
+        matvec_finish<double><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            part, js, b, n, pp, n, q + (int64_t)c0 * n, n, mu);
+        c0 += b;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "matvec_df launch");
+    return AFN_OK;
+}
+
+// double-float prescaled points: x * scale as (hi, lo) floats, n x ds
+__global__ void points_df_kernel(const double *__restrict__ X, int64_t n, int d, int ds,
+                                 double scale, float2 *__restrict__ Xd)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * ds) return;
+    const int64_t i = e / ds;
+    const int t = (int)(e % ds);
+    const double v = t < d ? X[i * d + t] * scale : 0.0;
+    const float h = (float)v;
+    Xd[e] = make_float2(h, (float)(v - (double)h));
+}
+
+afn_status make_points_df(const double *X, int64_t n, int d, int ds, int kernel, double l,
+                          float2 *Xd, cudaStream_t s)
+{
+    const double scale = (kernel == 0) ? 1.2011224087864498 / l    // sqrt(log2 e) / l
+                                       : 1.7320508075688772 / l;   // sqrt(3) / l
+    const int64_t tot = n * ds;
+    if (tot == 0) return AFN_OK;
+    points_df_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, n, d, ds, scale, Xd);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "points_df launch");
+    return AFN_OK;
+}
+
 // --------------------------------------------------- FP32 point staging --
 // Prescaled coordinates x~ = fl32(x * scale), n x ds (ds = stored_dim32(dp)).
 __global__ void points32_kernel(const double *__restrict__ X, int64_t n, int d, int ds,
@@ -718,6 +789,104 @@ afn_status make_points32(const double *X, int64_t n, int d, int dp, int kernel, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "points32 launch");
     return AFN_OK;
+}
+
+// ------------------------------------------------------ grouped matvecs --
+// One persistent launch over the 128-row (FP32) or 64-row (FP64) tiles of
+// every member system of a group.  A tile covers one column group of 8
+// right-hand sides and the whole j range of its system, so each output
+// element is summed by one CTA in a fixed order and a system's result does
+// not depend on which other systems share the launch.
+
+__device__ __forceinline__ bool group_live(const GSys &S, int cg)
+{
+    const int c0 = cg * GC, c1 = min(S.nrhs, c0 + GC);
+    for (int c = c0; c < c1; ++c)
+        if (S.cs[c].active) return true;
+    return false;
+}
+
+static constexpr int GMV32_MINB = 3;
+
+__global__ void __launch_bounds__(256, GMV32_MINB) gmv32_kernel(const GDev *__restrict__ gd)
+{
+    __shared__ __align__(16) f2_t xsd[TCJ * (16 + 2)];
+    __shared__ __align__(16) uint32_t phi[TCJ * TcPS<1>::v];
+    __shared__ __align__(16) uint32_t plo[TCJ * TcPS<1>::v];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int nt = gd->nmv;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const GTile tl = gd->mv[ti];
+        const GSys &S = gd->sys[tl.sys];
+        if (!group_live(S, tl.cg)) continue;
+        const int64_t n = S.n;
+        const float *P = S.p32 + (int64_t)tl.cg * GC * n;
+        float acc[1][4];
+        switch (S.ds * 2 + S.kernel) {
+        case 8:  mv32tc_rows<4, 1, 0>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        case 9:  mv32tc_rows<4, 1, 1>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        case 16: mv32tc_rows<8, 1, 0>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        case 17: mv32tc_rows<8, 1, 1>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        case 32: mv32tc_rows<16, 1, 0>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        default: mv32tc_rows<16, 1, 1>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        }
+        const int64_t ia = tl.r0 + warp * 16 + g, ib = ia + 8;
+        const float mu = S.mu32;
+        const float *p0 = P + (int64_t)(2 * t) * n, *p1 = p0 + n;
+        float *q0 = S.q32 + ((int64_t)tl.cg * GC + 2 * t) * n, *q1 = q0 + n;
+        if (ia < n) { q0[ia] = acc[0][0] + mu * p0[ia]; q1[ia] = acc[0][1] + mu * p1[ia]; }
+        if (ib < n) { q0[ib] = acc[0][2] + mu * p0[ib]; q1[ib] = acc[0][3] + mu * p1[ib]; }
+    }
+}
+
+// q = (K + mu I) x, FP64-accurate (double-float, matvec_df.cuh), for the
+// systems whose residual is being replaced
+__global__ void __launch_bounds__(NT) gmvdf_kernel(const GDev *__restrict__ gd)
+{
+    __shared__ __align__(16) float sm[MvDfSmem<16, GC>::v];
+    __shared__ DfExpTable T;
+    df_table_init(T);
+    const int nt = gd->nmv64;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const GTile tl = gd->mv64[ti];
+        if (!gd->rep[tl.sys]) continue;
+        const GSys &S = gd->sys[tl.sys];
+        const int64_t n = S.n;
+        const double *P = S.x + (int64_t)tl.cg * GC * n;
+        double acc[GC];
+        switch (S.ds * 2 + S.kernel) {
+        case 8:  mvdf_rows<4, GC, 0>(S.Xdf, n, P, n, tl.r0, 0, n, sm, T, acc); break;
+        case 9:  mvdf_rows<4, GC, 1>(S.Xdf, n, P, n, tl.r0, 0, n, sm, T, acc); break;
+        case 16: mvdf_rows<8, GC, 0>(S.Xdf, n, P, n, tl.r0, 0, n, sm, T, acc); break;
+        case 17: mvdf_rows<8, GC, 1>(S.Xdf, n, P, n, tl.r0, 0, n, sm, T, acc); break;
+        case 32: mvdf_rows<16, GC, 0>(S.Xdf, n, P, n, tl.r0, 0, n, sm, T, acc); break;
+        default: mvdf_rows<16, GC, 1>(S.Xdf, n, P, n, tl.r0, 0, n, sm, T, acc); break;
+        }
+        const int64_t i = tl.r0 + threadIdx.x;
+        if (threadIdx.x < TI && i < n) {
+            double *q = S.q + (int64_t)tl.cg * GC * n;
+#pragma unroll
+            for (int c = 0; c < GC; ++c) q[c * n + i] = acc[c] + S.mu * P[c * n + i];
+        }
+    }
+}
+
+int group_mv32_rows() { return TCR; }
+int group_mv64_rows() { return TI; }
+
+afn_status group_matvec32(const GDev *gd, cudaStream_t s)
+{
+    gmv32_kernel<<<num_sms() * GMV32_MINB, 256, 0, s>>>(gd);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped matvec32 launch");
+}
+
+afn_status group_matvec64(const GDev *gd, cudaStream_t s)
+{
+    gmvdf_kernel<<<num_sms() * 2, NT, 0, s>>>(gd);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped matvec64 launch");
 }
 
 }  // namespace afn

@@ -228,9 +228,9 @@ static afn_status tridiagonalize(double *A, int s, double *dg, double *of, int *
     void *args[] = {(void *)&A, (void *)&s, (void *)&dg, (void *)&of, (void *)&pgp, (void *)&pp,
                     (void *)&bp, (void *)&err};
     AFN_CUDA(cudaLaunchCooperativeKernel((void *)tridiag_kernel, dim3(nb), dim3(TT), args, 0, st));
-    AFN_CUDA(cudaStreamSynchronize(st));
     int he = 0;
-    AFN_CUDA(cudaMemcpy(&he, err, sizeof(int), cudaMemcpyDeviceToHost));
+    AFN_CUDA(cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AFN_CUDA(cudaStreamSynchronize(st));
     if (he == DEV_TIMEOUT) {
         set_error("tridiagonalisation: grid barrier wait exceeded its limit");
         return AFN_ERR_TIMEOUT;

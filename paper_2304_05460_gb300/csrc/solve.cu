@@ -313,9 +313,26 @@ static afn_status apply32(Handle *h, const float *r, int nrhs, float *z, void *t
                             h->G32.as<float>(), r, nrhs, z, static_cast<float *>(tmp), h->stream);
 }
 
+// AFN_RESID=fp64 computes the residual replacements of mixed handles with
+// the FP64 kernel instead of the double-float one (comparison)
+static bool resid_fp64()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("AFN_RESID");
+        v = (e && e[0] == 'f') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+// FP64-accurate q = (K + mu I) p: FP64 kernel on FP64 handles, double-float
+// kernel on the FP32 pipes for mixed handles
 static afn_status mv64(Handle *h, const double *p, int nrhs, double *q, const Work &wk)
 {
     Scope sc(&h->prof, K_MATVEC64);
+    if (h->Xdf.p && !resid_fp64())
+        return matvec_df(h->Xdf.as<float2>(), h->n, stored_dim32(h->dp), h->kernel, h->mu, p, nrhs,
+                         q, wk.mv, wk.mv_bytes, h->stream);
     KParams kp{h->kernel, h->l, h->mu};
     return matvec64(h->X64.as<double>(), h->n, h->d, kp, p, nrhs, q, wk.mv, wk.mv_bytes, h->stream);
 }

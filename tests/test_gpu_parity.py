@@ -97,10 +97,14 @@ def test_matvec_fp64(afn, n, d, ker, nrhs):
     X = inputs.normal_points(n, d, 300 + n)
     P = inputs.rhs(n, nrhs, 301 + n)
     l = 0.7 * np.sqrt(d)
-    q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=afn.PREC_FP64)
     ref = oracle.matvec(X, ker, l, 1e-2, P)
-    bound = scale_bound(X, ker, l, 1e-2, P).reshape(q.shape)
-    assert np.all(np.abs(q - ref.reshape(q.shape)) <= 1e-12 * bound + 1e-300)
+    # FP64 kernel, and the double-float kernel (FP32 pipes) of the mixed
+    # solves' residual replacements: both within 1e-12 of the scale
+    for prec in (afn.PREC_FP64, afn.MATVEC_DF):
+        q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=prec)
+        bound = scale_bound(X, ker, l, 1e-2, P).reshape(q.shape)
+        err = np.abs(q - ref.reshape(q.shape)) / (bound + 1e-300)
+        assert err.max() <= 1e-12, (prec, err.max())
 
 
 @pytest.mark.parametrize("n,d,ker,nrhs", [(257, 3, G, 1), (1000, 8, M32, 3), (2049, 16, G, 32),
@@ -119,7 +123,7 @@ def test_matvec_fp32(afn, n, d, ker, nrhs):
 def test_matvec_sampled_rows_full_size(afn):
     s = inputs.normal_8d(l=2.0, nrhs=2)
     rows = inputs.rng(9).choice(s.n, 64, replace=False)
-    for prec, tolr in ((afn.PREC_FP64, 1e-12), (afn.PREC_MIXED, 2e-5)):
+    for prec, tolr in ((afn.PREC_FP64, 1e-12), (afn.MATVEC_DF, 1e-11), (afn.PREC_MIXED, 2e-5)):
         q = afn.afn_kernel_matvec(s.X, G, 2.0, 1e-2, s.B, precision=prec)
         ref = oracle.matvec_rows(s.X, G, 2.0, 1e-2, s.B, rows)
         absb = oracle.matvec_rows(s.X, G, 2.0, 1e-2, np.abs(s.B), rows)
