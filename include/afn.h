@@ -50,8 +50,15 @@ typedef enum { AFN_GAUSSIAN = 0, AFN_MATERN32 = 1 } afn_kernel;
 
 typedef enum {
     AFN_PREC_FP64 = 0,         /* everything in FP64 */
-    AFN_PREC_MIXED = 1         /* FP32 matvec / apply / FSAI build + FP64 Cholesky, dots,
-                                  scalars and an outer FP64 residual-correction loop */
+    AFN_PREC_MIXED = 1,        /* FP32 matvec / apply / FSAI build + FP64 Cholesky, dots,
+                                  scalars and FP64 residual replacements (reliable updates) */
+    AFN_PREC_DF = 2,           /* FP64 PCG, factors and apply; the matvec FP64-accurate in
+                                  double-float on the FP32 pipes (matvec_df) */
+    AFN_PREC_AUTO = 3          /* per system at build time: MIXED when
+                                  rho = 2^-24 max_i sum_j K_ij / mu <= 0.3 (the FP32 matvec
+                                  error stays small next to mu; AFN_AUTO_RHO in the
+                                  environment overrides 0.3), else DF; the handle reports
+                                  the precision chosen and rho (afn_build_info) */
 } afn_precision;
 
 typedef enum {
@@ -94,6 +101,7 @@ typedef struct {
     double l, mu;
     double build_ms;           /* device time of afn_build */
     int64_t device_bytes;      /* device memory held by the handle */
+    double rho32;              /* AFN_PREC_AUTO: 2^-24 max_i sum_j K_ij / mu (0 otherwise) */
 } afn_build_info;
 
 typedef struct {
@@ -175,11 +183,11 @@ int64_t afn_launch_count(void);
  * points n x d row-major FP64; p, q n x nrhs column-major FP64.  precision:
  * AFN_PREC_FP64 computes in FP64; AFN_PREC_MIXED evaluates pairs in FP32
  * (points and p rounded to FP32, FP32 accumulation) and returns FP64;
- * AFN_MATVEC_DF computes FP64-accurate values (kernel values to about 1e-14
- * relative, double-float sums) on the FP32 pipes -- the kernel the mixed
- * solves use for their FP64 residual b - (K + mu I) x.
+ * AFN_PREC_DF computes FP64-accurate values (kernel values to about 1e-14
+ * relative, double-float sums) on the FP32 pipes -- the kernel of the DF
+ * solves and of the mixed solves' FP64 residual b - (K + mu I) x.
  */
-#define AFN_MATVEC_DF 2
+#define AFN_MATVEC_DF AFN_PREC_DF
 afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
                              double mu, const double *p, int32_t nrhs, double *q,
                              int32_t precision, void *stream);

@@ -22,8 +22,8 @@ AFN_ERR_TIMEOUT, AFN_ERR_CUDA, AFN_ERR_BUSY = 5, 6, 7
 STATUS_NAMES = {0: "AFN_OK", 1: "AFN_ERR_ARG", 2: "AFN_ERR_OOM", 3: "AFN_ERR_NOT_SPD",
                 4: "AFN_ERR_NO_CONVERGE", 5: "AFN_ERR_TIMEOUT", 6: "AFN_ERR_CUDA", 7: "AFN_ERR_BUSY"}
 GAUSSIAN, MATERN32 = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
-MATVEC_DF = 2              # afn_kernel_matvec only: FP64-accurate double-float
+PREC_FP64, PREC_MIXED, PREC_DF, PREC_AUTO = 0, 1, 2, 3
+MATVEC_DF = PREC_DF        # afn_kernel_matvec: FP64-accurate double-float
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
 
@@ -46,7 +46,7 @@ class afn_build_info(C.Structure):
                 ("w", C.c_int32), ("kernel", C.c_int32), ("precision", C.c_int32),
                 ("rank_r", C.c_int64), ("rank_branch", C.c_int32), ("pad_", C.c_int32),
                 ("l", C.c_double), ("mu", C.c_double), ("build_ms", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("rho32", C.c_double)]
 
 
 class afn_solve_info(C.Structure):
@@ -391,7 +391,7 @@ def afn_build_batched(systems, opt: afn_options | None = None, **kw):
     """Builds every system of ``systems`` (dicts with keys points, kernel, l,
     mu, k_max, fsai_nnz) with the mixed-precision options ``opt``."""
     if opt is None:
-        kw.setdefault("precision", PREC_MIXED)
+        kw.setdefault("precision", PREC_AUTO)
         opt = options(**kw)
     ns = len(systems)
     arr = (afn_system * ns)()
@@ -524,7 +524,7 @@ class Server:
         cfg.memory_budget = int(memory_budget)
         cfg.max_active = int(max_active)
         cfg.build_threads = int(build_threads)
-        kw.setdefault("precision", PREC_MIXED)
+        kw.setdefault("precision", PREC_AUTO)
         cfg.opt = options(**kw)
         self.ptr = C.c_void_p()
         _check(_lib.afn_server_create(C.byref(cfg), C.byref(self.ptr)))

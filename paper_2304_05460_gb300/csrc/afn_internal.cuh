@@ -90,6 +90,7 @@ struct Handle {
     int d = 0, dp = 0, w = 0, w_req = 1, kernel = 0, precision = 0;
     double l = 1, mu = 1;
     int64_t rank_r = 0; int rank_branch = -1;
+    double rho32 = 0;     // AFN_PREC_AUTO: 2^-24 max row sum of K / mu
     double build_ms = 0;
 
     // permuted points
@@ -126,11 +127,16 @@ afn_status sync_status(Handle *h, const char *what);   // sync + read device sta
 
 // pointer kind
 bool is_device_ptr(const void *p);
+// AFN_PREC_AUTO threshold on rho (AFN_AUTO_RHO in the environment, default 0.3)
+double auto_rho_limit();
 
 // the body of afn_build: validate, build on stream s, return a new handle
 afn_status create_handle(const double *points, int64_t n, int d, int kernel, double l, double mu,
                          int k_max, int fsai_nnz, const afn_options &o, cudaStream_t s,
                          Handle **out);
+// afn_solve on device data in original order (permute, PCG, scatter)
+afn_status solve_handle(Handle *h, const double *B0, int nrhs, double tol, double *x_dev,
+                        int32_t *iters, double *relres, int *outer, int *conv);
 // host or device input -> device pointer (copied into tmp when on the host)
 afn_status to_device(const double *src, int64_t count, DevBuf &tmp, const double **out,
                      cudaStream_t s);
@@ -165,6 +171,9 @@ afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu,
 size_t matvecdf_scratch(int64_t n, int nrhs);
 afn_status make_points_df(const double *X, int64_t n, int d, int ds, int kernel, double l,
                           float2 *Xd, cudaStream_t s);
+// max_i sum_j K(x_i, x_j) from the prescaled FP32 points (FP32 matvec of ones)
+afn_status kernel_row_sum_max(const float *Xs, int64_t n, int dp, int kernel, double *out,
+                              cudaStream_t s);
 // prescaled FP32 copy of FP64 points (n x d -> n x dp)
 afn_status make_points32(const double *X, int64_t n, int d, int dp, int kernel, double l,
                          float *Xs, cudaStream_t s);

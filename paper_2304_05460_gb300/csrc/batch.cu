@@ -676,10 +676,6 @@ afn_status afn_build_batched(const afn_system *systems, int32_t nsys, const afn_
     afn_options o;
     afn_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != AFN_PREC_MIXED) {
-        set_error("afn_build_batched: grouped solves run the mixed-precision path (precision = 1)");
-        return AFN_ERR_ARG;
-    }
     Batch *b = new Batch();
     cudaGetDevice(&b->dev);
     b->opt = o;
@@ -750,10 +746,36 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
     std::vector<int> conv(coff[ns], 0);
     std::vector<int32_t> it(coff[ns], 0);
     std::vector<double> rel(coff[ns], 0.0);
+    // systems whose handle is not mixed (DF or FP64, e.g. chosen by
+    // AFN_PREC_AUTO for a small mu) are solved one at a time on the build
+    // streams by host threads, overlapping the grouped solve of the others
+    std::vector<int> single;
+    for (int q = 0; q < ns; ++q)
+        if (b->h[q]->precision != AFN_PREC_MIXED) single.push_back(q);
+    std::vector<afn_status> sst(ns, AFN_OK);
+    std::vector<int> sconv(ns, 0);
+    std::atomic<int> snext{0};
+    auto solo = [&](int t) {
+        cudaSetDevice(b->dev);
+        for (;;) {
+            const int i = snext.fetch_add(1);
+            if (i >= (int)single.size()) return;
+            const int q = single[i];
+            Handle *h = b->h[q];
+            h->stream = b->bstreams[t % b->bstreams.size()];
+            int outer = 0;
+            sst[q] = solve_handle(h, R + off[q], nrhs[q], tol, X + off[q], it.data() + coff[q],
+                                  rel.data() + coff[q], &outer, &sconv[q]);
+        }
+    };
+    std::vector<std::thread> pool;
+    const int nsolo = std::min<int>((int)single.size(), (int)b->bstreams.size());
+    for (int t = 0; t < nsolo; ++t) pool.emplace_back(solo, t);
     {
         std::vector<Member> mem(ns);
         Group g(s, chunk, tol, delta, maxit);
-        for (int q = 0; q < ns && st == AFN_OK; ++q) st = g.add(&mem[q], b->h[q], R + off[q], nrhs[q]);
+        for (int q = 0; q < ns && st == AFN_OK; ++q)
+            if (b->h[q]->precision == AFN_PREC_MIXED) st = g.add(&mem[q], b->h[q], R + off[q], nrhs[q]);
         // every column stops by max_iter (a forced replacement), so the loop
         // ends; the bound below only guards against a logic error
         const int cap = (maxit + chunk) / chunk + 4;
@@ -768,8 +790,14 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
             ++launches;
         }
         for (int q = 0; q < ns && st == AFN_OK; ++q)
-            st = g.collect(&mem[q], X + off[q], it.data() + coff[q], rel.data() + coff[q],
-                           conv.data() + coff[q]);
+            if (b->h[q]->precision == AFN_PREC_MIXED)
+                st = g.collect(&mem[q], X + off[q], it.data() + coff[q], rel.data() + coff[q],
+                               conv.data() + coff[q]);
+        for (auto &th : pool) th.join();
+        for (int q : single) {
+            for (int c = 0; c < nrhs[q]; ++c) conv[coff[q] + c] = rel[coff[q] + c] <= tol ? 1 : 0;
+            if (st == AFN_OK && sst[q] != AFN_OK && sst[q] != AFN_ERR_NO_CONVERGE) st = sst[q];
+        }
         if (st == AFN_OK && !xdev)
             st = cudaMemcpyAsync(x_out, X, sizeof(double) * tot, cudaMemcpyDeviceToHost, s) == cudaSuccess
                      ? AFN_OK : cuda_fail(cudaGetLastError(), "copy x_out");

@@ -162,6 +162,13 @@ int64_t Handle::device_bytes() const
     return s;
 }
 
+double auto_rho_limit()
+{
+    const char *e = getenv("AFN_AUTO_RHO");
+    const double v = e ? atof(e) : 0.0;
+    return v > 0.0 ? v : 0.3;
+}
+
 bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -348,12 +355,24 @@ static afn_status build_impl(Handle *h, const double *points)
     AFN_TRY(gather_points(X0, h->perm.as<int64_t>(), n, d, h->X64.as<double>(), s));
     const double *Xk = h->X64.as<double>();
     const double *Xr = Xk + k * d;
-    const bool mixed = h->precision == AFN_PREC_MIXED;
     h->dp = pad_dim(d);
-    if (mixed) {
-        int ds = stored_dim32(h->dp);
+    const int ds = stored_dim32(h->dp);
+    if (h->precision == AFN_PREC_MIXED || h->precision == AFN_PREC_AUTO) {
         AFN_TRY(h->X32.alloc(sizeof(float) * (size_t)(n * ds)));
         AFN_TRY(make_points32(h->X64.as<double>(), n, d, h->dp, h->kernel, h->l, h->X32.as<float>(), s));
+    }
+    if (h->precision == AFN_PREC_AUTO) {
+        // the FP32 matvec errs by about 2^-24 sum_j K_ij |p_j|; next to mu |p_i|
+        // that is at most rho = 2^-24 max_i sum_j K_ij / mu (Gershgorin bound
+        // of ||K||_2 for a non-negative K)
+        double rmax = 0.0;
+        AFN_TRY(kernel_row_sum_max(h->X32.as<float>(), n, h->dp, h->kernel, &rmax, s));
+        h->rho32 = rmax * 0x1p-24 / h->mu;
+        h->precision = h->rho32 <= auto_rho_limit() ? AFN_PREC_MIXED : AFN_PREC_DF;
+        if (h->precision != AFN_PREC_MIXED) h->X32.release();
+    }
+    const bool mixed = h->precision == AFN_PREC_MIXED;
+    if (mixed || h->precision == AFN_PREC_DF) {
         AFN_TRY(h->Xdf.alloc(sizeof(float2) * (size_t)(n * ds)));
         AFN_TRY(make_points_df(h->X64.as<double>(), n, d, ds, h->kernel, h->l, h->Xdf.as<float2>(), s));
     }
@@ -384,7 +403,6 @@ static afn_status build_impl(Handle *h, const double *points)
             AFN_TRY(h->LinvT32.alloc(sizeof(float) * (size_t)(k * k)));
             AFN_TRY(tri_inverse32(L32.as<float>(), k, h->Linv32.as<float>(), h->LinvT32.as<float>(), s));
             if (nr > 0) {
-                int ds = stored_dim32(h->dp);
                 AFN_TRY(h->Wt32.alloc(sizeof(float) * (size_t)(nr * k)));
                 const float *X32 = h->X32.as<float>();
                 AFN_TRY(kernel_block32(X32 + k * ds, nr, X32, k, h->dp, h->kernel, h->Wt32.as<float>(), k, s));
@@ -438,7 +456,10 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
                   (long long)n, d, kernel, l, mu, k_max, fsai_nnz);
         return AFN_ERR_ARG;
     }
-    if (o.precision != 0 && o.precision != 1) { set_error("bad precision"); return AFN_ERR_ARG; }
+    if (o.precision < AFN_PREC_FP64 || o.precision > AFN_PREC_AUTO) {
+        set_error("bad precision %d", o.precision);
+        return AFN_ERR_ARG;
+    }
     Handle *h = new Handle();
     cudaGetDevice(&h->dev);
     h->opt = o;
@@ -475,6 +496,29 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
     }
     *out = h;
     return AFN_OK;
+}
+
+// The body of afn_solve on device data: B0 (n x nrhs, original order) is
+// permuted, solved by pcg_solve on the handle's stream and x scattered back
+// into x_dev (original order).  Synchronises the handle's stream.
+afn_status solve_handle(Handle *h, const double *B0, int nrhs, double tol, double *x_dev,
+                        int32_t *iters, double *relres, int *outer, int *conv)
+{
+    cudaStream_t s = h->stream;
+    StreamGuard sg(s);
+    const int64_t n = h->n, tot = n * nrhs;
+    DevBuf bp, xp;
+    AFN_TRY(bp.alloc(sizeof(double) * tot));
+    AFN_TRY(xp.alloc(sizeof(double) * tot));
+    gather_cols(B0, h->perm.as<int64_t>(), n, nrhs, bp.as<double>(), s);
+    afn_status st = pcg_solve(h, bp.as<double>(), nrhs, tol, xp.as<double>(), iters, relres, outer,
+                              conv);
+    if (st == AFN_OK || st == AFN_ERR_NO_CONVERGE) {
+        scatter_cols(xp.as<double>(), h->perm.as<int64_t>(), n, nrhs, x_dev, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "solve");
+    }
+    return st;
 }
 
 }  // namespace afn
@@ -575,39 +619,23 @@ afn_status afn_solve(afn_handle *hh, const double *rhs, int32_t nrhs, double tol
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    DevBuf bin, bp, xp, xo;
+    DevBuf bin, xo;
     const double *B0 = nullptr;
     afn_status st = to_device(rhs, tot, bin, &B0, s);
     if (st == AFN_OK) st = check_finite(B0, tot, h->status.as<int>() + 2, s, "rhs");
-    if (st == AFN_OK) st = bp.alloc(sizeof(double) * tot);
-    if (st == AFN_OK) st = xp.alloc(sizeof(double) * tot);
     std::vector<int32_t> its(nrhs, 0);
     std::vector<double> rel(nrhs, 0.0);
     int outer = 0, conv = 0;
-    if (st == AFN_OK) {
-        gather_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B0, h->perm.as<int64_t>(), n,
-                                                                         nrhs, bp.as<double>());
-        st = pcg_solve(h, bp.as<double>(), nrhs, tol, xp.as<double>(), its.data(), rel.data(),
-                       &outer, &conv);
+    const bool dev = is_device_ptr(x_out);
+    double *dst = x_out;
+    if (st == AFN_OK && !dev) {
+        st = xo.alloc(sizeof(double) * tot);
+        dst = xo.as<double>();
     }
-    if (st == AFN_OK || st == AFN_ERR_NO_CONVERGE) {
-        afn_status st2 = AFN_OK;
-        bool dev = is_device_ptr(x_out);
-        double *dst = x_out;
-        if (!dev) {
-            st2 = xo.alloc(sizeof(double) * tot);
-            dst = xo.as<double>();
-        }
-        if (st2 == AFN_OK) {
-            scatter_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-                xp.as<double>(), h->perm.as<int64_t>(), n, nrhs, dst);
-            if (!dev) {
-                cudaError_t e = cudaMemcpyAsync(x_out, dst, sizeof(double) * tot,
-                                                cudaMemcpyDeviceToHost, s);
-                if (e != cudaSuccess) st2 = cuda_fail(e, "copy x_out");
-            }
-        }
-        if (st2 != AFN_OK) st = st2;
+    if (st == AFN_OK) st = solve_handle(h, B0, nrhs, tol, dst, its.data(), rel.data(), &outer, &conv);
+    if ((st == AFN_OK || st == AFN_ERR_NO_CONVERGE) && !dev) {
+        cudaError_t e = cudaMemcpyAsync(x_out, dst, sizeof(double) * tot, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy x_out");
     }
     cudaEventRecord(e1, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -646,6 +674,7 @@ afn_status afn_get_build_info(const afn_handle *hh, afn_build_info *info)
     info->mu = h->mu;
     info->build_ms = h->build_ms;
     info->device_bytes = h->device_bytes();
+    info->rho32 = h->rho32;
     return AFN_OK;
 }
 

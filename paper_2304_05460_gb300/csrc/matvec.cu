@@ -10,6 +10,7 @@
 // order and each (row tile, j-chunk) CTA writes one partial; a second kernel
 // sums the chunks in order and adds mu p.  The result is deterministic.
 #include <algorithm>
+#include <cstring>
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
@@ -647,6 +648,14 @@ __device__ __forceinline__ void mvdf_rows(const float2 *__restrict__ Xd, int64_t
                 Cc[c] = __fadd_rn(Cc[c], __fadd_rn(t, e));
             }
         }
+        // renormalise so the correction term stays small next to the sum
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            float h, l;
+            two_sum(S[c], Cc[c], h, l);
+            S[c] = h;
+            Cc[c] = l;
+        }
     }
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[c] = (double)S[c] + (double)Cc[c];
@@ -760,6 +769,45 @@ afn_status make_points_df(const double *X, int64_t n, int d, int ds, int kernel,
     points_df_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, n, d, ds, scale, Xd);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "points_df launch");
+    return AFN_OK;
+}
+
+// ----------------------------------------------- row sums of the kernel --
+__global__ void fill_ones_kernel(float *p, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 1.f;
+}
+
+__global__ void max_kernel(const float *q, int64_t n, unsigned int *out)
+{
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, q[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // m >= 0
+}
+
+afn_status kernel_row_sum_max(const float *Xs, int64_t n, int dp, int kernel, double *out,
+                              cudaStream_t s)
+{
+    DevBuf buf, scratch;
+    const size_t sb = matvec32_scratch(n, 1);
+    AFN_TRY(buf.alloc(sizeof(float) * 2 * (size_t)n + 256));
+    AFN_TRY(scratch.alloc(sb));
+    float *p = buf.as<float>(), *q = p + n;
+    unsigned int *mx = reinterpret_cast<unsigned int *>(q + n);
+    fill_ones_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n);
+    AFN_TRY(matvec32(Xs, n, dp, kernel, 0.f, p, 1, q, scratch.p, sb, s));
+    AFN_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
+    max_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(q, n, mx);
+    unsigned int bits = 0;
+    AFN_CUDA(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    AFN_CUDA(cudaStreamSynchronize(s));
+    float v;
+    memcpy(&v, &bits, sizeof(v));
+    *out = (double)v;
     return AFN_OK;
 }
 

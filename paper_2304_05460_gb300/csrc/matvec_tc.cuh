@@ -131,11 +131,19 @@ __device__ __forceinline__ void mv32tc_rows(const float *__restrict__ Xs, int64_
             const f2_t *xa = xsd + (kb * 8 + t) * DSP;
             const f2_t *xb = xsd + (kb * 8 + t + 4) * DSP;
             f2_t ra = 0ull, rb = 0ull;
+            // two coordinates per 16-byte shared-memory load (rows are
+            // 16-byte aligned: DSP is even), half the wavefronts of 8-byte loads
 #pragma unroll
-            for (int q = 0; q < DS; ++q) {
-                f2_t u = f2_sub(xi[q], xa[q]);
+            for (int q = 0; q < DS; q += 2) {
+                const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(xa + q);
+                const ulonglong2 vb = *reinterpret_cast<const ulonglong2 *>(xb + q);
+                f2_t u = f2_sub(xi[q], va.x);
                 ra = f2_fma(u, u, ra);
-                u = f2_sub(xi[q], xb[q]);
+                u = f2_sub(xi[q], vb.x);
+                rb = f2_fma(u, u, rb);
+                u = f2_sub(xi[q + 1], va.y);
+                ra = f2_fma(u, u, ra);
+                u = f2_sub(xi[q + 1], vb.y);
                 rb = f2_fma(u, u, rb);
             }
             float r_aa, r_ba, r_ab, r_bb;   // (row ia|ib, column t|t+4)

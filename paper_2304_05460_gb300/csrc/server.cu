@@ -57,15 +57,16 @@ struct Request {
 
 // device bytes a request holds while admitted: its factors (mixed handle),
 // the largest build temporaries and its grouped-solve workspace
-static int64_t footprint(int64_t n, int d, int64_t kmax, int w, int nrhs)
+static int64_t footprint(int64_t n, int d, int64_t kmax, int w, int nrhs, bool wide)
 {
+    const int64_t fw = wide ? 8 : 4;                      // factor element bytes
     const int64_t k = std::min<int64_t>(kmax, n), nr = n - k;
     const int64_t ww = std::max<int64_t>(1, std::min<int64_t>(w, std::max<int64_t>(nr, 1)));
     const int ds = d <= 4 ? 4 : (d <= 8 ? 8 : 16);
     int64_t b = 0;
     b += n * 8 + n * d * 8 + n * ds * 4;                  // perm, X64, X32
-    b += k * k * 8 + 2 * k * k * 4;                      // L, L^{-1}, L^{-T} (FP32)
-    b += nr * k * 4;                                      // W^T (FP32)
+    b += k * k * 8 + 2 * k * k * fw;                     // L, L^{-1}, L^{-T}
+    b += nr * k * fw;                                     // W^T
     b += nr * ww * (4 + 8 + 4) + (nr + 1 + 2 * nr * ww) * 4;   // pattern, G, G32, G^T lists
     b += k * k * 4 + n * d * 8 + nr * ww * 8 * 4;         // build temporaries (L32, input, FSAI)
     const int C = (nrhs + GC - 1) / GC * GC;
@@ -136,6 +137,40 @@ void Server::build_loop(int t)
                 if (e != cudaSuccess) st = cuda_fail(e, "request rhs upload");
             }
             if (st != AFN_OK) err = afn_last_error();
+        }
+        if (st == AFN_OK && h->precision != AFN_PREC_MIXED) {
+            // a DF (or FP64) request -- AFN_PREC_AUTO's choice for a small mu --
+            // is solved here, on this thread's stream, beside the running group
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                r->t_built = Clock::now();
+                r->build_ms = ms_since(t0, r->t_built);
+                r->t_join = r->t_built;
+                r->h = h;
+            }
+            StreamGuard sg(s);
+            DevBuf xd;
+            r->iters.assign(r->nrhs, 0);
+            r->relres.assign(r->nrhs, 0.0);
+            int outer = 0, conv = 0;
+            st = xd.alloc(sizeof(double) * r->sys.n * r->nrhs);
+            if (st == AFN_OK)
+                st = solve_handle(h, r->bdev.as<double>(), r->nrhs, r->tol, xd.as<double>(),
+                                  r->iters.data(), r->relres.data(), &outer, &conv);
+            if (st == AFN_OK || st == AFN_ERR_NO_CONVERGE) {
+                r->x.resize((size_t)r->sys.n * r->nrhs);
+                cudaError_t e = cudaMemcpyAsync(r->x.data(), xd.p, sizeof(double) * r->x.size(),
+                                                cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) st = cuda_fail(e, "request result copy");
+            }
+            r->converged = conv;
+            r->status = st;
+            r->error = st == AFN_OK ? "" : (st == AFN_ERR_NO_CONVERGE ? "some columns missed tol"
+                                                                     : afn_last_error());
+            r->state = RQ_READY;
+            finish(r, nullptr);
+            continue;
         }
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -301,7 +336,7 @@ void afn_server_default_config(afn_server_config *c)
     if (!c) return;
     memset(c, 0, sizeof(*c));
     afn_default_options(&c->opt);
-    c->opt.precision = AFN_PREC_MIXED;
+    c->opt.precision = AFN_PREC_AUTO;
     c->build_threads = 8;
 }
 
@@ -312,8 +347,8 @@ afn_status afn_server_create(const afn_server_config *cfg, afn_server **out)
     afn_server_config c;
     afn_server_default_config(&c);
     if (cfg) c = *cfg;
-    if (c.opt.precision != AFN_PREC_MIXED) {
-        set_error("afn_server_create: the serving loop runs the mixed-precision path (opt.precision = 1)");
+    if (c.opt.precision < AFN_PREC_FP64 || c.opt.precision > AFN_PREC_AUTO) {
+        set_error("afn_server_create: bad precision %d", c.opt.precision);
         return AFN_ERR_ARG;
     }
     if (c.memory_budget < 0 || c.max_active < 0 || c.build_threads < 0) {
@@ -377,7 +412,8 @@ afn_status afn_server_submit(afn_server *ss, const afn_system *sys, const double
     for (double v : r->B)
         if (!std::isfinite(v)) { delete r; set_error("afn_server_submit: rhs contains NaN or Inf"); return AFN_ERR_ARG; }
     r->sys.points = r->X.data();
-    r->bytes = footprint(sys->n, sys->d, sys->k_max, sys->fsai_nnz, nrhs);
+    r->bytes = footprint(sys->n, sys->d, sys->k_max, sys->fsai_nnz, nrhs,
+                         s->opt.precision != AFN_PREC_MIXED);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -452,8 +488,9 @@ afn_status afn_server_result(afn_server *ss, int64_t id, double *x_out, int32_t 
         info->nrhs = r->nrhs;
         info->queue_ms = ms_since(r->t_submit, r->t_admit);
         info->build_ms = r->build_ms;
-        info->wait_ms = r->state == RQ_DONE && r->t_join > r->t_built ? ms_since(r->t_built, r->t_join) : 0.0;
-        info->solve_ms = r->t_join > r->t_built ? ms_since(r->t_join, r->t_done) : 0.0;
+        const bool joined = r->t_join.time_since_epoch().count() != 0;
+        info->wait_ms = joined ? ms_since(r->t_built, r->t_join) : 0.0;
+        info->solve_ms = joined ? ms_since(r->t_join, r->t_done) : 0.0;
         info->latency_ms = ms_since(r->t_submit, r->t_done);
         info->device_bytes = r->bytes;
     }

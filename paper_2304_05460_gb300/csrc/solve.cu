@@ -267,9 +267,13 @@ static afn_status get_work(Handle *h, int nrhs, Work &wk)
     wk.mv_bytes = mvb;
     wk.mv32 = mixed ? carve<char>(p, mv32b) : nullptr;
     wk.mv32_bytes = mv32b;
+    char *c0 = p;
     carve_cols(p, nrhs, wk.cs);
     carve_cols(p, nrhs, wk.cs_out);
     wk.rn = carve<double>(p, nrhs);
+    // the dot kernels' arrival counters (and every column field) start at
+    // zero; pooled memory is reused, so clear it
+    AFN_CUDA(cudaMemsetAsync(c0, 0, (size_t)(p - c0), h->stream));
     return AFN_OK;
 }
 

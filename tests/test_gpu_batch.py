@@ -81,7 +81,8 @@ def test_batched_mix_reaches_tol(afn):
 def test_batched_matches_single_mixed(afn):
     mix = make_mix()[:6]
     tol = 1e-6
-    b = afn.afn_build_batched([m[0] for m in mix], seed=5, max_iter=2000)
+    b = afn.afn_build_batched([m[0] for m in mix], seed=5, max_iter=2000,
+                              precision=afn.PREC_MIXED)
     xs, info = afn.afn_solve_batched(b, [m[1] for m in mix], tol)
     for s, (sy, B) in enumerate(mix):
         h = afn.afn_build(sy["points"], sy["kernel"], sy["l"], sy["mu"], sy["k_max"],
@@ -132,7 +133,7 @@ def test_batched_zero_column_and_device_memory(afn):
 def test_batched_rejects_bad_input(afn):
     sy, B = system(300, 3, G, 1.0, 1e-2, 2, 41)
     with pytest.raises(afn.AfnError) as e:
-        afn.afn_build_batched([sy], precision=afn.PREC_FP64)
+        afn.afn_build_batched([sy], precision=7)
     assert e.value.status == afn.AFN_ERR_ARG
     bad = dict(sy, mu=-1.0)
     with pytest.raises(afn.AfnError) as e:
@@ -161,3 +162,21 @@ def test_batched_512_workload_sample(afn):
     for s, sy in enumerate(sys_args):
         if sy["points"].shape[0] <= 3000:
             check_residuals(sy, np.asarray(xs[s]), systems[s].B, tol)
+
+
+def test_auto_precision_routes_small_mu(afn):
+    """AFN_PREC_AUTO sends a system whose FP32 matvec error would swamp mu
+    (mu = 1e-4, length-scale 4x the median distance) to the DF path (FP64 PCG,
+    double-float matvec) and keeps the easy ones mixed; both reach tol in one
+    batched call, and the DF system needs few iterations."""
+    hard, Bh = system(2500, 8, G, 4.0, 1e-4, 8, 51)
+    easy, Be = system(1200, 5, M32, 0.7, 1e-2, 8, 52)
+    b = afn.afn_build_batched([hard, easy], seed=5, max_iter=2000)
+    ih, ie = afn.afn_batch_build_info(b, 0), afn.afn_batch_build_info(b, 1)
+    assert ih.precision == afn.PREC_DF and ih.rho32 > 0.3
+    assert ie.precision == afn.PREC_MIXED and 0 < ie.rho32 <= 0.3
+    xs, info = afn.afn_solve_batched(b, [Bh, Be], 1e-6)
+    assert info["status"] == afn.AFN_OK
+    check_residuals(hard, np.asarray(xs[0]), Bh, 1e-6)
+    check_residuals(easy, np.asarray(xs[1]), Be, 1e-6)
+    assert info["iters"][0].max() < 200

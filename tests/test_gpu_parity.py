@@ -211,6 +211,22 @@ def test_solve_fp64_uniform_cube(afn):
     afn.afn_free(h)
 
 
+def test_solve_df_uniform_cube(afn):
+    """The DF precision (FP64 PCG, factors and apply; double-float matvec on
+    the FP32 pipes) follows the FP64 oracle like the FP64 path: residual <=
+    tol, iterations within +-2."""
+    s = inputs.uniform_cube_3d()
+    ref = oracle.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w)
+    xr, itr, relr, str_ = oracle.pcg(ref, s.B[:, 0], 1e-6)
+    h = afn.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w, precision=afn.PREC_DF)
+    assert afn.afn_get_build_info(h).precision == afn.PREC_DF
+    x, info = afn.afn_solve(h, s.B, 1e-6)
+    rel = oracle.true_relres(s.X, s.kernel, s.l, s.mu, x, s.B)
+    assert rel.max() <= 1e-6
+    assert abs(int(info["iters"][0]) - itr) <= 2, (info["iters"], itr)
+    afn.afn_free(h)
+
+
 @pytest.mark.parametrize("ker,nrhs", [(G, 1), (M32, 5), (G, 33)])
 def test_solve_fp64_and_mixed_multi_rhs(afn, ker, nrhs):
     X = inputs.uniform_points(1500, 3, 800 + nrhs)
