@@ -268,6 +268,10 @@ typedef struct {
     int32_t graph_launches; /* CUDA graph launches (opt.check_every iterations each) */
     int32_t iters_max;      /* largest per-column iteration count */
     double solve_ms;        /* device time of the whole solve */
+    double group_ms;        /* host wall time until the grouped (mixed) systems finished */
+    double single_ms;       /* host wall time until the last one-at-a-time (DF) system finished */
+    int32_t single_systems; /* systems solved one at a time (precision other than MIXED) */
+    int32_t pad_;
 } afn_batch_solve_info;
 
 /*

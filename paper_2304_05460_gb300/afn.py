@@ -62,7 +62,8 @@ class afn_system(C.Structure):
 
 class afn_batch_solve_info(C.Structure):
     _fields_ = [("converged", C.c_int32), ("columns", C.c_int32), ("graph_launches", C.c_int32),
-                ("iters_max", C.c_int32), ("solve_ms", C.c_double)]
+                ("iters_max", C.c_int32), ("solve_ms", C.c_double), ("group_ms", C.c_double),
+                ("single_ms", C.c_double), ("single_systems", C.c_int32), ("pad_", C.c_int32)]
 
 
 def _load():
@@ -469,7 +470,8 @@ def afn_solve_batched(b: Batch, rhs, tol):
         c += m
     return xs, dict(iters=iters, relres=relres, converged=info.converged, columns=info.columns,
                     graph_launches=info.graph_launches, iters_max=info.iters_max,
-                    solve_ms=info.solve_ms, status=st)
+                    solve_ms=info.solve_ms, group_ms=info.group_ms, single_ms=info.single_ms,
+                    single_systems=info.single_systems, status=st)
 
 
 # ----------------------------------------------------------------- serving --

@@ -160,7 +160,8 @@ afn_status matvec64(const double *X, int64_t n, int d, KParams kp, const double 
                     double *q, void *scratch, size_t scratch_bytes, cudaStream_t s);
 size_t matvec64_scratch(int64_t n, int nrhs);
 afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, const float *p,
-                    int nrhs, float *q, void *scratch, size_t scratch_bytes, cudaStream_t s);
+                    int nrhs, float *q, void *scratch, size_t scratch_bytes, int *err,
+                    cudaStream_t s);   // err: device word set to DEV_TIMEOUT if a staged copy stalls
 size_t matvec32_scratch(int64_t n, int nrhs);
 int pad_dim(int d);
 int stored_dim32(int dp);
@@ -225,10 +226,16 @@ size_t apply_tmp_elems(const Handle *h, int nrhs);
 
 // ---- grouped steps (many systems per launch; group.cuh describes the group)
 struct GDev;
-afn_status group_matvec32(const GDev *gd, cudaStream_t s);
-afn_status group_matvec64(const GDev *gd, cudaStream_t s);
-afn_status group_apply(const GDev *gd, cudaStream_t s);
+// share: fraction of each SM's CTA slots the persistent grids take (1 = all;
+// less leaves room for work on other streams, e.g. the server's builds)
+afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share);
+afn_status group_matvec64(const GDev *gd, cudaStream_t s, double share);
+afn_status group_apply(const GDev *gd, cudaStream_t s, double share);
+int persistent_grid(int ctas_per_sm, double share);   // max(1, SMs x ctas_per_sm x share)
 int group_mv32_rows();      // rows per tile of the grouped FP32 matvec
+int group_npad(int64_t n);  // n rounded up to the staged point tile
+// duplicated (x, x) FP32 pairs of the prescaled points, ds + 2 per row, npad rows
+void dup_points(const float *Xs, int64_t n, int ds, int64_t npad, void *Xdup, cudaStream_t s);
 int group_mv64_rows();      // rows per tile of the grouped FP64 matvec
 int group_block_rows();     // rows per block of the grouped dense products
 int group_sparse_rows();    // rows per block of the grouped sparse products

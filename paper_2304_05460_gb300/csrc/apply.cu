@@ -635,9 +635,9 @@ static int sm_count()
 int group_sparse_rows() { return 256 / GC; }
 int group_block_rows() { return GM; }
 
-afn_status group_apply(const GDev *gd, cudaStream_t s)
+afn_status group_apply(const GDev *gd, cudaStream_t s, double share)
 {
-    const int g = sm_count() * 4;
+    const int g = persistent_grid(4, share);
     gap_gemm_kernel<0><<<g, 256, 0, s>>>(gd);
     gap_gemm_kernel<1><<<g, 256, 0, s>>>(gd);
     gap_sparse_kernel<0><<<g, 256, 0, s>>>(gd);

@@ -27,6 +27,7 @@
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
 #include "engine.cuh"
+#include "matvec_tc.cuh"
 
 namespace afn {
 
@@ -62,11 +63,20 @@ __global__ void __launch_bounds__(CB) gbeta_kernel(const GDev *__restrict__ gd)
         const int64_t n = S.n, off = (int64_t)sc.y * n;
         const float *r = S.r32 + off, *z = S.z32 + off;
         float *p = S.p32 + off;
+        // the tf32 (hi, lo) split of p, staged by the grouped matvec
+        uint32_t *psp = S.Psp + (int64_t)(sc.y / GC) * S.npad * TcRow<1>::ROW + sc.y % GC;
         double acc = 0.0;
         for (int64_t i = threadIdx.x; i < n; i += CB) acc += (double)r[i] * (double)z[i];
         const double v = block_total(acc, red);
         const float be = first ? 0.f : (float)(v / rho);
-        for (int64_t i = threadIdx.x; i < n; i += CB) p[i] = first ? z[i] : z[i] + be * p[i];
+        for (int64_t i = threadIdx.x; i < n; i += CB) {
+            const float pv = first ? z[i] : z[i] + be * p[i];
+            p[i] = pv;
+            uint32_t hi, lo;
+            tf32_split(pv, hi, lo);
+            psp[i * TcRow<1>::ROW] = hi;
+            psp[i * TcRow<1>::ROW + TcRow<1>::PS] = lo;
+        }
         if (threadIdx.x == 0) {
             if (!first) cs.beta = v / rho;
             cs.rho = v;
@@ -261,10 +271,10 @@ static size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 static constexpr int64_t KCH = 2048;   // rows of W^T per split-K chunk
 
 struct WsLayout {
-    size_t b, x, q, x32, r32, q32, z32, p32, zp, u, t, y, part, cs, total;
+    size_t b, x, q, x32, r32, q32, z32, p32, zp, u, t, y, part, cs, xdup, psp, total;
 };
 
-static WsLayout layout(int64_t n, int64_t k, int64_t nr, int C, int js)
+static WsLayout layout(int64_t n, int64_t k, int64_t nr, int C, int js, int ds)
 {
     WsLayout L{};
     size_t o = 0;
@@ -284,6 +294,9 @@ static WsLayout layout(int64_t n, int64_t k, int64_t nr, int C, int js)
     L.y = put(sizeof(float) * (size_t)nr * C);
     L.part = put(sizeof(float) * (size_t)js * C * (size_t)k);
     L.cs = put(sizeof(GCol) * (size_t)C);
+    const size_t np = (size_t)group_npad(n);
+    L.xdup = put(sizeof(unsigned long long) * np * (size_t)(ds + 2));
+    L.psp = put(sizeof(uint32_t) * (size_t)(C / GC) * np * TcRow<1>::ROW);
     L.total = o;
     return L;
 }
@@ -292,11 +305,12 @@ size_t Group::workspace_bytes(const Handle *h, int nrhs)
 {
     const int ncg = (nrhs + GC - 1) / GC;
     const int js = h->nr > 0 ? (int)((h->nr + KCH - 1) / KCH) : 0;
-    return layout(h->n, h->k, h->nr, ncg * GC, js).total;
+    return layout(h->n, h->k, h->nr, ncg * GC, js, stored_dim32(h->dp)).total;
 }
 
-Group::Group(cudaStream_t s, int chunk, double tol, double delta, int maxit)
-    : strm_(s), chunk_(std::max(1, chunk)), tol_(tol), delta_(delta), maxit_(maxit)
+Group::Group(cudaStream_t s, int chunk, double tol, double delta, int maxit, double share)
+    : strm_(s), chunk_(std::max(1, chunk)), tol_(tol), delta_(delta), maxit_(maxit),
+      share_(share > 0 && share <= 1 ? share : 1.0)
 {
 }
 
@@ -319,7 +333,7 @@ afn_status Group::add(Member *m, Handle *h, const double *b_dev, int nrhs)
     const int C = m->ncg * GC;
     m->kch = KCH;
     m->js = h->nr > 0 ? (int)((h->nr + KCH - 1) / KCH) : 0;
-    const WsLayout L = layout(h->n, h->k, h->nr, C, m->js);
+    const WsLayout L = layout(h->n, h->k, h->nr, C, m->js, stored_dim32(h->dp));
     AFN_TRY(m->ws.alloc(L.total));
     AFN_CUDA(cudaMemsetAsync(m->ws.p, 0, L.total, strm_));
     char *base = static_cast<char *>(m->ws.p);
@@ -364,6 +378,10 @@ afn_status Group::add(Member *m, Handle *h, const double *b_dev, int nrhs)
     g.y = reinterpret_cast<float *>(base + L.y);
     g.part = reinterpret_cast<float *>(base + L.part);
     g.cs = reinterpret_cast<GCol *>(base + L.cs);
+    g.npad = group_npad(h->n);
+    g.Xdup = reinterpret_cast<const unsigned long long *>(base + L.xdup);
+    g.Psp = reinterpret_cast<uint32_t *>(base + L.psp);
+    dup_points(h->X32.as<float>(), h->n, g.ds, g.npad, base + L.xdup, strm_);
     gather_cols(b_dev, h->perm.as<int64_t>(), h->n, nrhs, g.b, strm_);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "grouped solve: gather rhs");
@@ -458,7 +476,10 @@ afn_status Group::upload()
     AFN_TRY(ensure<int2>(cols_, hcols_.size()));
     AFN_TRY(ensure<int2>(init_, hinit_.size()));
     if (!rep_.p) AFN_TRY(rep_.alloc(sizeof(int) * MAX_SYS));
-    if (!nact_.p) AFN_TRY(nact_.alloc(sizeof(int) * MAX_SYS));
+    if (!nact_.p) {
+        AFN_TRY(nact_.alloc(sizeof(int) * (MAX_SYS + 1)));   // + the staging status word
+        AFN_CUDA(cudaMemsetAsync(nact_.p, 0, sizeof(int) * (MAX_SYS + 1), strm_));
+    }
     if (!gd_.p) AFN_TRY(gd_.alloc(sizeof(GDev)));
     if (!hsys_.empty())
         AFN_CUDA(cudaMemcpyAsync(sys_.p, hsys_.data(), sizeof(GSys) * hsys_.size(), cudaMemcpyHostToDevice, strm_));
@@ -481,6 +502,7 @@ afn_status Group::upload()
     h.ncol = (int)hcols_.size();
     h.rep = rep_.as<int>();
     h.nact = nact_.as<int>();
+    h.err = nact_.as<int>() + MAX_SYS;
     h.nsys = (int)hsys_.size();
     h.maxit = maxit_;
     h.tol = tol_;
@@ -494,15 +516,15 @@ afn_status Group::upload()
 afn_status Group::iteration()
 {
     const GDev *gd = gd_.as<GDev>();
-    const int gc = sms() * 8;
-    AFN_TRY(group_apply(gd, strm_));                       // z = M^{-1} r
+    const int gc = persistent_grid(8, share_);
+    AFN_TRY(group_apply(gd, strm_, share_));                       // z = M^{-1} r
     gbeta_kernel<<<gc, CB, 0, strm_>>>(gd);                // rho, beta, p
-    AFN_TRY(group_matvec32(gd, strm_));                    // q = (K + mu I) p
+    AFN_TRY(group_matvec32(gd, strm_, share_));                    // q = (K + mu I) p
     galpha_kernel<<<gc, CB, 0, strm_>>>(gd);
     gupdate_kernel<<<gc, CB, 0, strm_>>>(gd);              // x, r, reliable-update test
     grep_kernel<<<MAX_SYS / 256, 256, 0, strm_>>>(gd);
     gacc_kernel<<<gc, CB, 0, strm_>>>(gd);                 // x += dx on replaced systems
-    AFN_TRY(group_matvec64(gd, strm_));                    // q = (K + mu I) x in FP64
+    AFN_TRY(group_matvec64(gd, strm_, share_));                    // q = (K + mu I) x in FP64
     gresid_kernel<<<gc, CB, 0, strm_>>>(gd);               // r = b - q, FP64 test
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped iteration launch");
@@ -510,14 +532,14 @@ afn_status Group::iteration()
 
 afn_status Group::capture()
 {
-    if (!nact_host_) AFN_CUDA(cudaMallocHost(&nact_host_, sizeof(int) * MAX_SYS));
+    if (!nact_host_) AFN_CUDA(cudaMallocHost(&nact_host_, sizeof(int) * (MAX_SYS + 1)));
     const long long c0 = afn_launch_count();
     AFN_CUDA(cudaStreamBeginCapture(strm_, cudaStreamCaptureModeThreadLocal));
     afn_status st = AFN_OK;
     for (int it = 0; it < chunk_ && st == AFN_OK; ++it) st = iteration();
     if (st == AFN_OK) {
         gstatus_kernel<<<MAX_SYS / 256, 256, 0, strm_>>>(gd_.as<GDev>());
-        cudaError_t e = cudaMemcpyAsync(nact_host_, nact_.p, sizeof(int) * MAX_SYS,
+        cudaError_t e = cudaMemcpyAsync(nact_host_, nact_.p, sizeof(int) * (MAX_SYS + 1),
                                         cudaMemcpyDeviceToHost, strm_);
         if (e != cudaSuccess) st = cuda_fail(e, "grouped status copy");
     }
@@ -550,6 +572,10 @@ afn_status Group::step(std::vector<Member *> &finished)
     count_launches(kpg_);
     ++launches_;
     AFN_CUDA(cudaStreamSynchronize(strm_));
+    if (nact_host_[MAX_SYS]) {
+        set_error("grouped matvec: a staged tile copy did not complete in time");
+        return AFN_ERR_TIMEOUT;
+    }
     for (auto *m : mem_) {
         if (m->done || m->slot < 0) continue;
         if (nact_host_[m->slot] == 0) {
@@ -749,6 +775,9 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
     // systems whose handle is not mixed (DF or FP64, e.g. chosen by
     // AFN_PREC_AUTO for a small mu) are solved one at a time on the build
     // streams by host threads, overlapping the grouped solve of the others
+    double group_ms = 0;
+    const auto w0 = std::chrono::steady_clock::now();
+    std::atomic<long long> single_end_us{0};
     std::vector<int> single;
     for (int q = 0; q < ns; ++q)
         if (b->h[q]->precision != AFN_PREC_MIXED) single.push_back(q);
@@ -766,6 +795,11 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
             int outer = 0;
             sst[q] = solve_handle(h, R + off[q], nrhs[q], tol, X + off[q], it.data() + coff[q],
                                   rel.data() + coff[q], &outer, &sconv[q]);
+            const long long us = std::chrono::duration_cast<std::chrono::microseconds>(
+                                     std::chrono::steady_clock::now() - w0).count();
+            long long prev = single_end_us.load();
+            while (us > prev && !single_end_us.compare_exchange_weak(prev, us)) {
+            }
         }
     };
     std::vector<std::thread> pool;
@@ -789,6 +823,7 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
             st = g.step(fin);
             ++launches;
         }
+        group_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
         for (int q = 0; q < ns && st == AFN_OK; ++q)
             if (b->h[q]->precision == AFN_PREC_MIXED)
                 st = g.collect(&mem[q], X + off[q], it.data() + coff[q], rel.data() + coff[q],
@@ -823,6 +858,9 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
         info->graph_launches = launches;
         info->iters_max = imax;
         info->solve_ms = ms;
+        info->group_ms = group_ms;
+        info->single_ms = single_end_us.load() / 1e3;
+        info->single_systems = (int32_t)single.size();
     }
     if (nconv != coff[ns]) {
         set_error("afn_solve_batched: %d of %lld columns reached tol", nconv, (long long)coff[ns]);

@@ -817,10 +817,19 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
         AFN_TRY(convert64to32(P, p32.as<float>(), tot, s));
         size_t sb = matvec32_scratch(n, nrhs);
         AFN_TRY(scratch.alloc(sb));
+        DevBuf flag;
+        AFN_TRY(flag.alloc(sizeof(int)));
+        AFN_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
         AFN_TRY(matvec32(x32.as<float>(), n, dp, kernel, (float)mu, p32.as<float>(), nrhs,
-                         q32.as<float>(), scratch.p, sb, s));
+                         q32.as<float>(), scratch.p, sb, flag.as<int>(), s));
         AFN_TRY(convert32to64(q32.as<float>(), Q, tot, s));
+        int hf = 0;
+        AFN_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         AFN_CUDA(cudaStreamSynchronize(s));
+        if (hf) {
+            set_error("afn_kernel_matvec: a staged tile copy did not complete in time");
+            return AFN_ERR_TIMEOUT;
+        }
     }
     if (!qdev) AFN_CUDA(cudaMemcpyAsync(q, Q, sizeof(double) * tot, cudaMemcpyDeviceToHost, s));
     AFN_CUDA(cudaStreamSynchronize(s));

@@ -31,7 +31,8 @@ class Group {
 public:
     static constexpr int MAX_SYS = 1 << 16;
 
-    Group(cudaStream_t s, int chunk, double tol, double delta, int maxit);
+    // share: fraction of the GPU's CTA slots the persistent grids take
+    Group(cudaStream_t s, int chunk, double tol, double delta, int maxit, double share = 1.0);
     ~Group();
     Group(const Group &) = delete;
     Group &operator=(const Group &) = delete;
@@ -60,6 +61,7 @@ private:
     int chunk_;
     double tol_, delta_;
     int maxit_;
+    double share_;
     std::vector<Member *> mem_;
     bool dirty_ = true;
     // device buffers

@@ -25,6 +25,9 @@ struct GSys {                         // one member system
     const double *X64;                // n x d permuted points
     const float *X32;                 // n x ds prescaled points
     const float2 *Xdf;                // n x ds prescaled double-float points
+    const unsigned long long *Xdup;   // npad x (ds + 2) duplicated FP32 pairs (staged tiles)
+    uint32_t *Psp;                    // [ncg][npad][40] tf32 (hi, lo) split of p32 (staged tiles)
+    int npad;                         // n rounded up to the 64-point tile
     const float *Linv, *LinvT, *Wt, *G;
     const int32_t *pat, *gptr, *grow, *gslot;
     double *b, *x, *q;                // n x C column-major (C = GC * ncg)
@@ -50,6 +53,7 @@ struct GDev {                         // the group, as the kernels see it
     int2 *col;   int ncol;            // (system, column) of every real column
     int *rep;                         // per system: FP64 residual replacement now
     int *nact;                        // per system: active columns (status output)
+    int *err;                         // set when a staged copy did not complete in time
     int nsys;
     int maxit;
     double tol, delta;

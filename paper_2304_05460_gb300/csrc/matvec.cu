@@ -336,15 +336,108 @@ __global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MI
 }
 
 
+// The same CTA with TMA-staged, double-buffered tiles (mv32tc_rows_async)
+// read from the prepared Xdup / Psp arrays.
+template <int DS, int NB, int KER>
+__global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MINB : 2)
+    matvec32tca_kernel(const float *__restrict__ Xs, int64_t n, const f2_t *__restrict__ Xdup,
+                       const uint32_t *__restrict__ Psp, float *__restrict__ part, int64_t chunk,
+                       int *__restrict__ err)
+{
+    constexpr int NR = NB * 8;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ia = (int64_t)blockIdx.x * TCR + warp * 16 + g;
+    const int64_t ib = ia + 8;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk;
+    const int64_t j1 = min(n, j0 + chunk);
+    float acc[NB][4];
+    uint32_t parity = 0;
+    if (!mv32tc_rows_async<DS, NB, KER>(Xs, n, Xdup, Psp, (int64_t)blockIdx.x * TCR, j0, j1, dsm,
+                                        bars, parity, acc)) {
+        if (threadIdx.x == 0) atomicExch(err, DEV_TIMEOUT);
+        return;
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int c = b * 8 + 2 * t;
+        float *p0 = part + ((int64_t)blockIdx.y * NR + c) * n;
+        float *p1 = p0 + n;
+        if (ia < n) { p0[ia] = acc[b][0]; p1[ia] = acc[b][1]; }
+        if (ib < n) { p0[ib] = acc[b][2]; p1[ib] = acc[b][3]; }
+    }
+}
+
+// Xdup: rows of (x, x) pairs, DS + 2 per row, zero rows up to npad
+__global__ void dup_points_kernel(const float *__restrict__ Xs, int64_t n, int ds, int64_t npad,
+                                  f2_t *__restrict__ Xdup)
+{
+    const int dsp = ds + 2;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npad * dsp) return;
+    const int64_t j = e / dsp;
+    const int q = (int)(e % dsp);
+    const float v = (j < n && q < ds) ? Xs[j * ds + q] : 0.f;
+    Xdup[e] = f2_pack(v, v);
+}
+
+// Psp: row j = [tf32 hi of p(j, c), c < NR | pad | lo | pad], zero rows up to npad
+template <int NB>
+__global__ void psplit_kernel(const float *__restrict__ P, int64_t ldp, int64_t n, int64_t npad,
+                              uint32_t *__restrict__ Psp)
+{
+    constexpr int NR = NB * 8;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npad * NR) return;
+    const int64_t j = e % npad;
+    const int c = (int)(e / npad);
+    uint32_t hi, lo;
+    tf32_split(j < n ? P[c * ldp + j] : 0.f, hi, lo);
+    Psp[j * TcRow<NB>::ROW + c] = hi;
+    Psp[j * TcRow<NB>::ROW + TcRow<NB>::PS + c] = lo;
+}
+
+static int64_t tc_npad(int64_t n) { return (n + TCJ - 1) / TCJ * TCJ; }
+
 size_t matvec32_scratch(int64_t n, int nrhs)
 {
-    return sizeof(float) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 32) *
-               (size_t)n + 256;
+    const size_t part = sizeof(float) * (size_t)pick_js(n) *
+                        (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
+    const size_t np = (size_t)tc_npad(n);
+    const size_t dup = sizeof(f2_t) * np * 18;                     // DS + 2 <= 18
+    const size_t psp = sizeof(uint32_t) * np * TcRow<4>::ROW;
+    return (part + 255) / 256 * 256 + (dup + 255) / 256 * 256 + psp + 256;
 }
+
+template <int DS, int NB, int KER>
+static void launch_tca(const float *Xs, int64_t n, const f2_t *Xdup, const uint32_t *Psp,
+                       float *part, int js, int64_t chunk, int *err, cudaStream_t s)
+{
+    const int smem = 2 * TcStage<DS, NB>::BYTES;
+    cudaFuncSetAttribute(matvec32tca_kernel<DS, NB, KER>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 g((unsigned)((n + TCR - 1) / TCR), (unsigned)js);
+    matvec32tca_kernel<DS, NB, KER><<<g, 256, smem, s>>>(Xs, n, Xdup, Psp, part, chunk, err);
+}
+
+struct TcPrep {           // prepared operands of the asynchronous TC path
+    const f2_t *Xdup;
+    uint32_t *Psp;
+    int64_t npad;
+    int *err;
+};
 
 template <int D, int NR, int KER>
 static void launch32(const float *Xs, int64_t n, const float *P, float *part, int js,
-                     int64_t chunk, cudaStream_t s)
+                     int64_t chunk, const TcPrep &tp, cudaStream_t s)
 {
     dim3 grid((unsigned)((n + TI - 1) / TI), (unsigned)js);
 #ifdef AFN_NO_TC
@@ -353,8 +446,10 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
     constexpr bool use_tc = true;
 #endif
     if constexpr (NR >= 8 && use_tc) {
-        dim3 gtc((unsigned)((n + TCR - 1) / TCR), (unsigned)js);
-        matvec32tc_kernel<(D == 3 ? 4 : D), NR / 8, KER><<<gtc, 256, 0, s>>>(Xs, n, P, n, part, chunk);
+        constexpr int DS = (D == 3 ? 4 : D);
+        const int64_t tot = tp.npad * NR;
+        psplit_kernel<NR / 8><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, n, n, tp.npad, tp.Psp);
+        launch_tca<DS, NR / 8, KER>(Xs, n, tp.Xdup, tp.Psp, part, js, chunk, tp.err, s);
     } else if constexpr (NR >= 2) {
         matvec32p_kernel<(D == 3 ? 4 : D), NR, KER><<<grid, NT, 0, s>>>(Xs, n, P, n, part, chunk);
     } else {
@@ -364,43 +459,64 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
 
 template <int D, int KER>
 static void launch32_nr(int nr, const float *Xs, int64_t n, const float *P, float *part, int js,
-                        int64_t chunk, cudaStream_t s)
+                        int64_t chunk, const TcPrep &tp, cudaStream_t s)
 {
     switch (nr) {
-    case 1: launch32<D, 1, KER>(Xs, n, P, part, js, chunk, s); break;
-    case 2: launch32<D, 2, KER>(Xs, n, P, part, js, chunk, s); break;
-    case 4: launch32<D, 4, KER>(Xs, n, P, part, js, chunk, s); break;
-    case 8: launch32<D, 8, KER>(Xs, n, P, part, js, chunk, s); break;
-    case 16: launch32<D, 16, KER>(Xs, n, P, part, js, chunk, s); break;
-    default: launch32<D, 32, KER>(Xs, n, P, part, js, chunk, s); break;
+    case 1: launch32<D, 1, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    case 2: launch32<D, 2, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    case 4: launch32<D, 4, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    case 8: launch32<D, 8, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    case 16: launch32<D, 16, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    default: launch32<D, 32, KER>(Xs, n, P, part, js, chunk, tp, s); break;
     }
 }
 
 template <int KER>
 static void launch32_d(int dp, int nr, const float *Xs, int64_t n, const float *P, float *part,
-                       int js, int64_t chunk, cudaStream_t s)
+                       int js, int64_t chunk, const TcPrep &tp, cudaStream_t s)
 {
     switch (dp) {
-    case 3: launch32_nr<3, KER>(nr, Xs, n, P, part, js, chunk, s); break;
-    case 4: launch32_nr<4, KER>(nr, Xs, n, P, part, js, chunk, s); break;
-    case 8: launch32_nr<8, KER>(nr, Xs, n, P, part, js, chunk, s); break;
-    default: launch32_nr<16, KER>(nr, Xs, n, P, part, js, chunk, s); break;
+    case 3: launch32_nr<3, KER>(nr, Xs, n, P, part, js, chunk, tp, s); break;
+    case 4: launch32_nr<4, KER>(nr, Xs, n, P, part, js, chunk, tp, s); break;
+    case 8: launch32_nr<8, KER>(nr, Xs, n, P, part, js, chunk, tp, s); break;
+    default: launch32_nr<16, KER>(nr, Xs, n, P, part, js, chunk, tp, s); break;
     }
 }
 
 // p, q: n x nrhs column-major with leading dimension n.
 afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, const float *p,
-                    int nrhs, float *q, void *scratch, size_t scratch_bytes, cudaStream_t s)
+                    int nrhs, float *q, void *scratch, size_t scratch_bytes, int *err,
+                    cudaStream_t s)
 {
     if (n <= 0 || nrhs <= 0) return AFN_OK;
     if (scratch_bytes < matvec32_scratch(n, nrhs)) {
         set_error("matvec32: scratch too small");
         return AFN_ERR_ARG;
     }
+    if (nrhs >= 8 && !err) {
+        set_error("matvec32: the tensor-core path needs a status word");
+        return AFN_ERR_ARG;
+    }
     int js;
     int64_t chunk;
     chunking(n, js, chunk);
     float *part = static_cast<float *>(scratch);
+    TcPrep tp{};
+    tp.npad = tc_npad(n);
+    tp.err = err;
+    {
+        char *b = static_cast<char *>(scratch);
+        const size_t pb = sizeof(float) * (size_t)js * (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
+        f2_t *xd = reinterpret_cast<f2_t *>(b + (pb + 255) / 256 * 256);
+        const size_t db = sizeof(f2_t) * (size_t)tp.npad * 18;
+        tp.Psp = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(xd) + (db + 255) / 256 * 256);
+        tp.Xdup = xd;
+        if (nrhs >= 8) {
+            const int ds = stored_dim32(dp);
+            const int64_t tot = tp.npad * (ds + 2);
+            dup_points_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Xs, n, ds, tp.npad, xd);
+        }
+    }
     for (int c0 = 0; c0 < nrhs;) {
 #ifdef AFN_NO_TC
         int b = piece(nrhs - c0, 16);
@@ -408,8 +524,8 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
         int b = piece(nrhs - c0, 32);
 #endif
         const float *pp = p + (int64_t)c0 * n;
-        if (kernel == 0) launch32_d<0>(dp, b, Xs, n, pp, part, js, chunk, s);
-        else launch32_d<1>(dp, b, Xs, n, pp, part, js, chunk, s);
+        if (kernel == 0) launch32_d<0>(dp, b, Xs, n, pp, part, js, chunk, tp, s);
+        else launch32_d<1>(dp, b, Xs, n, pp, part, js, chunk, tp, s);
         int64_t tot = n * b;
         matvec_finish<float><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
             part, js, b, n, pp, n, q + (int64_t)c0 * n, n, mu);
@@ -799,7 +915,7 @@ afn_status kernel_row_sum_max(const float *Xs, int64_t n, int dp, int kernel, do
     float *p = buf.as<float>(), *q = p + n;
     unsigned int *mx = reinterpret_cast<unsigned int *>(q + n);
     fill_ones_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n);
-    AFN_TRY(matvec32(Xs, n, dp, kernel, 0.f, p, 1, q, scratch.p, sb, s));
+    AFN_TRY(matvec32(Xs, n, dp, kernel, 0.f, p, 1, q, scratch.p, sb, nullptr, s));   // 1 column: no TC
     AFN_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
     max_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(q, n, mx);
     unsigned int bits = 0;
@@ -856,11 +972,19 @@ __device__ __forceinline__ bool group_live(const GSys &S, int cg)
 
 static constexpr int GMV32_MINB = 3;
 
+// tiles staged by bulk copies from the system's Xdup and Psp (written by the
+// beta/p update), double-buffered; the mbarriers persist over the CTA's tiles
 __global__ void __launch_bounds__(256, GMV32_MINB) gmv32_kernel(const GDev *__restrict__ gd)
 {
-    __shared__ __align__(16) f2_t xsd[TCJ * (16 + 2)];
-    __shared__ __align__(16) uint32_t phi[TCJ * TcPS<1>::v];
-    __shared__ __align__(16) uint32_t plo[TCJ * TcPS<1>::v];
+    __shared__ __align__(16) unsigned char stage[2 * TcStage<16, 1>::BYTES];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int nt = gd->nmv;
@@ -869,23 +993,40 @@ __global__ void __launch_bounds__(256, GMV32_MINB) gmv32_kernel(const GDev *__re
         const GSys &S = gd->sys[tl.sys];
         if (!group_live(S, tl.cg)) continue;
         const int64_t n = S.n;
-        const float *P = S.p32 + (int64_t)tl.cg * GC * n;
+        const f2_t *xd = reinterpret_cast<const f2_t *>(S.Xdup);
+        const uint32_t *ps = S.Psp + (int64_t)tl.cg * S.npad * TcRow<1>::ROW;
         float acc[1][4];
+        bool ok;
         switch (S.ds * 2 + S.kernel) {
-        case 8:  mv32tc_rows<4, 1, 0>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
-        case 9:  mv32tc_rows<4, 1, 1>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
-        case 16: mv32tc_rows<8, 1, 0>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
-        case 17: mv32tc_rows<8, 1, 1>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
-        case 32: mv32tc_rows<16, 1, 0>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
-        default: mv32tc_rows<16, 1, 1>(S.X32, n, P, n, tl.r0, 0, n, xsd, phi, plo, acc); break;
+        case 8:  ok = mv32tc_rows_async<4, 1, 0>(S.X32, n, xd, ps, tl.r0, 0, n, stage, bars, parity, acc); break;
+        case 9:  ok = mv32tc_rows_async<4, 1, 1>(S.X32, n, xd, ps, tl.r0, 0, n, stage, bars, parity, acc); break;
+        case 16: ok = mv32tc_rows_async<8, 1, 0>(S.X32, n, xd, ps, tl.r0, 0, n, stage, bars, parity, acc); break;
+        case 17: ok = mv32tc_rows_async<8, 1, 1>(S.X32, n, xd, ps, tl.r0, 0, n, stage, bars, parity, acc); break;
+        case 32: ok = mv32tc_rows_async<16, 1, 0>(S.X32, n, xd, ps, tl.r0, 0, n, stage, bars, parity, acc); break;
+        default: ok = mv32tc_rows_async<16, 1, 1>(S.X32, n, xd, ps, tl.r0, 0, n, stage, bars, parity, acc); break;
+        }
+        if (!ok) {
+            if (threadIdx.x == 0) atomicExch(gd->err, DEV_TIMEOUT);
+            return;
         }
         const int64_t ia = tl.r0 + warp * 16 + g, ib = ia + 8;
         const float mu = S.mu32;
+        const float *P = S.p32 + (int64_t)tl.cg * GC * n;
         const float *p0 = P + (int64_t)(2 * t) * n, *p1 = p0 + n;
         float *q0 = S.q32 + ((int64_t)tl.cg * GC + 2 * t) * n, *q1 = q0 + n;
         if (ia < n) { q0[ia] = acc[0][0] + mu * p0[ia]; q1[ia] = acc[0][1] + mu * p1[ia]; }
         if (ib < n) { q0[ib] = acc[0][2] + mu * p0[ib]; q1[ib] = acc[0][3] + mu * p1[ib]; }
     }
+}
+
+int group_npad(int64_t n) { return (int)tc_npad(n); }
+
+void dup_points(const float *Xs, int64_t n, int ds, int64_t npad, void *Xdup, cudaStream_t s)
+{
+    const int64_t tot = npad * (ds + 2);
+    if (tot > 0)
+        dup_points_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Xs, n, ds, npad,
+                                                                       static_cast<f2_t *>(Xdup));
 }
 
 // q = (K + mu I) x, FP64-accurate (double-float, matvec_df.cuh), for the
@@ -923,16 +1064,22 @@ __global__ void __launch_bounds__(NT) gmvdf_kernel(const GDev *__restrict__ gd)
 int group_mv32_rows() { return TCR; }
 int group_mv64_rows() { return TI; }
 
-afn_status group_matvec32(const GDev *gd, cudaStream_t s)
+int persistent_grid(int ctas_per_sm, double share)
 {
-    gmv32_kernel<<<num_sms() * GMV32_MINB, 256, 0, s>>>(gd);
+    const int g = (int)(num_sms() * ctas_per_sm * share + 0.5);
+    return g > 0 ? g : 1;
+}
+
+afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share)
+{
+    gmv32_kernel<<<persistent_grid(GMV32_MINB, share), 256, 0, s>>>(gd);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped matvec32 launch");
 }
 
-afn_status group_matvec64(const GDev *gd, cudaStream_t s)
+afn_status group_matvec64(const GDev *gd, cudaStream_t s, double share)
 {
-    gmvdf_kernel<<<num_sms() * 2, NT, 0, s>>>(gd);
+    gmvdf_kernel<<<persistent_grid(2, share), NT, 0, s>>>(gd);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped matvec64 launch");
 }

@@ -190,4 +190,214 @@ __device__ __forceinline__ void mv32tc_rows(const float *__restrict__ Xs, int64_
     }
 }
 
+// --------------------------------------------------------------------------
+// Asynchronous staging.  The point and p tiles are laid out in global memory
+// exactly as the compute loop reads them from shared memory -- points as
+// duplicated (x, x) pairs, TCJ rows of DS + 2 pairs (Xdup); p split into tf32
+// (hi, lo) words, row j = [hi(c), c < NR | pad | lo(c) | pad] of ROW = 2 PS
+// words with ROW = 8 mod 32 (conflict-free fragment reads) (Psp) -- both
+// padded with zero rows to a multiple of TCJ.  Each tile is then two bulk
+// copies (cp.async.bulk, the TMA engine) issued by one thread and completed
+// on an mbarrier, double-buffered so that the copies of tile i+1 overlap the
+// tensor-core work on tile i.
+// --------------------------------------------------------------------------
+template <int NB> struct TcRow {
+    static constexpr int PS = (NB <= 2) ? 20 : 36;   // hi block + pad, words
+    static constexpr int ROW = 2 * PS;               // words per staged p row
+};
+
+template <int DS, int NB> struct TcStage {
+    static constexpr int PTS = TCJ * (DS + 2) * 8;        // bytes of the point tile
+    static constexpr int PB = TCJ * TcRow<NB>::ROW * 4;   // bytes of the p tile
+    static constexpr int BYTES = PTS + PB;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// wait for phase `parity` of the barrier, giving up after 2 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0;; ++spin) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spin & 63u) == 0) {
+            const uint64_t t = globaltimer_ns();
+            if (spin == 0) t0 = t;
+            else if (t - t0 > 2000000000ull) return false;
+        }
+    }
+}
+
+// The tile loop of mv32tc_rows over [j0, j1) with staged tiles read from the
+// prepared Xdup / Psp arrays.  stage: 2 x TcStage<DS,NB>::BYTES of shared
+// memory (16-byte aligned); bars: 2 mbarriers initialised with count 1;
+// parity: the phase bits of the two barriers, carried across calls by every
+// thread.  Returns false (block-uniformly) when a copy did not complete in
+// time; in that case the sums are invalid and the caller reports the error.
+template <int DS, int NB, int KER>
+__device__ __forceinline__ bool mv32tc_rows_async(const float *__restrict__ Xs, int64_t n,
+                                                  const f2_t *__restrict__ Xdup,
+                                                  const uint32_t *__restrict__ Psp,
+                                                  int64_t row0, int64_t j0, int64_t j1,
+                                                  unsigned char *stage, uint64_t *bars,
+                                                  uint32_t &parity, float (&acc)[NB][4])
+{
+    constexpr int ROW = TcRow<NB>::ROW;
+    constexpr int PS = TcRow<NB>::PS;
+    constexpr int DSP = DS + 2;
+    constexpr int SB = TcStage<DS, NB>::BYTES;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ia = row0 + warp * 16 + g;
+    const int64_t ib = ia + 8;
+    f2_t xi[DS];
+#pragma unroll
+    for (int q = 0; q < DS; ++q)
+        xi[q] = f2_pack(ia < n ? Xs[ia * DS + q] : 0.f, ib < n ? Xs[ib * DS + q] : 0.f);
+    float cmp[TC_KAHAN ? NB : 1][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[b][r] = 0.f;
+#pragma unroll
+    for (int b = 0; b < (TC_KAHAN ? NB : 1); ++b)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) cmp[b][r] = 0.f;
+
+    const int ntiles = (int)((j1 - j0 + TCJ - 1) / TCJ);
+    auto issue = [&](int it) {
+        unsigned char *st = stage + (it & 1) * SB;
+        const int64_t j = j0 + (int64_t)it * TCJ;
+        uint64_t *bar = bars + (it & 1);
+        mbar_expect_tx(bar, (uint32_t)SB);
+        bulk_g2s(st, Xdup + j * DSP, (uint32_t)TcStage<DS, NB>::PTS, bar);
+        bulk_g2s(st + TcStage<DS, NB>::PTS, Psp + j * ROW, (uint32_t)TcStage<DS, NB>::PB, bar);
+    };
+    bool ok = true;
+    if (threadIdx.x == 0 && ntiles > 0) issue(0);
+    int it = 0;
+    for (; it < ntiles; ++it) {
+        const int b = it & 1;
+        if (threadIdx.x == 0 && it + 1 < ntiles) issue(it + 1);
+        const bool got = mbar_wait_bounded(bars + b, (parity >> b) & 1u);
+        if (!__syncthreads_and(got)) {
+            ok = false;      // tile it (and it + 1, if issued) may still be in flight
+            break;
+        }
+        parity ^= 1u << b;
+        const f2_t *xsd = reinterpret_cast<const f2_t *>(stage + b * SB);
+        const uint32_t *pw = reinterpret_cast<const uint32_t *>(stage + b * SB + TcStage<DS, NB>::PTS);
+        float tac[NB][4];
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) tac[bb][r] = 0.f;
+#pragma unroll
+        for (int kb = 0; kb < TCJ / 8; ++kb) {
+            const f2_t *xa = xsd + (kb * 8 + t) * DSP;
+            const f2_t *xb = xsd + (kb * 8 + t + 4) * DSP;
+            f2_t ra = 0ull, rb = 0ull;
+#pragma unroll
+            for (int q = 0; q < DS; q += 2) {
+                const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(xa + q);
+                const ulonglong2 vb = *reinterpret_cast<const ulonglong2 *>(xb + q);
+                f2_t u = f2_sub(xi[q], va.x);
+                ra = f2_fma(u, u, ra);
+                u = f2_sub(xi[q], vb.x);
+                rb = f2_fma(u, u, rb);
+                u = f2_sub(xi[q + 1], va.y);
+                ra = f2_fma(u, u, ra);
+                u = f2_sub(xi[q + 1], vb.y);
+                rb = f2_fma(u, u, rb);
+            }
+            float r_aa, r_ba, r_ab, r_bb;
+            f2_unpack(ra, r_aa, r_ba);
+            f2_unpack(rb, r_ab, r_bb);
+            uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3;
+            tf32_split(kernel32_scaled<KER>(r_aa), ah0, al0);
+            tf32_split(kernel32_scaled<KER>(r_ba), ah1, al1);
+            tf32_split(kernel32_scaled<KER>(r_ab), ah2, al2);
+            tf32_split(kernel32_scaled<KER>(r_bb), ah3, al3);
+            const uint32_t *p0 = pw + (kb * 8 + t) * ROW + g;
+            const uint32_t *p1 = pw + (kb * 8 + t + 4) * ROW + g;
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) {
+                const uint32_t bh0 = p0[bb * 8], bh1 = p1[bb * 8];
+                const uint32_t bl0 = p0[PS + bb * 8], bl1 = p1[PS + bb * 8];
+                mma_tf32(tac[bb], al0, al1, al2, al3, bh0, bh1);
+                mma_tf32(tac[bb], ah0, ah1, ah2, ah3, bl0, bl1);
+                mma_tf32(tac[bb], ah0, ah1, ah2, ah3, bh0, bh1);
+            }
+            if ((kb + 1) % TC_FOLD == 0) {
+#pragma unroll
+                for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        if constexpr (TC_KAHAN) {
+                            float y = tac[bb][r] - cmp[bb][r];
+                            float s = acc[bb][r] + y;
+                            cmp[bb][r] = (s - acc[bb][r]) - y;
+                            acc[bb][r] = s;
+                        } else {
+                            acc[bb][r] += tac[bb][r];
+                        }
+                        tac[bb][r] = 0.f;
+                    }
+            }
+        }
+        __syncthreads();   // buffer b is free for the copies of tile it + 2
+    }
+    if (!ok && threadIdx.x == 0) {
+        // copies issued but not consumed (tiles it and it + 1): wait for them,
+        // again bounded, before the shared memory they write goes out of scope
+        for (int k = it; k < ntiles && k <= it + 1; ++k) {
+            const int b = k & 1;
+            if (mbar_wait_bounded(bars + b, (parity >> b) & 1u)) parity ^= 1u << b;
+        }
+    }
+    return ok;
+}
+
 }  // namespace afn

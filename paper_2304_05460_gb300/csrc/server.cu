@@ -72,6 +72,7 @@ static int64_t footprint(int64_t n, int d, int64_t kmax, int w, int nrhs, bool w
     const int C = (nrhs + GC - 1) / GC * GC;
     const int64_t js = nr > 0 ? (nr + 2047) / 2048 : 0;
     b += n * C * (3 * 8 + 5 * 4) + 2 * k * C * 4 + 2 * nr * C * 4 + js * C * k * 4 + C * 128;
+    b += (n + 64) * (ds + 2) * 8 + (n + 64) * C * 20;    // staged point and p tiles
     b += n * nrhs * 8;                                    // rhs upload
     return b + (4 << 20);                                 // allocator granularity, small arrays
 }
@@ -85,12 +86,13 @@ struct Server {
     cudaStream_t stream = nullptr;
 
     std::mutex mu;
-    std::condition_variable cv_sched, cv_build, cv_done;
+    std::condition_variable cv_sched, cv_build, cv_done, cv_single;
     bool stop = false;
     int64_t next_id = 1;
     std::deque<Request *> queue;           // submitted, not admitted
     std::deque<Request *> to_build;        // admitted, waiting for a build thread
     std::vector<Request *> ready;          // built, waiting to join the group
+    std::deque<Request *> single;          // built DF requests, waiting for a solver thread
     std::map<int64_t, Request *> all;
     std::deque<int64_t> completed;         // done, not yet reported by poll
     int64_t reserved = 0, peak_reserved = 0;
@@ -99,10 +101,12 @@ struct Server {
     int peak_live = 0;
 
     std::thread sched;
-    std::vector<std::thread> builders;
-    std::vector<cudaStream_t> bstreams;
+    std::vector<std::thread> builders, singles;
+    std::vector<cudaStream_t> bstreams, sstreams;
+    int nsingle = 4;
 
     void build_loop(int t);
+    void single_loop(int t);
     void sched_loop();
     void finish(Request *r, Group *g);
 };
@@ -140,36 +144,17 @@ void Server::build_loop(int t)
         }
         if (st == AFN_OK && h->precision != AFN_PREC_MIXED) {
             // a DF (or FP64) request -- AFN_PREC_AUTO's choice for a small mu --
-            // is solved here, on this thread's stream, beside the running group
+            // goes to the one-at-a-time solver threads, so builds keep flowing
             {
                 std::lock_guard<std::mutex> lk(mu);
                 r->t_built = Clock::now();
                 r->build_ms = ms_since(t0, r->t_built);
-                r->t_join = r->t_built;
                 r->h = h;
+                r->bstream = s;
+                r->state = RQ_READY;
+                single.push_back(r);
             }
-            StreamGuard sg(s);
-            DevBuf xd;
-            r->iters.assign(r->nrhs, 0);
-            r->relres.assign(r->nrhs, 0.0);
-            int outer = 0, conv = 0;
-            st = xd.alloc(sizeof(double) * r->sys.n * r->nrhs);
-            if (st == AFN_OK)
-                st = solve_handle(h, r->bdev.as<double>(), r->nrhs, r->tol, xd.as<double>(),
-                                  r->iters.data(), r->relres.data(), &outer, &conv);
-            if (st == AFN_OK || st == AFN_ERR_NO_CONVERGE) {
-                r->x.resize((size_t)r->sys.n * r->nrhs);
-                cudaError_t e = cudaMemcpyAsync(r->x.data(), xd.p, sizeof(double) * r->x.size(),
-                                                cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                if (e != cudaSuccess) st = cuda_fail(e, "request result copy");
-            }
-            r->converged = conv;
-            r->status = st;
-            r->error = st == AFN_OK ? "" : (st == AFN_ERR_NO_CONVERGE ? "some columns missed tol"
-                                                                     : afn_last_error());
-            r->state = RQ_READY;
-            finish(r, nullptr);
+            cv_single.notify_one();
             continue;
         }
         {
@@ -184,6 +169,48 @@ void Server::build_loop(int t)
             ready.push_back(r);
         }
         cv_sched.notify_one();
+    }
+}
+
+// One-at-a-time solves of the DF (or FP64) requests, on low-priority streams
+// of their own beside the running group and the builds.
+void Server::single_loop(int t)
+{
+    cudaSetDevice(dev);
+    cudaStream_t s = sstreams[t];
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_single.wait(lk, [&] { return stop || !single.empty(); });
+            if (stop) return;
+            r = single.front();
+            single.pop_front();
+            r->t_join = Clock::now();
+        }
+        Handle *h = r->h;
+        h->stream = s;
+        StreamGuard sg(s);
+        DevBuf xd;
+        r->iters.assign(r->nrhs, 0);
+        r->relres.assign(r->nrhs, 0.0);
+        int outer = 0, conv = 0;
+        afn_status st = xd.alloc(sizeof(double) * r->sys.n * r->nrhs);
+        if (st == AFN_OK)
+            st = solve_handle(h, r->bdev.as<double>(), r->nrhs, r->tol, xd.as<double>(),
+                              r->iters.data(), r->relres.data(), &outer, &conv);
+        if (st == AFN_OK || st == AFN_ERR_NO_CONVERGE) {
+            r->x.resize((size_t)r->sys.n * r->nrhs);
+            cudaError_t e = cudaMemcpyAsync(r->x.data(), xd.p, sizeof(double) * r->x.size(),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_fail(e, "request result copy");
+        }
+        r->converged = conv;
+        r->status = st;
+        r->error = st == AFN_OK ? "" : (st == AFN_ERR_NO_CONVERGE ? "some columns missed tol"
+                                                                 : afn_last_error());
+        finish(r, nullptr);
     }
 }
 
@@ -247,7 +274,9 @@ void Server::sched_loop()
     auto group_for = [&](double tol) {
         auto it = groups.find(tol);
         if (it != groups.end()) return it->second;
-        Group *g = new Group(stream, chunk, tol, delta, maxit);
+        // the group leaves about a third of the SMs' CTA slots to the builds
+        // and one-at-a-time solves running beside it
+        Group *g = new Group(stream, chunk, tol, delta, maxit, 0.65);
         groups[tol] = g;
         return g;
     };
@@ -363,14 +392,21 @@ afn_status afn_server_create(const afn_server_config *cfg, afn_server **out)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     s->budget = c.memory_budget > 0 ? c.memory_budget : (int64_t)(fr / 2);
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    // builds get the highest stream priority (their many short kernels are
+    // not held back by the long ones), the group the middle, DF solves the lowest
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, (lo + hi) / 2) != cudaSuccess) {
         delete s;
         set_error("afn_server_create: stream creation failed");
         return AFN_ERR_CUDA;
     }
     s->bstreams.resize(s->nbuild);
-    for (auto &b : s->bstreams) cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+    for (auto &b : s->bstreams) cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, hi);
+    s->sstreams.resize(s->nsingle);
+    for (auto &b : s->sstreams) cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, lo);
     for (int t = 0; t < s->nbuild; ++t) s->builders.emplace_back(&Server::build_loop, s, t);
+    for (int t = 0; t < s->nsingle; ++t) s->singles.emplace_back(&Server::single_loop, s, t);
     s->sched = std::thread(&Server::sched_loop, s);
     *out = reinterpret_cast<afn_server *>(s);
     return AFN_OK;
@@ -526,7 +562,9 @@ void afn_server_destroy(afn_server *ss)
     }
     s->cv_build.notify_all();
     s->cv_sched.notify_all();
+    s->cv_single.notify_all();
     for (auto &t : s->builders) t.join();
+    for (auto &t : s->singles) t.join();
     if (s->sched.joinable()) s->sched.join();
     cudaStreamSynchronize(s->stream);
     for (auto &kv : s->all) {
@@ -537,6 +575,10 @@ void afn_server_destroy(afn_server *ss)
         delete r;
     }
     for (auto b : s->bstreams) {
+        cudaStreamSynchronize(b);
+        cudaStreamDestroy(b);
+    }
+    for (auto b : s->sstreams) {
         cudaStreamSynchronize(b);
         cudaStreamDestroy(b);
     }

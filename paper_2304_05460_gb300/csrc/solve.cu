@@ -345,7 +345,7 @@ static afn_status mv32(Handle *h, const float *p, int nrhs, float *q, const Work
 {
     Scope sc(&h->prof, K_MATVEC32);
     return matvec32(h->X32.as<float>(), h->n, h->dp, h->kernel, (float)h->mu, p, nrhs, q, wk.mv32,
-                    wk.mv32_bytes, h->stream);
+                    wk.mv32_bytes, h->status.as<int>() + 3, h->stream);
 }
 
 // Generic PCG on the columns that are active in cs (x, r given; r = b - A x).
@@ -553,13 +553,20 @@ __global__ void ru_post_kernel(Cols cs, int nrhs, double tol, int maxit, double 
     }
 }
 
-static afn_status poll_both(const Cols &cs, int nrhs, cudaStream_t s, int *na, int *nf)
+// active and flagged columns, and the status word of the staged matvec copies
+static afn_status poll_both(const Cols &cs, int nrhs, const int *err, cudaStream_t s, int *na,
+                            int *nf)
 {
     count_active_kernel<<<1, 1, 0, s>>>(cs, nrhs);
-    int h[2];
+    int h[3];
     AFN_CUDA(cudaMemcpyAsync(&h[0], cs.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
     AFN_CUDA(cudaMemcpyAsync(&h[1], cs.nflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AFN_CUDA(cudaMemcpyAsync(&h[2], err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AFN_CUDA(cudaStreamSynchronize(s));
+    if (h[2]) {
+        set_error("FP32 matvec: a staged tile copy did not complete in time");
+        return AFN_ERR_TIMEOUT;
+    }
     *na = h[0];
     *nf = h[1];
     return AFN_OK;
@@ -600,7 +607,7 @@ static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int 
         }
         if ((it + 1) % every == 0) {
             int na = 0, nf = 0;
-            AFN_TRY(poll_both(cs, nrhs, s, &na, &nf));
+            AFN_TRY(poll_both(cs, nrhs, h->status.as<int>() + 3, s, &na, &nf));
             if (na == 0) break;
             if (nf > 0) {
                 // replacement for every active column: x += dx, r = b - (K + mu I) x
@@ -611,7 +618,7 @@ static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int 
                 ru_post_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(cs, nrhs, tol, maxit, drel);
                 to32_kernel<<<g1(tot), 256, 0, s>>>(wk.r, wk.r32, tot);
                 ++steps;
-                AFN_TRY(poll_both(cs, nrhs, s, &na, &nf));
+                AFN_TRY(poll_both(cs, nrhs, h->status.as<int>() + 3, s, &na, &nf));
                 if (log_on()) {
                     std::vector<double> hr(nrhs);
                     std::vector<int> hi(nrhs);
