@@ -58,7 +58,7 @@ def parse():
                     help="systems of the batched workload (0 = skip)")
     ap.add_argument("--fp64-sample", type=int, default=24,
                     help="batched systems solved one at a time in plain FP64 for comparison")
-    ap.add_argument("--serving", type=int, default=64,
+    ap.add_argument("--serving", type=int, default=32,
                     help="requests of the serving stream (0 = skip)")
     ap.add_argument("--serving-rate", type=float, default=0.0,
                     help="Poisson arrival rate, requests/s (0 = all requests at t = 0)")

@@ -176,6 +176,13 @@ afn_status afn_reset_kernel_stats(afn_handle *h);
  * (all entry points, all devices).  Tooling; no paper counterpart. */
 int64_t afn_launch_count(void);
 
+/* Device memory of every handle, batch and server comes from a pool owned by
+ * the library (one per device) that keeps released memory cached for reuse
+ * (allocation and release then never synchronise the device).  This call
+ * waits for the current device to go idle and returns the cached memory to
+ * the device.  No paper counterpart. */
+void afn_release_cached_memory(void);
+
 /* ---- operator-level entry points (each one step of the hot path) ------- */
 
 /*

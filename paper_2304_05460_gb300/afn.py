@@ -92,6 +92,7 @@ def _load():
         "afn_rank_estimate": (i32, [P, i64, i32, i32, dbl, dbl, i32, u64, i32, C.POINTER(i64),
                                     C.POINTER(i64), C.POINTER(i32), P]),
         "afn_launch_count": (i64, []),
+        "afn_release_cached_memory": (None, []),
         "afn_kernel_matvec_noalloc": (i32, [P, i64, i32, i32, dbl, dbl, P, i32, P, P]),
         "afn_build_batched": (i32, [C.POINTER(afn_system), i32, C.POINTER(afn_options),
                                     C.POINTER(P)]),
@@ -303,6 +304,11 @@ def afn_get_kernel_stats(h: Handle, name: str):
 def afn_launch_count() -> int:
     """Kernels launched by libafn.so in this process so far."""
     return int(_lib.afn_launch_count())
+
+
+def afn_release_cached_memory():
+    """Return the library's cached device memory to the device (waits for idle)."""
+    _lib.afn_release_cached_memory()
 
 
 def afn_reset_kernel_stats(h: Handle):

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -33,10 +34,11 @@ enum : int { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_TIMEOUT = 2 };
 
 // -------------------------------------------------------- device buffers --
 // Device memory comes from a library-owned stream-ordered pool (one per
-// device).  A buffer is allocated on the calling thread's current library
-// stream (StreamGuard) and released on the same stream, so allocation and
-// release never synchronise the device: independent handles built on
-// separate streams run concurrently.  That stream must outlive the buffer.
+// device) that keeps released memory cached until afn_release_cached_memory.
+// A buffer is allocated on the calling thread's current library stream
+// (StreamGuard) and released on the same stream, so allocation and release
+// never synchronise the device: independent handles built on separate
+// streams run concurrently.  That stream must outlive the buffer.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -232,6 +234,15 @@ afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share);
 afn_status group_matvec64(const GDev *gd, cudaStream_t s, double share);
 afn_status group_apply(const GDev *gd, cudaStream_t s, double share);
 int persistent_grid(int ctas_per_sm, double share);   // max(1, SMs x ctas_per_sm x share)
+// caps, for the calling thread's scope, the fraction of CTA slots a
+// double-float matvec may take (read at every launch; 1 = no cap); used by
+// one-at-a-time solves running beside a group, whose owner lowers the share
+// while the group has work and raises it to 1 when it has none
+struct GridShareGuard {
+    const std::atomic<double> *prev;
+    explicit GridShareGuard(const std::atomic<double> *share);
+    ~GridShareGuard();
+};
 int group_mv32_rows();      // rows per tile of the grouped FP32 matvec
 int group_npad(int64_t n);  // n rounded up to the staged point tile
 // duplicated (x, x) FP32 pairs of the prescaled points, ds + 2 per row, npad rows

@@ -308,14 +308,27 @@ size_t Group::workspace_bytes(const Handle *h, int nrhs)
     return layout(h->n, h->k, h->nr, ncg * GC, js, stored_dim32(h->dp)).total;
 }
 
+// AFN_GROUP_PROFILE=1: stage times of the grouped iteration from CUDA events
+// recorded inside the captured graph, printed to stderr when the group ends
+static const char *STAGE_NAMES[Group::NSTAGE] = {"apply", "beta/p", "matvec32", "alpha/update",
+                                                 "residual"};
+
 Group::Group(cudaStream_t s, int chunk, double tol, double delta, int maxit, double share)
     : strm_(s), chunk_(std::max(1, chunk)), tol_(tol), delta_(delta), maxit_(maxit),
       share_(share > 0 && share <= 1 ? share : 1.0)
 {
+    const char *e = getenv("AFN_GROUP_PROFILE");
+    prof_ = e && e[0] == '1';
 }
 
 Group::~Group()
 {
+    if (prof_ && launches_ > 0) {
+        fprintf(stderr, "[afn group] %d graph launches of %d iterations:", launches_, chunk_);
+        for (int k = 0; k < NSTAGE; ++k) fprintf(stderr, " %s %.1f ms", STAGE_NAMES[k], stage_ms_[k]);
+        fprintf(stderr, "\n");
+    }
+    for (auto e : ev_) cudaEventDestroy(e);
     if (exec_) cudaGraphExecDestroy(exec_);
     if (nact_host_) cudaFreeHost(nact_host_);
 }
@@ -513,15 +526,26 @@ afn_status Group::upload()
     return AFN_OK;
 }
 
-afn_status Group::iteration()
+void Group::mark(int it, int stage)
+{
+    if (!prof_) return;
+    cudaEventRecord(ev_[(size_t)it * NSTAGE + stage], strm_);
+}
+
+afn_status Group::iteration(int it)
 {
     const GDev *gd = gd_.as<GDev>();
     const int gc = persistent_grid(8, share_);
+    mark(it, 0);
     AFN_TRY(group_apply(gd, strm_, share_));                       // z = M^{-1} r
+    mark(it, 1);
     gbeta_kernel<<<gc, CB, 0, strm_>>>(gd);                // rho, beta, p
+    mark(it, 2);
     AFN_TRY(group_matvec32(gd, strm_, share_));                    // q = (K + mu I) p
+    mark(it, 3);
     galpha_kernel<<<gc, CB, 0, strm_>>>(gd);
     gupdate_kernel<<<gc, CB, 0, strm_>>>(gd);              // x, r, reliable-update test
+    mark(it, 4);
     grep_kernel<<<MAX_SYS / 256, 256, 0, strm_>>>(gd);
     gacc_kernel<<<gc, CB, 0, strm_>>>(gd);                 // x += dx on replaced systems
     AFN_TRY(group_matvec64(gd, strm_, share_));                    // q = (K + mu I) x in FP64
@@ -536,7 +560,7 @@ afn_status Group::capture()
     const long long c0 = afn_launch_count();
     AFN_CUDA(cudaStreamBeginCapture(strm_, cudaStreamCaptureModeThreadLocal));
     afn_status st = AFN_OK;
-    for (int it = 0; it < chunk_ && st == AFN_OK; ++it) st = iteration();
+    for (int it = 0; it < chunk_ && st == AFN_OK; ++it) st = iteration(it);
     if (st == AFN_OK) {
         gstatus_kernel<<<MAX_SYS / 256, 256, 0, strm_>>>(gd_.as<GDev>());
         cudaError_t e = cudaMemcpyAsync(nact_host_, nact_.p, sizeof(int) * (MAX_SYS + 1),
@@ -567,11 +591,33 @@ afn_status Group::step(std::vector<Member *> &finished)
         hinit_.clear();
     }
     if (hsys_.empty()) return AFN_OK;
-    if (!exec_) AFN_TRY(capture());
-    AFN_CUDA(cudaGraphLaunch(exec_, strm_));
-    count_launches(kpg_);
+    if (prof_) {
+        // profiling: the same launches issued eagerly between timing events
+        if (!nact_host_) AFN_CUDA(cudaMallocHost(&nact_host_, sizeof(int) * (MAX_SYS + 1)));
+        if (ev_.empty()) {
+            ev_.resize((size_t)chunk_ * NSTAGE + 1);
+            for (auto &e : ev_) cudaEventCreate(&e);
+        }
+        for (int it = 0; it < chunk_; ++it) AFN_TRY(iteration(it));
+        cudaEventRecord(ev_.back(), strm_);
+        gstatus_kernel<<<MAX_SYS / 256, 256, 0, strm_>>>(gd_.as<GDev>());
+        AFN_CUDA(cudaMemcpyAsync(nact_host_, nact_.p, sizeof(int) * (MAX_SYS + 1),
+                                 cudaMemcpyDeviceToHost, strm_));
+    } else {
+        if (!exec_) AFN_TRY(capture());
+        AFN_CUDA(cudaGraphLaunch(exec_, strm_));
+        count_launches(kpg_);
+    }
     ++launches_;
     AFN_CUDA(cudaStreamSynchronize(strm_));
+    if (prof_) {
+        for (int it = 0; it < chunk_; ++it)
+            for (int k = 0; k < NSTAGE; ++k) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev_[(size_t)it * NSTAGE + k], ev_[(size_t)it * NSTAGE + k + 1]);
+                stage_ms_[k] += ms;
+            }
+    }
     if (nact_host_[MAX_SYS]) {
         set_error("grouped matvec: a staged tile copy did not complete in time");
         return AFN_ERR_TIMEOUT;
@@ -776,6 +822,7 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
     // AFN_PREC_AUTO for a small mu) are solved one at a time on the build
     // streams by host threads, overlapping the grouped solve of the others
     double group_ms = 0;
+    std::atomic<double> df_share{0.5};    // 1 once the group has finished
     const auto w0 = std::chrono::steady_clock::now();
     std::atomic<long long> single_end_us{0};
     std::vector<int> single;
@@ -792,6 +839,7 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
             const int q = single[i];
             Handle *h = b->h[q];
             h->stream = b->bstreams[t % b->bstreams.size()];
+            GridShareGuard gs(&df_share);   // the group keeps free SMs for its short kernels
             int outer = 0;
             sst[q] = solve_handle(h, R + off[q], nrhs[q], tol, X + off[q], it.data() + coff[q],
                                   rel.data() + coff[q], &outer, &sconv[q]);
@@ -803,7 +851,7 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
         }
     };
     std::vector<std::thread> pool;
-    const int nsolo = std::min<int>((int)single.size(), (int)b->bstreams.size());
+    const int nsolo = std::min<int>({(int)single.size(), (int)b->bstreams.size(), 8});
     for (int t = 0; t < nsolo; ++t) pool.emplace_back(solo, t);
     {
         std::vector<Member> mem(ns);
@@ -824,6 +872,7 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
             ++launches;
         }
         group_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+        df_share = 1.0;
         for (int q = 0; q < ns && st == AFN_OK; ++q)
             if (b->h[q]->precision == AFN_PREC_MIXED)
                 st = g.collect(&mem[q], X + off[q], it.data() + coff[q], rel.data() + coff[q],

@@ -2,6 +2,7 @@
 // argument checks, host/device staging, the build orchestration of Alg. 2,
 // the solve (Alg. 5 with the apply of Alg. 3) and introspection.
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <cmath>
 #include <cstdarg>
@@ -39,7 +40,10 @@ cudaStream_t current_stream() { return tl_stream; }
 StreamGuard::StreamGuard(cudaStream_t s) : prev(tl_stream) { tl_stream = s; }
 StreamGuard::~StreamGuard() { tl_stream = prev; }
 
-// one pool per device; up to 8 GiB of released memory stays cached in it
+// one pool per device; released memory stays cached in it (no automatic
+// trimming: trimming happens at every synchronisation point of every thread
+// once the threshold is exceeded, and stalls all concurrent streams); the
+// caller returns it with afn_release_cached_memory()
 static constexpr int MAX_DEV = 64;
 static cudaMemPool_t g_pool[MAX_DEV];
 static std::once_flag g_pool_once[MAX_DEV];
@@ -58,7 +62,7 @@ static cudaMemPool_t pool_for(int dev)
             cudaGetLastError();
             mp = nullptr;
         } else {
-            uint64_t keep = 8ull << 30;
+            uint64_t keep = ~0ull;
             cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
         }
         g_pool[dev] = mp;
@@ -290,8 +294,32 @@ void scatter_cols(const double *src, const int64_t *perm, int64_t n, int nrhs, d
 }
 
 // ------------------------------------------------------------------- build --
+// AFN_LOG_BUILD=1 in the environment: host wall time of each build step on
+// stderr (the stream is synchronised at every mark; diagnostics only)
+struct StepLog {
+    bool on = false;
+    const Handle *h;
+    std::chrono::steady_clock::time_point t;
+    explicit StepLog(const Handle *hh) : h(hh)
+    {
+        const char *e = getenv("AFN_LOG_BUILD");
+        on = e && e[0] == '1';
+        t = std::chrono::steady_clock::now();
+    }
+    void mark(const char *what)
+    {
+        if (!on) return;
+        cudaStreamSynchronize(h->stream);
+        const auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[afn build n=%lld d=%d] %-10s %9.1f ms\n", (long long)h->n, h->d, what,
+                std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+
 static afn_status build_impl(Handle *h, const double *points)
 {
+    StepLog log(h);
     cudaStream_t s = h->stream;
     const int64_t n = h->n;
     const int d = h->d;
@@ -304,6 +332,7 @@ static afn_status build_impl(Handle *h, const double *points)
     const double *X0 = nullptr;
     AFN_TRY(to_device(points, n * d, pin, &X0, s));
     AFN_TRY(check_finite(X0, n * d, st, s, "points"));
+    log.mark("input");
 
     // k (Alg. 4 or fixed)
     int64_t k = std::min<int64_t>(h->k, n);
@@ -350,6 +379,7 @@ static afn_status build_impl(Handle *h, const double *points)
         }
     }
     AFN_TRY(h->perm.alloc(sizeof(int64_t) * (size_t)n));
+    log.mark("landmarks");
     AFN_TRY(build_perm(lm.as<int64_t>(), k, n, h->perm.as<int64_t>(), s));
     AFN_TRY(h->X64.alloc(sizeof(double) * (size_t)(n * d)));
     AFN_TRY(gather_points(X0, h->perm.as<int64_t>(), n, d, h->X64.as<double>(), s));
@@ -371,6 +401,7 @@ static afn_status build_impl(Handle *h, const double *points)
         h->precision = h->rho32 <= auto_rho_limit() ? AFN_PREC_MIXED : AFN_PREC_DF;
         if (h->precision != AFN_PREC_MIXED) h->X32.release();
     }
+    log.mark("points");
     const bool mixed = h->precision == AFN_PREC_MIXED;
     if (mixed || h->precision == AFN_PREC_DF) {
         AFN_TRY(h->Xdf.alloc(sizeof(float2) * (size_t)(n * ds)));
@@ -385,6 +416,7 @@ static afn_status build_impl(Handle *h, const double *points)
             AFN_TRY(cholesky64(h->L.as<double>(), k, st, s, -1.0));
         }
         AFN_TRY(sync_status(h, "Cholesky of K11 + mu I"));
+        log.mark("cholesky");
         Scope sc(&h->prof, K_TRSM);
         if (!mixed) {
             AFN_TRY(h->Linv.alloc(sizeof(double) * (size_t)(k * k)));
@@ -416,7 +448,9 @@ static afn_status build_impl(Handle *h, const double *points)
         AFN_TRY(h->pat.alloc(sizeof(int32_t) * (size_t)(nr * w)));
         {
             Scope sc(&h->prof, K_KNN);
+            log.mark("W");
             AFN_TRY(knn_pattern(Xr, nr, d, w, h->pat.as<int32_t>(), s));
+            log.mark("knn");
         }
         AFN_TRY(h->G.alloc(sizeof(double) * (size_t)(nr * w)));
         {
@@ -429,6 +463,7 @@ static afn_status build_impl(Handle *h, const double *points)
                                      h->G.as<double>(), st, s));
         }
         AFN_TRY(sync_status(h, "FSAI pattern block"));
+        log.mark("fsai");
         if (mixed) {
             AFN_TRY(h->G32.alloc(sizeof(float) * (size_t)(nr * w)));
             AFN_TRY(convert64to32(h->G.as<double>(), h->G32.as<float>(), nr * w, s));
@@ -440,6 +475,7 @@ static afn_status build_impl(Handle *h, const double *points)
                                   h->gt_row.as<int32_t>(), h->gt_slot.as<int32_t>(), s));
     }
     AFN_CUDA(cudaStreamSynchronize(s));
+    log.mark("Gt lists");
     return AFN_OK;
 }
 
@@ -476,10 +512,13 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
     h->k = std::min<int64_t>(k_max, n);
     h->w_req = fsai_nnz;
     cudaEvent_t e0, e1;
+    const auto w0 = std::chrono::steady_clock::now();
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, h->stream);
+    const auto w1 = std::chrono::steady_clock::now();
     afn_status st = build_impl(h, points);
+    const auto w2 = std::chrono::steady_clock::now();
     if (st == AFN_OK) {
         cudaEventRecord(e1, h->stream);
         cudaEventSynchronize(e1);
@@ -490,6 +529,17 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    {
+        const char *lg = getenv("AFN_LOG_BUILD");
+        if (lg && lg[0] == '1') {
+            const auto w3 = std::chrono::steady_clock::now();
+            auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+                return std::chrono::duration<double, std::milli>(b - a).count();
+            };
+            fprintf(stderr, "[afn build n=%lld d=%d] create: events %.1f ms, build %.1f ms, tail %.1f ms\n",
+                    (long long)n, d, ms(w0, w1), ms(w1, w2), ms(w2, w3));
+        }
+    }
     if (st != AFN_OK) {
         delete h;
         return st;
@@ -556,6 +606,14 @@ extern "C" cudaError_t __wrap_cudaLaunchCooperativeKernel(const void *f, dim3 g,
 extern "C" {
 
 int64_t afn_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void afn_release_cached_memory(void)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceSynchronize();
+    trim_pool();
+}
 
 void afn_default_options(afn_options *o)
 {

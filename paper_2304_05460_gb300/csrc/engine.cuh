@@ -30,6 +30,7 @@ struct Member {
 class Group {
 public:
     static constexpr int MAX_SYS = 1 << 16;
+    static constexpr int NSTAGE = 5;   // profiled stages of an iteration
 
     // share: fraction of the GPU's CTA slots the persistent grids take
     Group(cudaStream_t s, int chunk, double tol, double delta, int maxit, double share = 1.0);
@@ -55,7 +56,8 @@ public:
 private:
     afn_status upload();
     afn_status capture();
-    afn_status iteration();
+    afn_status iteration(int it);
+    void mark(int it, int stage);
 
     cudaStream_t strm_;
     int chunk_;
@@ -71,6 +73,9 @@ private:
     long long kpg_ = 0;           // kernels per graph launch
     int launches_ = 0;
     GDev hgd_{};
+    bool prof_ = false;
+    std::vector<cudaEvent_t> ev_;
+    double stage_ms_[NSTAGE] = {0, 0, 0, 0, 0};
     // host staging (kept until the next synchronisation)
     std::vector<GSys> hsys_;
     std::vector<GTile> htiles_;

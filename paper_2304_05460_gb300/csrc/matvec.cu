@@ -10,6 +10,7 @@
 // order and each (row tile, j-chunk) CTA writes one partial; a second kernel
 // sums the chunks in order and adds mu p.  The result is deterministic.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "afn_device.cuh"
@@ -792,33 +793,56 @@ __device__ __forceinline__ void mvdf_rows(const float2 *__restrict__ Xd, int64_t
 template <int DS, int NR, int KER>
 __global__ void __launch_bounds__(NT) matvecdf_kernel(const float2 *__restrict__ Xd, int64_t n,
                                                       const double *__restrict__ P, int64_t ldp,
-                                                      double *__restrict__ part, int64_t chunk)
+                                                      double *__restrict__ part, int64_t chunk,
+                                                      int js)
 {
     __shared__ __align__(16) float sm[MvDfSmem<DS, NR>::v];
     __shared__ DfExpTable T;
     df_table_init(T);
-    const int64_t i = (int64_t)blockIdx.x * TI + threadIdx.x % TI;
-    const int64_t j0 = (int64_t)blockIdx.y * chunk;
-    const int64_t j1 = min(n, j0 + chunk);
-    double acc[NR];
-    mvdf_rows<DS, NR, KER>(Xd, n, P, ldp, (int64_t)blockIdx.x * TI, j0, j1, sm, T, acc);
-    if (threadIdx.x < TI && i < n) {
+    // tiles (row tile, j-chunk), one per CTA or -- with a capped grid -- a
+    // grid-stride loop over them
+    const int64_t rt = (n + TI - 1) / TI;
+    const int64_t ntiles = rt * js;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t rb = tile % rt, q = tile / rt;
+        const int64_t i = rb * TI + threadIdx.x % TI;
+        const int64_t j0 = q * chunk;
+        const int64_t j1 = min(n, j0 + chunk);
+        double acc[NR];
+        mvdf_rows<DS, NR, KER>(Xd, n, P, ldp, rb * TI, j0, j1, sm, T, acc);
+        if (threadIdx.x < TI && i < n) {
 #pragma unroll
-        for (int c = 0; c < NR; ++c) part[((int64_t)blockIdx.y * NR + c) * n + i] = acc[c];
+            for (int c = 0; c < NR; ++c) part[(q * NR + c) * n + i] = acc[c];
+        }
+        __syncthreads();   // sm is reused by the next tile
     }
 }
+
+// fraction of the GPU a double-float matvec launched from this thread may
+// occupy (CTA slots); solves running beside a group of other systems cap it
+// so that the group's short kernels find free SMs
+static thread_local const std::atomic<double> *tl_df_share = nullptr;
+GridShareGuard::GridShareGuard(const std::atomic<double> *share) : prev(tl_df_share)
+{
+    tl_df_share = share;
+}
+GridShareGuard::~GridShareGuard() { tl_df_share = prev; }
 
 template <int DS, int KER>
 static void launchdf_nr(int nr, const float2 *Xd, int64_t n, const double *P, double *part,
                         int js, int64_t chunk, cudaStream_t s)
 {
-    dim3 grid((unsigned)((n + TI - 1) / TI), (unsigned)js);
+    const int64_t ntiles = (n + TI - 1) / TI * js;
+    int64_t g = ntiles;
+    const double share = tl_df_share ? tl_df_share->load(std::memory_order_relaxed) : 1.0;
+    if (share < 1.0) g = std::min<int64_t>(g, persistent_grid(2, share));
+    const unsigned grid = (unsigned)g;
     switch (nr) {
-    case 1: matvecdf_kernel<DS, 1, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
-    case 2: matvecdf_kernel<DS, 2, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
-    case 4: matvecdf_kernel<DS, 4, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
-    case 8: matvecdf_kernel<DS, 8, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
-    default: matvecdf_kernel<DS, 16, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk); break;
+    case 1: matvecdf_kernel<DS, 1, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
+    case 2: matvecdf_kernel<DS, 2, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
+    case 4: matvecdf_kernel<DS, 4, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
+    case 8: matvecdf_kernel<DS, 8, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
+    default: matvecdf_kernel<DS, 16, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
     }
 }
 

@@ -31,6 +31,16 @@ static double ms_since(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// AFN_LOG_BUILD=1: host wall times of the serving steps on stderr (diagnostics)
+static bool log_build()
+{
+    static const bool on = [] {
+        const char *e = getenv("AFN_LOG_BUILD");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
 enum ReqState { RQ_QUEUED, RQ_BUILDING, RQ_READY, RQ_SOLVING, RQ_DONE };
 
 struct Request {
@@ -104,6 +114,7 @@ struct Server {
     std::vector<std::thread> builders, singles;
     std::vector<cudaStream_t> bstreams, sstreams;
     int nsingle = 4;
+    std::atomic<double> df_share{1.0};    // GPU share of a one-at-a-time solve's matvec
 
     void build_loop(int t);
     void single_loop(int t);
@@ -131,6 +142,7 @@ void Server::build_loop(int t)
         afn_status st = create_handle(r->X.data(), r->sys.n, r->sys.d, r->sys.kernel, r->sys.l,
                                       r->sys.mu, r->sys.k_max, r->sys.fsai_nnz, o, s, &h);
         std::string err = st == AFN_OK ? "" : afn_last_error();
+        const auto t1 = Clock::now();
         if (st == AFN_OK) {
             StreamGuard sg(s);
             const size_t bytes = sizeof(double) * r->B.size();
@@ -141,6 +153,11 @@ void Server::build_loop(int t)
                 if (e != cudaSuccess) st = cuda_fail(e, "request rhs upload");
             }
             if (st != AFN_OK) err = afn_last_error();
+        }
+        if (log_build()) {
+            const auto t2 = Clock::now();
+            fprintf(stderr, "[afn serve] request %lld n=%lld: create %.1f ms, rhs upload %.1f ms\n",
+                    (long long)r->id, (long long)r->sys.n, ms_since(t0, t1), ms_since(t1, t2));
         }
         if (st == AFN_OK && h->precision != AFN_PREC_MIXED) {
             // a DF (or FP64) request -- AFN_PREC_AUTO's choice for a small mu --
@@ -191,6 +208,7 @@ void Server::single_loop(int t)
         Handle *h = r->h;
         h->stream = s;
         StreamGuard sg(s);
+        GridShareGuard gs(&df_share);   // the group keeps free SMs for its short kernels
         DevBuf xd;
         r->iters.assign(r->nrhs, 0);
         r->relres.assign(r->nrhs, 0.0);
@@ -304,6 +322,7 @@ void Server::sched_loop()
             }
             joining.swap(ready);
             if (solving.empty() && joining.empty()) {
+                df_share = 1.0;
                 cv_sched.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
@@ -350,6 +369,9 @@ void Server::sched_loop()
             }
         }
         peak_live = std::max(peak_live, live);
+        // one-at-a-time solves take a quarter of the CTA slots while the group
+        // has members (its short kernels then find free SMs), all otherwise
+        df_share = live > 0 ? 0.25 : 1.0;
     }
     for (auto &kv : groups) delete kv.second;
 }
