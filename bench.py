@@ -478,7 +478,7 @@ def main():
     peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "matvec32_kernel<D=8,NR=%d,Gaussian>" % nr_piece,
+            "kernel": "matvec32tca_kernel<DS=8,NB=%d,Gaussian>" % (nr_piece // 8),
             "flops_per_pair": 3 * D + 2 * nr_piece,
             "pairs_per_launch": float(n) * n, "avg_launch_ms": avg_ms, "launches": mv_cnt,
             "peak_basis": "FP32 pipe: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"}

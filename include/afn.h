@@ -99,7 +99,7 @@ typedef struct {
     int32_t rank_branch;       /* Alg. 4: 0 = k from r n / m, 1 = eigenvalue count, -1 = fixed k */
     int32_t pad_;
     double l, mu;
-    double build_ms;           /* device time of afn_build */
+    double build_ms;           /* wall time of the build (it ends synchronised) */
     int64_t device_bytes;      /* device memory held by the handle */
     double rho32;              /* AFN_PREC_AUTO: 2^-24 max_i sum_j K_ij / mu (0 otherwise) */
 } afn_build_info;

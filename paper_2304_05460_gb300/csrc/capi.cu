@@ -511,34 +511,14 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
     h->precision = o.precision;
     h->k = std::min<int64_t>(k_max, n);
     h->w_req = fsai_nnz;
-    cudaEvent_t e0, e1;
+    // host wall time: build_impl ends with a synchronisation of the stream
+    // (no CUDA events here: event calls stall behind graph launches of other
+    // threads, e.g. the serving loop's running group)
     const auto w0 = std::chrono::steady_clock::now();
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, h->stream);
-    const auto w1 = std::chrono::steady_clock::now();
     afn_status st = build_impl(h, points);
-    const auto w2 = std::chrono::steady_clock::now();
     if (st == AFN_OK) {
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        h->build_ms = ms;
+        h->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
         h->prof.flush();
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    {
-        const char *lg = getenv("AFN_LOG_BUILD");
-        if (lg && lg[0] == '1') {
-            const auto w3 = std::chrono::steady_clock::now();
-            auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
-                return std::chrono::duration<double, std::milli>(b - a).count();
-            };
-            fprintf(stderr, "[afn build n=%lld d=%d] create: events %.1f ms, build %.1f ms, tail %.1f ms\n",
-                    (long long)n, d, ms(w0, w1), ms(w1, w2), ms(w2, w3));
-        }
     }
     if (st != AFN_OK) {
         delete h;

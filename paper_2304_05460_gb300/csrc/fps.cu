@@ -1,14 +1,15 @@
 // fps.cu -- farthest point sampling (Alg. 6) and the landmark-first
 // permutation (the 2x2 partition of Sec. 2).
 //
-// FPS is one persistent cooperative launch.  Each thread owns up to PPT
-// points (j = gtid + s*T) and keeps their distance-to-selected-set entries in
-// registers for all k-1 steps; points are read in SoA layout (coalesced) from
-// L2.  One step = exact FP64 distance update (no FMA, dimensions in order),
-// warp/block argmax with lowest-index ties, one partial per block, one grid
-// barrier (bounded wait), and a redundant in-order reduction of the partials
-// by every block.  Partials are double-buffered by step parity, so one
-// barrier per step suffices.
+// FPS runs one launch per step, so it never needs its whole grid resident at
+// once and shares the GPU with other streams.  The distance-to-selected-set
+// array d_j lives in global memory (L2-resident), points in SoA layout
+// (coalesced).  A step = exact FP64 distance update against the last
+// selected point (no FMA, dimensions in order), warp/block argmax with
+// lowest-index ties, one partial per block; the last block to finish (an
+// arrival counter) reduces the partials, writes the next selected index and
+// marks it selected (d = -1).  The next launch reads that index, so the k-1
+// launches are queued back to back without host round trips.
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -20,7 +21,6 @@
 namespace afn {
 
 static constexpr int FPS_T = 256;
-static constexpr uint64_t BARRIER_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
 __global__ void to_soa_kernel(const double *__restrict__ X, int64_t n, int d,
                               double *__restrict__ Xt)
@@ -32,99 +32,81 @@ __global__ void to_soa_kernel(const double *__restrict__ X, int64_t n, int d,
     Xt[(int64_t)t * n + j] = X[e];
 }
 
-template <int PPT>
-__global__ void __launch_bounds__(FPS_T) fps_kernel(const double *__restrict__ Xt, int64_t n,
-                                                    int d, int64_t k, int64_t start,
-                                                    int64_t *__restrict__ idx,
-                                                    double *partv, int64_t *parti,
-                                                    unsigned int *bar, int *err)
+// d_j = +inf (unvisited), -1 for the start point; idx[0] = start
+__global__ void fps_init_kernel(int64_t n, int64_t start, double *__restrict__ dm,
+                                int64_t *__restrict__ idx, unsigned int *cnt)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dm[j] = (j == start) ? -1.0 : (double)INFINITY;
+    if (j == 0) {
+        idx[0] = start;
+        *cnt = 0;
+    }
+}
+
+__global__ void __launch_bounds__(FPS_T) fps_step_kernel(const double *__restrict__ Xt, int64_t n,
+                                                         int d, int64_t it,
+                                                         int64_t *__restrict__ idx,
+                                                         double *__restrict__ dm,
+                                                         double *partv, int64_t *parti,
+                                                         unsigned int *cnt)
 {
     __shared__ double xl[16];
     __shared__ double wv[FPS_T / 32];
     __shared__ int64_t wi[FPS_T / 32];
-    __shared__ int64_t lsel;
-    const int64_t T = (int64_t)gridDim.x * FPS_T;
-    const int64_t gtid = (int64_t)blockIdx.x * FPS_T + threadIdx.x;
-    const unsigned nb = gridDim.x;
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-    double dm[PPT];
-#pragma unroll
-    for (int s = 0; s < PPT; ++s) {
-        int64_t j = gtid + s * T;
-        dm[s] = (j < n) ? ((j == start) ? -1.0 : (double)INFINITY) : -2.0;   // unvisited, selected, absent
-    }
-    if (gtid == 0) idx[0] = start;
-    int64_t l = start;
-    for (int64_t it = 1; it < k; ++it) {
-        if (threadIdx.x < d) xl[threadIdx.x] = Xt[(int64_t)threadIdx.x * n + l];
-        __syncthreads();
-        double bv = -3.0;
-        int64_t bi = LLONG_MAX;
-#pragma unroll
-        for (int s = 0; s < PPT; ++s) {
-            int64_t j = gtid + s * T;
-            if (dm[s] >= 0.0) {
-                double r2 = 0.0;
-                for (int t = 0; t < d; ++t) {
-                    double u = __dsub_rn(Xt[(int64_t)t * n + j], xl[t]);
-                    r2 = __dadd_rn(r2, __dmul_rn(u, u));
-                }
-                if (r2 < dm[s]) dm[s] = r2;
+    const int64_t l = idx[it - 1];
+    if (threadIdx.x < d) xl[threadIdx.x] = Xt[(int64_t)threadIdx.x * n + l];
+    __syncthreads();
+    double bv = -3.0;
+    int64_t bi = LLONG_MAX;
+    for (int64_t j = (int64_t)blockIdx.x * FPS_T + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * FPS_T) {
+        double v = dm[j];
+        if (v >= 0.0) {
+            double r2 = 0.0;
+            for (int t = 0; t < d; ++t) {
+                double u = __dsub_rn(Xt[(int64_t)t * n + j], xl[t]);
+                r2 = __dadd_rn(r2, __dmul_rn(u, u));
             }
-            if (better_max(dm[s], j, bv, bi)) { bv = dm[s]; bi = j; }
+            if (r2 < v) {
+                v = r2;
+                dm[j] = v;
+            }
         }
+        if (better_max(v, j, bv, bi)) { bv = v; bi = j; }
+    }
+    warp_argmax(bv, bi);
+    if (lane == 0) { wv[wid] = bv; wi[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+        bv = (lane < FPS_T / 32) ? wv[lane] : -3.0;
+        bi = (lane < FPS_T / 32) ? wi[lane] : LLONG_MAX;
         warp_argmax(bv, bi);
-        if (lane == 0) { wv[wid] = bv; wi[wid] = bi; }
-        __syncthreads();
-        if (wid == 0) {
-            bv = (lane < FPS_T / 32) ? wv[lane] : -3.0;
-            bi = (lane < FPS_T / 32) ? wi[lane] : LLONG_MAX;
-            warp_argmax(bv, bi);
-            if (lane == 0) {
-                partv[(it & 1) * nb + blockIdx.x] = bv;
-                parti[(it & 1) * nb + blockIdx.x] = bi;
-            }
+        if (lane == 0) {
+            partv[blockIdx.x] = bv;
+            parti[blockIdx.x] = bi;
+            __threadfence();
+            last = atomicAdd(cnt, 1u) == gridDim.x - 1;
         }
-        if (!grid_barrier(bar, bar + 1, nb, err, BARRIER_LIMIT_NS)) return;
-        if (wid == 0) {
-            double v = -3.0;
-            int64_t ii = LLONG_MAX;
-            for (unsigned b = lane; b < nb; b += 32) {
-                double v2 = __ldcg(partv + (it & 1) * nb + b);
-                int64_t i2 = __ldcg(parti + (it & 1) * nb + b);
-                if (better_max(v2, i2, v, ii)) { v = v2; ii = i2; }
-            }
-            warp_argmax(v, ii);
-            if (lane == 0) lsel = ii;
-        }
-        __syncthreads();
-        l = lsel;
-        if (gtid == 0) idx[it] = l;
-#pragma unroll
-        for (int s = 0; s < PPT; ++s)
-            if (gtid + s * T == l) dm[s] = -1.0;
     }
-}
-
-template <int PPT>
-static cudaError_t launch_fps(int nb, const double *Xt, int64_t n, int d, int64_t k,
-                              int64_t start, int64_t *idx, double *pv, int64_t *pi,
-                              unsigned int *bar, int *err, cudaStream_t s)
-{
-    void *args[] = {(void *)&Xt, (void *)&n, (void *)&d, (void *)&k, (void *)&start,
-                    (void *)&idx, (void *)&pv, (void *)&pi, (void *)&bar, (void *)&err};
-    return cudaLaunchCooperativeKernel((void *)fps_kernel<PPT>, dim3(nb), dim3(FPS_T), args, 0, s);
-}
-
-template <int PPT>
-static int max_coop_blocks()
-{
-    int dev = 0, sms = 1, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fps_kernel<PPT>, FPS_T, 0);
-    return std::max(1, per) * sms;
+    __syncthreads();
+    if (!last || wid != 0) return;
+    __threadfence();
+    double v = -3.0;
+    int64_t ii = LLONG_MAX;
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
+        double v2 = __ldcg(partv + b);
+        int64_t i2 = __ldcg(parti + b);
+        if (better_max(v2, i2, v, ii)) { v = v2; ii = i2; }
+    }
+    warp_argmax(v, ii);
+    if (lane == 0) {
+        idx[it] = ii;
+        dm[ii] = -1.0;
+        *cnt = 0;
+    }
 }
 
 afn_status fps_run(const double *X, int64_t n, int d, int64_t k, int64_t start, int64_t *idx,
@@ -136,59 +118,30 @@ afn_status fps_run(const double *X, int64_t n, int d, int64_t k, int64_t start, 
                   (long long)k, (long long)start);
         return AFN_ERR_ARG;
     }
+    (void)status;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nb = (int)std::min<int64_t>((n + 2 * FPS_T - 1) / (2 * FPS_T), sms);
-    nb = std::max(nb, 1);
-    int64_t T = (int64_t)nb * FPS_T;
-    int64_t ppt = (n + T - 1) / T;
-    int P = ppt <= 1 ? 1 : ppt <= 2 ? 2 : ppt <= 4 ? 4 : ppt <= 8 ? 8 : ppt <= 16 ? 16 : 32;
-    if (ppt > 32) {
-        set_error("fps: n=%lld too large for one cooperative launch", (long long)n);
-        return AFN_ERR_ARG;
-    }
-    int cap = 0;
-    switch (P) {
-    case 1: cap = max_coop_blocks<1>(); break;
-    case 2: cap = max_coop_blocks<2>(); break;
-    case 4: cap = max_coop_blocks<4>(); break;
-    case 8: cap = max_coop_blocks<8>(); break;
-    case 16: cap = max_coop_blocks<16>(); break;
-    default: cap = max_coop_blocks<32>(); break;
-    }
-    if (nb > cap) {
-        set_error("fps: %d blocks exceed the co-resident limit %d", nb, cap);
-        return AFN_ERR_ARG;
-    }
-    DevBuf xt, pv, pi, bar;
+    // about 8 points per thread, at most 4 blocks per SM
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 8 * FPS_T - 1) / (8 * FPS_T),
+                                                               (int64_t)sms * 4));
+    DevBuf xt, dm, pv, pi, cnt;
     AFN_TRY(xt.alloc(sizeof(double) * (size_t)(n * d)));
-    AFN_TRY(pv.alloc(sizeof(double) * 2 * nb));
-    AFN_TRY(pi.alloc(sizeof(int64_t) * 2 * nb));
-    AFN_TRY(bar.alloc(sizeof(unsigned int) * 2));
-    AFN_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(unsigned int) * 2, s));
-    AFN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-    int64_t tot = n * d;
+    AFN_TRY(dm.alloc(sizeof(double) * (size_t)n));
+    AFN_TRY(pv.alloc(sizeof(double) * nb));
+    AFN_TRY(pi.alloc(sizeof(int64_t) * nb));
+    AFN_TRY(cnt.alloc(sizeof(unsigned int)));
+    const int64_t tot = n * d;
     to_soa_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, n, d, xt.as<double>());
-    cudaError_t e;
-    switch (P) {
-    case 1: e = launch_fps<1>(nb, xt.as<double>(), n, d, k, start, idx, pv.as<double>(), pi.as<int64_t>(), bar.as<unsigned int>(), status, s); break;
-    case 2: e = launch_fps<2>(nb, xt.as<double>(), n, d, k, start, idx, pv.as<double>(), pi.as<int64_t>(), bar.as<unsigned int>(), status, s); break;
-    case 4: e = launch_fps<4>(nb, xt.as<double>(), n, d, k, start, idx, pv.as<double>(), pi.as<int64_t>(), bar.as<unsigned int>(), status, s); break;
-    case 8: e = launch_fps<8>(nb, xt.as<double>(), n, d, k, start, idx, pv.as<double>(), pi.as<int64_t>(), bar.as<unsigned int>(), status, s); break;
-    case 16: e = launch_fps<16>(nb, xt.as<double>(), n, d, k, start, idx, pv.as<double>(), pi.as<int64_t>(), bar.as<unsigned int>(), status, s); break;
-    default: e = launch_fps<32>(nb, xt.as<double>(), n, d, k, start, idx, pv.as<double>(), pi.as<int64_t>(), bar.as<unsigned int>(), status, s); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "fps cooperative launch");
-    // the temporaries are released at scope exit: make sure the kernel is done
-    AFN_CUDA(cudaStreamSynchronize(s));
-    int hs = 0;
-    AFN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AFN_CUDA(cudaStreamSynchronize(s));
-    if (hs == DEV_TIMEOUT) {
-        set_error("fps: grid barrier wait exceeded its limit");
-        return AFN_ERR_TIMEOUT;
-    }
+    fps_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, start, dm.as<double>(), idx,
+                                                                  cnt.as<unsigned int>());
+    for (int64_t it = 1; it < k; ++it)
+        fps_step_kernel<<<nb, FPS_T, 0, s>>>(xt.as<double>(), n, d, it, idx, dm.as<double>(),
+                                             pv.as<double>(), pi.as<int64_t>(),
+                                             cnt.as<unsigned int>());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fps launch");
+    // the temporaries are released on stream s after the steps that use them
     return AFN_OK;
 }
 
