@@ -34,9 +34,13 @@ sys.path.insert(0, ROOT)
 LS = (0.5, 1.0, 2.0, 4.0)
 N, D, MU, KMAX, W, NRHS, TOL, SEED = 50_000, 8, 1e-2, 4000, 64, 32, 1e-6, 1002
 MAXIT = 3000   # per PCG solve; tol 1e-6 on these 8-D systems needs more than 500
+SERVE_MAXIT = 1000   # per request in the serving stream (a request past it reports unconverged)
 METRIC = "AFN-PCG solves/s at rel. residual 1e-6 (mixed precision, 8-D normal, n=50k, 32 RHS)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES, MUFU_PER_SM, SM_MAX_MHZ = 152, 128, 16, 2070.0
+# DRAM bytes read + written per launch of matvec32tca_kernel<8, 4, Gaussian> at n = 50,000,
+# 32 columns, from one ncu capture of that launch; to be re-taken when the kernel changes
+MATVEC32_TRAFFIC_BYTES = 20043008 + 302592
 
 
 def parse():
@@ -293,7 +297,7 @@ def run_serving(afn, count, rate, fp64_sample):
     args_ = [dict(points=s.X, kernel=s.kernel, l=s.l, mu=s.mu, k_max=s.k, fsai_nnz=s.w)
              for s in systems]
     cols = sum(s.nrhs for s in systems)
-    srv = afn.Server(seed=1005, max_iter=MAXIT, build_threads=8)
+    srv = afn.Server(seed=1005, max_iter=SERVE_MAXIT, build_threads=8)
     # warm-up request (graph capture, pool growth), not counted
     wid = srv.submit(args_[0], systems[0].B, TOL)
     while not srv.poll(wait_ms=100):
@@ -326,9 +330,10 @@ def run_serving(afn, count, rate, fp64_sample):
     lat = np.sort(np.array(lat))
     out = {"workload": "serving_stream: %d requests, n log-uniform [1e3, 1e5], d in {3,8,16}, "
                        "N(0,I), Gaussian/Matern-3/2 50/50, l = median dist x logU[0.1, 10], "
-                       "mu logU[1e-4, 1e-1], k = min(n/4, 1000), w = 32, 1-16 RHS, tol 1e-6; "
-                       "arrivals: %s" % (count, "Poisson %.3g/s" % rate if rate > 0 else
-                                         "all at t = 0 (saturation)"),
+                       "mu logU[1e-4, 1e-1], k = min(n/4, 1000), w = 32, 1-16 RHS, tol 1e-6, "
+                       "at most %d iterations; arrivals: %s"
+                       % (count, SERVE_MAXIT, "Poisson %.3g/s" % rate if rate > 0 else
+                          "all at t = 0 (saturation)"),
            "requests": count, "columns": cols, "converged_columns": conv, "makespan_s": span,
            "requests_per_s": count / span, "solves_per_s": cols / span,
            "latency_p50_ms": float(np.percentile(lat, 50)),
@@ -341,7 +346,7 @@ def run_serving(afn, count, rate, fp64_sample):
         g = np.random.Generator(np.random.PCG64(11))
         small = [i for i, s in enumerate(systems) if s.n <= 20_000]
         pick = sorted(g.choice(small, size=min(fp64_sample, len(small)), replace=False).tolist())
-        o64 = afn.options(precision=afn.PREC_FP64, seed=1005, max_iter=MAXIT)
+        o64 = afn.options(precision=afn.PREC_FP64, seed=1005, max_iter=SERVE_MAXIT)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         for i in pick:
@@ -477,7 +482,8 @@ def main():
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if mv_cnt else None
     peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": MATVEC32_TRAFFIC_BYTES if (n == N and nr_piece == 32) else None,
             "kernel": "matvec32tca_kernel<DS=8,NB=%d,Gaussian>" % (nr_piece // 8),
             "flops_per_pair": 3 * D + 2 * nr_piece,
             "pairs_per_launch": float(n) * n, "avg_launch_ms": avg_ms, "launches": mv_cnt,

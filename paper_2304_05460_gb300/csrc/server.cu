@@ -113,7 +113,7 @@ struct Server {
     std::thread sched;
     std::vector<std::thread> builders, singles;
     std::vector<cudaStream_t> bstreams, sstreams;
-    int nsingle = 4;
+    int nsingle = 6;
     std::atomic<double> df_share{1.0};    // GPU share of a one-at-a-time solve's matvec
 
     void build_loop(int t);
@@ -369,9 +369,9 @@ void Server::sched_loop()
             }
         }
         peak_live = std::max(peak_live, live);
-        // one-at-a-time solves take a quarter of the CTA slots while the group
+        // a one-at-a-time solve takes a fifth of the CTA slots while the group
         // has members (its short kernels then find free SMs), all otherwise
-        df_share = live > 0 ? 0.25 : 1.0;
+        df_share = live > 0 ? 0.2 : 1.0;
     }
     for (auto &kv : groups) delete kv.second;
 }
