@@ -152,6 +152,15 @@ __global__ void lmax_kernel(const double *dg, const double *of, int m, double *o
     *out = 0.5 * (lo + hi);
 }
 
+// A <- factor * (*base) I - A  (sz x sz)
+__global__ void shift_neg_kernel(double *A, int sz, const double *base, double factor)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)sz * sz) return;
+    const int64_t i = e / sz, j = e % sz;
+    A[e] = (i == j ? factor * (*base) : 0.0) - A[e];
+}
+
 __global__ void gather_scale_kernel(const double *__restrict__ X, const int64_t *__restrict__ idx,
                                     int64_t m, int d, double sc, double *__restrict__ out)
 {
@@ -280,19 +289,23 @@ afn_status rank_estimate(const double *X, int64_t n, int d, KParams kp, int m, u
     AFN_CUDA(cudaMemcpyAsync(Lo.p, Ko.p, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
     const double tiny = (double)m * 2.220446049250313e-16;   // max diag of K_o is 1
     AFN_TRY(cholesky64(Lo.as<double>(), m, status, s, tiny));
+    // ||E_r||_2 < 0.1 ||K_o||_2  <=>  every eigenvalue of the Schur complement
+    // E_r is below theta = 0.1 lambda_max(K_o)  <=>  theta I - E_r is positive
+    // definite, which a Cholesky decides (a quarter of the flops of the
+    // tridiagonalisation that the eigenvalue count would need)
     auto below = [&](int r, bool *res) -> afn_status {
         int sz = m - r;
         if (sz <= 0) { *res = true; return AFN_OK; }
         dim3 gg((unsigned)((sz + 63) / 64), (unsigned)((sz + 63) / 64));
         schur_kernel<<<gg, 256, 0, s>>>(Ko.as<double>(), Lo.as<double>(), m, r, E.as<double>());
-        AFN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-        AFN_TRY(tridiagonalize(E.as<double>(), sz, dg.as<double>(), of.as<double>(), status, s));
-        sturm_kernel<<<1, 1, 0, s>>>(dg.as<double>(), of.as<double>(), sz, lm.as<double>(), 0.1,
-                                     cnt.as<int>());
-        int hc = 0;
-        AFN_CUDA(cudaMemcpyAsync(&hc, cnt.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        const int64_t tot = (int64_t)sz * sz;
+        shift_neg_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(E.as<double>(), sz,
+                                                                       lm.as<double>(), 0.1);
+        AFN_TRY(cholesky64(E.as<double>(), sz, status, s, -1.0));
+        int hs = 0;
+        AFN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
         AFN_CUDA(cudaStreamSynchronize(s));
-        *res = (hc == sz);
+        *res = (hs == 0);
         return AFN_OK;
     };
     int lo = 1, hi = m;
