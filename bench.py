@@ -38,9 +38,9 @@ SERVE_MAXIT = 1000   # per request in the serving stream (a request past it repo
 METRIC = "AFN-PCG solves/s at rel. residual 1e-6 (mixed precision, 8-D normal, n=50k, 32 RHS)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES, MUFU_PER_SM, SM_MAX_MHZ = 152, 128, 16, 2070.0
-# DRAM bytes read + written per launch of matvec32tca_kernel<8, 4, Gaussian> at n = 50,000,
-# 32 columns, from one ncu capture of that launch; to be re-taken when the kernel changes
-MATVEC32_TRAFFIC_BYTES = 20043008 + 302592
+# DRAM bytes read + written per launch of the dominant FP32 matvec kernel at n = 50,000,
+# 32 columns, from one ncu capture of that launch (None until taken for the current kernel)
+MATVEC32_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -484,10 +484,19 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": MATVEC32_TRAFFIC_BYTES if (n == N and nr_piece == 32) else None,
-            "kernel": "matvec32tca_kernel<DS=8,NB=%d,Gaussian>" % (nr_piece // 8),
+            "kernel": ("matvec32u_kernel<DS=8,NB=%d,Gaussian,direct> (tcgen05)" % (nr_piece // 8)
+                       if nr_piece >= 16 else "matvec32tca_kernel<DS=8,NB=%d,Gaussian>" % (nr_piece // 8)),
             "flops_per_pair": 3 * D + 2 * nr_piece,
             "pairs_per_launch": float(n) * n, "avg_launch_ms": avg_ms, "launches": mv_cnt,
             "peak_basis": "FP32 pipe: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"}
+    if achieved and nr_piece >= 16:
+        # the contraction runs on the tensor cores; the FP32 pipe still evaluates every
+        # kernel value: d subtractions, d FMAs and the split, 2d + 1 lane-operations a pair
+        pairs_s = float(n) * n / (avg_ms / 1e3)
+        eval_peak = N_SM * FP32_LANES * SM_MAX_MHZ * 1e6 / (2 * D + 1)
+        roof["eval_bound"] = {"pairs_per_s": pairs_s, "peak_pairs_per_s": eval_peak,
+                              "frac": pairs_s / eval_peak,
+                              "basis": "FP32 pipe, 2d+1 lane-ops per kernel value (derived)"}
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in stats.items()}
     step_ms = ms / args.steps
 

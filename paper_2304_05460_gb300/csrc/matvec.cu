@@ -16,6 +16,7 @@
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
 #include "matvec_tc.cuh"
+#include "matvec_umma.cuh"
 #include "matvec_df.cuh"
 #include "group.cuh"
 
@@ -407,16 +408,155 @@ __global__ void psplit_kernel(const float *__restrict__ P, int64_t ldp, int64_t 
 }
 
 static int64_t tc_npad(int64_t n) { return (n + TCJ - 1) / TCJ * TCJ; }
+static_assert(TCJ % UJ == 0, "the prepared arrays of both tensor-core paths share npad");
+
+// Xpr: per stage of UJ points, the point tile of matvec32u_kernel for the
+// distance form VAR (zero rows up to npad); the norms are the FMA chain the
+// kernel uses for its dot products
+template <int VAR>
+__global__ void upoints_kernel(const float *__restrict__ Xs, int64_t n, int ds, int64_t npad,
+                               float *__restrict__ Xpr)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npad) return;
+    const int64_t base = (j / UJ) * (int64_t)UJ * (ds + (VAR == UDIRECT ? 0 : 1));
+    const int jj = (int)(j % UJ);
+    float nrm = 0.f;
+    for (int q = 0; q < ds; ++q) {
+        const float v = j < n ? Xs[j * ds + q] : 0.f;
+        nrm = __fmaf_rn(v, v, nrm);
+        if (VAR == UNORM) Xpr[base + (int64_t)jj * ds + q] = v;
+        else Xpr[base + (int64_t)(jj & ~1) * ds + 2 * q + (jj & 1)] = v;
+    }
+    if (VAR != UDIRECT) Xpr[base + (int64_t)UJ * ds + jj] = nrm;
+}
+
+// Pk: per stage of UJ points, the tf32 hi then lo halves of p in the K-major
+// core-matrix layout of matvec32u_kernel, zero rows up to npad
+template <int NR>
+__global__ void ksplit_kernel(const float *__restrict__ P, int64_t ldp, int64_t n, int64_t npad,
+                              uint32_t *__restrict__ Pk)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npad * NR) return;
+    const int64_t j = e % npad;
+    const int c = (int)(e / npad);
+    uint32_t hi, lo;
+    tf32_split(j < n ? P[c * ldp + j] : 0.f, hi, lo);
+    const int64_t st = j / UJ;
+    const int jj = (int)(j % UJ);
+    const int64_t w = st * (2 * UJ * NR) + (c / 8) * (UJ / 4) * 32 + (jj / 4) * 32 + (c % 8) * 4 +
+                      (jj % 4);
+    Pk[w] = hi;
+    Pk[w + UJ * NR] = lo;
+}
+
+static constexpr int UJS_MAX = 8;   // j-chunks of the tcgen05 path
+
+// j-chunks (in staged tiles) of the tcgen05 path: the count whose CTAs fill
+// the last wave of 2 CTAs per SM best, chunks of at least 4 tiles
+static void chunking_u(int64_t n, int64_t nstage, int &js, int64_t &chunk_st)
+{
+    const int64_t rt = (n + UR - 1) / UR;
+    const int64_t slots = 2 * (int64_t)num_sms();
+    double best = -1.0;
+    js = 1;
+    chunk_st = nstage;
+    for (int q = 1; q <= UJS_MAX; ++q) {
+        const int64_t cs = (nstage + q - 1) / q;
+        if (q > 1 && cs < 4) break;
+        const int64_t jq = (nstage + cs - 1) / cs;
+        const int64_t tot = rt * jq;
+        const int64_t waves = (tot + slots - 1) / slots;
+        const double eff = (double)tot / (double)(waves * slots);
+        if (eff > best + 1e-9) {
+            best = eff;
+            js = (int)jq;
+            chunk_st = cs;
+        }
+    }
+}
+
+// AFN_MATVEC_TC=mma selects the mma.sync kernel for 16 and 32 right-hand
+// sides as well (comparison runs); the default is the tcgen05 kernel
+static bool use_umma()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("AFN_MATVEC_TC");
+        v = (e && strcmp(e, "mma") == 0) ? 0 : 1;
+    }
+    return v == 1;
+}
+
+template <int DS, int NB, int KER, int VAR, int UH>
+static void launch_u(const float *Xs, int64_t n, const float *Xpr, const uint32_t *Pk, float *part,
+                     int js, int64_t chunk_st, int64_t nstage, int *err, cudaStream_t s)
+{
+    // at least 80 KB of shared memory keeps residency at 2 CTAs per SM, the
+    // number whose tensor-memory allocations fit together
+    const int smem = std::max(UNST * UStage<DS, NB * 8, VAR>::BYTES, 80 * 1024);
+    cudaFuncSetAttribute(matvec32u_kernel<DS, NB, KER, VAR, UH>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 g((unsigned)((n + UR - 1) / UR), (unsigned)js);
+    matvec32u_kernel<DS, NB, KER, VAR, UH><<<g, umma_threads(UH), smem, s>>>(
+        Xs, n, Xpr, Pk, part, chunk_st, nstage, err);
+}
+
+// distance form and row-warp split of the tcgen05 path (AFN_UMMA_VARIANT =
+// d1 d2 n1 n2 m1 m2: UDIRECT / UNORM / UNORM2, 1 or 2 row warps per lane
+// quarter; comparison runs only).  The default d1 is the fastest solve: the
+// norm forms save FP32 work but their larger distance error for close pairs
+// costs PCG iterations (l = 4: 740 against 624).
+static int umma_variant()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("AFN_UMMA_VARIANT");
+        v = 0;   // UDIRECT, UH = 1
+        if (e && strlen(e) == 2 && strchr("dnm", e[0]) && (e[1] == '1' || e[1] == '2'))
+            v = (e[0] == 'd' ? 0 : e[0] == 'n' ? 2 : 4) + (e[1] - '1');
+    }
+    return v;
+}
+
+// the tuning variants exist for d = 8, 32 right-hand sides, the Gaussian
+// kernel; every other shape takes the default
+template <int DS, int NB, int KER>
+static void launch_u_any(const float *Xs, int64_t n, float *Xpr, const uint32_t *Pk, float *part,
+                         int js, int64_t chunk_st, int64_t npad, int *err, cudaStream_t s)
+{
+    const int64_t nst = npad / UJ;
+    const unsigned gb = (unsigned)((npad + 255) / 256);
+    int v = 0;
+    if constexpr (DS == 8 && NB == 4 && KER == 0) v = umma_variant();
+    const int form = v / 2 == 0 ? UDIRECT : v / 2 == 1 ? UNORM : UNORM2;
+    if (form == UDIRECT) upoints_kernel<UDIRECT><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
+    else if (form == UNORM) upoints_kernel<UNORM><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
+    else upoints_kernel<UNORM2><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
+    if constexpr (DS == 8 && NB == 4 && KER == 0) {
+        switch (v) {
+        case 1: launch_u<DS, NB, KER, UDIRECT, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 2: launch_u<DS, NB, KER, UNORM, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 3: launch_u<DS, NB, KER, UNORM, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 4: launch_u<DS, NB, KER, UNORM2, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 5: launch_u<DS, NB, KER, UNORM2, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        default: break;
+        }
+    }
+    launch_u<DS, NB, KER, UDIRECT, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+}
 
 size_t matvec32_scratch(int64_t n, int nrhs)
 {
-    const size_t part = sizeof(float) * (size_t)pick_js(n) *
+    const size_t part = sizeof(float) * (size_t)std::max(pick_js(n), UJS_MAX) *
                         (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
     const size_t np = (size_t)tc_npad(n);
     const size_t dup = sizeof(f2_t) * np * 18;                     // DS + 2 <= 18
     const size_t psp = sizeof(uint32_t) * np * TcRow<4>::ROW;
     return (part + 255) / 256 * 256 + (dup + 255) / 256 * 256 + psp + 256;
 }
+
 
 template <int DS, int NB, int KER>
 static void launch_tca(const float *Xs, int64_t n, const f2_t *Xdup, const uint32_t *Psp,
@@ -429,11 +569,15 @@ static void launch_tca(const float *Xs, int64_t n, const f2_t *Xdup, const uint3
     matvec32tca_kernel<DS, NB, KER><<<g, 256, smem, s>>>(Xs, n, Xdup, Psp, part, chunk, err);
 }
 
-struct TcPrep {           // prepared operands of the asynchronous TC path
-    const f2_t *Xdup;
-    uint32_t *Psp;
+
+struct TcPrep {           // prepared operands of the asynchronous TC paths
+    f2_t *Xdup;              // mma.sync path: duplicated points; tcgen05 path: Xpr
+    uint32_t *Psp;           // mma.sync path: Psp; tcgen05 path: Pk
     int64_t npad;
     int *err;
+    bool umma;               // tcgen05 path for 16 and 32 right-hand sides
+    int jsu;                 // its j-chunks
+    int64_t chunk_st;
 };
 
 template <int D, int NR, int KER>
@@ -446,6 +590,16 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
 #else
     constexpr bool use_tc = true;
 #endif
+    if constexpr (NR >= 16 && use_tc) {
+        if (tp.umma) {
+            constexpr int DS = (D == 3 ? 4 : D);
+            const int64_t tot = tp.npad * NR;
+            ksplit_kernel<NR><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, n, n, tp.npad, tp.Psp);
+            launch_u_any<DS, NR / 8, KER>(Xs, n, reinterpret_cast<float *>(tp.Xdup),
+                                          tp.Psp, part, tp.jsu, tp.chunk_st, tp.npad, tp.err, s);
+            return;
+        }
+    }
     if constexpr (NR >= 8 && use_tc) {
         constexpr int DS = (D == 3 ? 4 : D);
         const int64_t tot = tp.npad * NR;
@@ -507,12 +661,16 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
     tp.err = err;
     {
         char *b = static_cast<char *>(scratch);
-        const size_t pb = sizeof(float) * (size_t)js * (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
+        const size_t pb = sizeof(float) * (size_t)std::max(js, UJS_MAX) *
+                          (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
         f2_t *xd = reinterpret_cast<f2_t *>(b + (pb + 255) / 256 * 256);
         const size_t db = sizeof(f2_t) * (size_t)tp.npad * 18;
         tp.Psp = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(xd) + (db + 255) / 256 * 256);
         tp.Xdup = xd;
-        if (nrhs >= 8) {
+        tp.umma = use_umma() && nrhs >= 16 && nrhs % 16 == 0;
+        if (tp.umma) {
+            chunking_u(n, tp.npad / UJ, tp.jsu, tp.chunk_st);
+        } else if (nrhs >= 8) {
             const int ds = stored_dim32(dp);
             const int64_t tot = tp.npad * (ds + 2);
             dup_points_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Xs, n, ds, tp.npad, xd);
@@ -528,8 +686,9 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
         if (kernel == 0) launch32_d<0>(dp, b, Xs, n, pp, part, js, chunk, tp, s);
         else launch32_d<1>(dp, b, Xs, n, pp, part, js, chunk, tp, s);
         int64_t tot = n * b;
+        const int jsb = (tp.umma && b >= 16) ? tp.jsu : js;
         matvec_finish<float><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-            part, js, b, n, pp, n, q + (int64_t)c0 * n, n, mu);
+            part, jsb, b, n, pp, n, q + (int64_t)c0 * n, n, mu);
         c0 += b;
     }
     cudaError_t e = cudaGetLastError();

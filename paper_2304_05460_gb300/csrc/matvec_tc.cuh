@@ -37,6 +37,7 @@ __device__ __forceinline__ uint32_t tf32_bits(float x)
 #define AFN_TC_KAHAN 1
 #endif
 static constexpr int TC_FOLD = AFN_TC_FOLD;        // blocks of 8 points per accumulator fold
+static_assert(TC_FOLD >= 1 && 8 % TC_FOLD == 0, "a fold chunk must not cross a staged tile");
 static constexpr bool TC_KAHAN = AFN_TC_KAHAN != 0;
 
 // x = hi + lo with hi, lo tf32 (10-bit mantissa) values, each rounded to
@@ -60,6 +61,16 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1
                  "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
                  : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// c = A B (the accumulator input is zero: no registers to clear)
+__device__ __forceinline__ void mma_tf32_z(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                           uint32_t a3, uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, "
+                 "{%4,%5,%6,%7}, {%8,%9}, {%10,%10,%10,%10};"
+                 : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f));
 }
 
 static constexpr int TCR = 128;   // rows per CTA (8 warps x 16)
@@ -296,15 +307,14 @@ __device__ __forceinline__ bool mv32tc_rows_async(const float *__restrict__ Xs, 
 #pragma unroll
     for (int q = 0; q < DS; ++q)
         xi[q] = f2_pack(ia < n ? Xs[ia * DS + q] : 0.f, ib < n ? Xs[ib * DS + q] : 0.f);
-    float cmp[TC_KAHAN ? NB : 1][4];
+    // running sums and Kahan compensations as packed pairs of the C-fragment
+    // registers (0,1) and (2,3): one f32x2 instruction per two elements,
+    // rounding identical to the scalar sequence
+    f2_t acc2[NB][2], cmp2[TC_KAHAN ? NB : 1][2];
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
+    for (int b = 0; b < NB; ++b) acc2[b][0] = acc2[b][1] = 0ull;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[b][r] = 0.f;
-#pragma unroll
-    for (int b = 0; b < (TC_KAHAN ? NB : 1); ++b)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) cmp[b][r] = 0.f;
+    for (int b = 0; b < (TC_KAHAN ? NB : 1); ++b) cmp2[b][0] = cmp2[b][1] = 0ull;
 
     const int ntiles = (int)((j1 - j0 + TCJ - 1) / TCJ);
     auto issue = [&](int it) {
@@ -330,10 +340,6 @@ __device__ __forceinline__ bool mv32tc_rows_async(const float *__restrict__ Xs, 
         const f2_t *xsd = reinterpret_cast<const f2_t *>(stage + b * SB);
         const uint32_t *pw = reinterpret_cast<const uint32_t *>(stage + b * SB + TcStage<DS, NB>::PTS);
         float tac[NB][4];
-#pragma unroll
-        for (int bb = 0; bb < NB; ++bb)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) tac[bb][r] = 0.f;
 #pragma unroll
         for (int kb = 0; kb < TCJ / 8; ++kb) {
             const f2_t *xa = xsd + (kb * 8 + t) * DSP;
@@ -366,7 +372,9 @@ __device__ __forceinline__ bool mv32tc_rows_async(const float *__restrict__ Xs, 
             for (int bb = 0; bb < NB; ++bb) {
                 const uint32_t bh0 = p0[bb * 8], bh1 = p1[bb * 8];
                 const uint32_t bl0 = p0[PS + bb * 8], bl1 = p1[PS + bb * 8];
-                mma_tf32(tac[bb], al0, al1, al2, al3, bh0, bh1);
+                // the first product of a fold chunk starts from zero
+                if (kb % TC_FOLD == 0) mma_tf32_z(tac[bb], al0, al1, al2, al3, bh0, bh1);
+                else mma_tf32(tac[bb], al0, al1, al2, al3, bh0, bh1);
                 mma_tf32(tac[bb], ah0, ah1, ah2, ah3, bl0, bl1);
                 mma_tf32(tac[bb], ah0, ah1, ah2, ah3, bh0, bh1);
             }
@@ -374,20 +382,25 @@ __device__ __forceinline__ bool mv32tc_rows_async(const float *__restrict__ Xs, 
 #pragma unroll
                 for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
+                    for (int h = 0; h < 2; ++h) {
+                        const f2_t tv = f2_pack(tac[bb][2 * h], tac[bb][2 * h + 1]);
                         if constexpr (TC_KAHAN) {
-                            float y = tac[bb][r] - cmp[bb][r];
-                            float s = acc[bb][r] + y;
-                            cmp[bb][r] = (s - acc[bb][r]) - y;
-                            acc[bb][r] = s;
+                            const f2_t y = f2_sub(tv, cmp2[bb][h]);
+                            const f2_t s = f2_add(acc2[bb][h], y);
+                            cmp2[bb][h] = f2_sub(f2_sub(s, acc2[bb][h]), y);
+                            acc2[bb][h] = s;
                         } else {
-                            acc[bb][r] += tac[bb][r];
+                            acc2[bb][h] = f2_add(acc2[bb][h], tv);
                         }
-                        tac[bb][r] = 0.f;
                     }
             }
         }
         __syncthreads();   // buffer b is free for the copies of tile it + 2
+    }
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb) {
+        f2_unpack(acc2[bb][0], acc[bb][0], acc[bb][1]);
+        f2_unpack(acc2[bb][1], acc[bb][2], acc[bb][3]);
     }
     if (!ok && threadIdx.x == 0) {
         // copies issued but not consumed (tiles it and it + 1): wait for them,
