@@ -38,9 +38,9 @@ SERVE_MAXIT = 1000   # per request in the serving stream (a request past it repo
 METRIC = "AFN-PCG solves/s at rel. residual 1e-6 (mixed precision, 8-D normal, n=50k, 32 RHS)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES, MUFU_PER_SM, SM_MAX_MHZ = 152, 128, 16, 2070.0
-# DRAM bytes read + written per launch of the dominant FP32 matvec kernel at n = 50,000,
-# 32 columns, from one ncu capture of that launch (None until taken for the current kernel)
-MATVEC32_TRAFFIC_BYTES = None
+# DRAM bytes read + written per launch of matvec32u_kernel<8, 4, Gaussian> at n = 50,000,
+# 32 columns, from one ncu capture of that launch; to be re-taken when the kernel changes
+MATVEC32_TRAFFIC_BYTES = 16048128 + 0
 
 
 def parse():
