@@ -162,7 +162,11 @@ afn_status afn_get_G(const afn_handle *h, int32_t *pattern, double *values);
 /* W = L^{-1} K12 as nr x k row-major (row j = column j of W), FP64 or the
  * precision the handle keeps (FP64 handle: FP64; mixed: FP32 converted). */
 afn_status afn_get_W(const afn_handle *h, double *Wt);
-/* s = M^{-1} r for nrhs columns (Alg. 3), FP64, vectors in PERMUTED order. */
+/* s = M^{-1} r for nrhs columns (Alg. 3), vectors in PERMUTED order, FP64 in
+ * and out.  FP64 handles apply in FP64; mixed handles run the FP32 apply of
+ * their solves (r rounded to FP32; with AFN_APPLY_TC=1 in the environment
+ * and a multiple of 16 columns the W products run on the tensor cores).
+ * AFN_ERR_TIMEOUT if a staged copy or MMA did not complete. */
 afn_status afn_apply_precond(afn_handle *h, const double *r, int32_t nrhs, double *s);
 
 /* per-kernel timing gathered while opt.profile was set (CUDA events on the

@@ -286,7 +286,8 @@ def afn_get_W(h: Handle):
 
 
 def afn_apply_precond(h: Handle, r):
-    """M^{-1} r (Alg. 3), FP64 handles; r in PERMUTED order, (n,) or (n, nrhs)."""
+    """M^{-1} r (Alg. 3); r in PERMUTED order, (n,) or (n, nrhs).  FP64 handles
+    apply in FP64, mixed handles run the FP32 apply of their solves."""
     R, nrhs = _f64_colmajor(r)
     out = np.empty(R.shape, dtype=np.float64)
     pr, kr = _ptr(R)

@@ -108,6 +108,8 @@ struct Handle {
     DevBuf LinvT32;   // float  [k*k]
     DevBuf Wt;        // double [nr*k]  (FP64 handles)
     DevBuf Wt32;      // float  [nr*k]  (mixed handles)
+    DevBuf Wu1, Wu2;  // float tiled images of W^T and W for the tcgen05 apply (built on first use)
+    bool wu_tried = false;
     DevBuf pat;       // int32 [nr*w]
     DevBuf G;         // double [nr*w]
     DevBuf G32;       // float  [nr*w]
@@ -225,6 +227,9 @@ template <class T>
 afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt, const T *G,
                      const T *r, int nrhs, T *s, T *tmp, cudaStream_t st);
 size_t apply_tmp_elems(const Handle *h, int nrhs);
+// tiled images of W for the tcgen05 apply of a mixed handle (no-op when they
+// exist, the handle has no W, or AFN_APPLY_TC=1 is not set)
+afn_status apply_tc_prepare(Handle *h, cudaStream_t s);
 
 // ---- grouped steps (many systems per launch; group.cuh describes the group)
 struct GDev;

@@ -9,10 +9,13 @@
 // bound by HBM bandwidth: W^T (nr x k) is read twice, L^{-1} and L^{-T} once,
 // G twice.  Vectors are n x nrhs column-major (ld = n) in permuted order.
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
 #include "gemm_tile.cuh"
+#include "gemm_umma.cuh"
 #include "group.cuh"
 
 namespace afn {
@@ -368,12 +371,155 @@ static int colmul_js(int64_t nrows, int64_t ncols)
 
 static constexpr int GEMM_JS_MAX = 64;
 
+// words of the split vector block of the tcgen05 products (both products, 32 columns)
+static int64_t gu_bk_words(int64_t nr, int64_t k)
+{
+    return 2 * 32 * ((std::max(nr, k) + GKU - 1) / GKU * GKU);
+}
+
 size_t apply_tmp_elems(const Handle *h, int nrhs)
 {
     int64_t k = h->k, nr = h->nr;
     int js = std::max(colmul_js(nr, k), GEMM_JS_MAX);
-    // zp, u (k x nrhs), t, y (nr x nrhs), GEMM partials, row-major copy (nr x nrhs)
-    return (size_t)(2 * k * nrhs + 3 * nr * nrhs) + (size_t)js * 32 * (size_t)std::max<int64_t>(k, 1) + 64;
+    // zp, u (k x nrhs), t, y (nr x nrhs), GEMM partials, row-major copy (nr x nrhs), split
+    // vector block of the tcgen05 products
+    return (size_t)(2 * k * nrhs + 3 * nr * nrhs) + (size_t)js * 32 * (size_t)std::max<int64_t>(k, 1) +
+           (size_t)gu_bk_words(nr, k) + 64;
+}
+
+// ------------------------------------------------ tcgen05 W products --------
+// Atl (see gemm32u_kernel): A[row][kk] = Wt[row k + kk] (trans = 0, M = nr,
+// K = k) or Wt[kk k + row] (trans = 1, M = k, K = nr), zero outside
+__global__ void gu_arrange_kernel(const float *__restrict__ Wt, int64_t k, int trans, int64_t M,
+                                  int64_t K, int64_t nks, float *__restrict__ Atl, int64_t total)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t per = nks * (UR * GKU);
+    const int64_t rt = e / per, rem = e % per;
+    const int64_t st = rem / (UR * GKU);
+    const int wd = (int)(rem % (UR * GKU));
+    const int row = (wd / ((GKU / 4) * 32)) * 8 + (wd % 32) / 4;
+    const int kk = ((wd % ((GKU / 4) * 32)) / 32) * 4 + wd % 4;
+    const int64_t gi = rt * UR + row, gk = st * GKU + kk;
+    float v = 0.f;
+    if (gi < M && gk < K) v = trans ? Wt[gk * k + gi] : Wt[gi * k + gk];
+    Atl[e] = v;
+}
+
+// Bk: the K x NR block of X (column-major, leading dimension ldx) split into
+// tf32 hi / lo, per stage of GKU rows the hi then lo halves in the K-major
+// core-matrix layout of gemm32u_kernel, zero past K
+template <int NR>
+__global__ void gu_bsplit_kernel(const float *__restrict__ X, int64_t ldx, int64_t K, int64_t nks,
+                                 uint32_t *__restrict__ Bk)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t kp = nks * GKU;
+    if (e >= kp * NR) return;
+    const int64_t kg = e % kp;
+    const int c = (int)(e / kp);
+    uint32_t hi, lo;
+    tf32_split(kg < K ? X[c * ldx + kg] : 0.f, hi, lo);
+    const int64_t st = kg / GKU;
+    const int kk = (int)(kg % GKU);
+    const int64_t w = st * (2 * GKU * NR) + (c / 8) * (GKU / 4) * 32 + (kk / 4) * 32 + (c % 8) * 4 +
+                      (kk % 4);
+    Bk[w] = hi;
+    Bk[w + GKU * NR] = lo;
+}
+
+// AFN_APPLY_TC=1 runs the W products on the tensor cores (read at every
+// apply).  Off by default: on the normal_8d systems the products are 1.5x
+// faster but the solve takes 5 % more iterations (l = 2: 1044 against 992),
+// a net loss.
+static bool use_apply_tc()
+{
+    const char *e = getenv("AFN_APPLY_TC");
+    return e && strcmp(e, "1") == 0;
+}
+
+static int64_t gu_nks(int64_t K) { return (K + GKU - 1) / GKU; }
+static int64_t gu_tiles(int64_t M) { return (M + UR - 1) / UR; }
+
+afn_status apply_tc_prepare(Handle *h, cudaStream_t s)
+{
+    if (h->wu_tried || !use_apply_tc()) return AFN_OK;
+    h->wu_tried = true;
+    const int64_t k = h->k, nr = h->nr;
+    // small products stay on the CUDA-core tiles
+    if (!h->Wt32.p || k < 128 || nr < 128) return AFN_OK;
+    const int64_t n1 = gu_tiles(nr) * gu_nks(k) * (UR * GKU);
+    const int64_t n2 = gu_tiles(k) * gu_nks(nr) * (UR * GKU);
+    AFN_TRY(h->Wu1.alloc(sizeof(float) * (size_t)n1));
+    AFN_TRY(h->Wu2.alloc(sizeof(float) * (size_t)n2));
+    gu_arrange_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(h->Wt32.as<float>(), k, 0, nr, k,
+                                                                   gu_nks(k), h->Wu1.as<float>(), n1);
+    gu_arrange_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(h->Wt32.as<float>(), k, 1, k, nr,
+                                                                   gu_nks(nr), h->Wu2.as<float>(), n2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "apply tile images");
+    return AFN_OK;
+}
+
+// j-chunks of a tcgen05 product: 1 CTA per SM; the count whose CTAs fill the
+// last wave best, chunks of at least 8 stages, partials within cap
+static void gu_chunking(int64_t M, int64_t nks, size_t cap_words, int nr, int &js, int64_t &cs)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t rt = gu_tiles(M);
+    double best = -1.0;
+    js = 1;
+    cs = nks;
+    for (int q = 1; q <= 64; ++q) {
+        const int64_t c = (nks + q - 1) / q;
+        if (q > 1 && c < 8) break;
+        const int64_t jq = (nks + c - 1) / c;
+        if ((size_t)jq * (size_t)nr * (size_t)M > cap_words) break;
+        const int64_t tot = rt * jq, waves = (tot + sms - 1) / sms;
+        const double eff = (double)tot / (double)(waves * sms);
+        if (eff > best + 1e-9) {
+            best = eff;
+            js = (int)jq;
+            cs = c;
+        }
+    }
+}
+
+// O = beta Y + alpha A X on the tensor cores for nrhs columns (a multiple of 16)
+static afn_status prod_tc(const float *Atl, int64_t M, int64_t K, const float *X, int64_t ldx,
+                          const float *Y, int64_t ldy, float *O, int64_t ldo, float alpha, float beta,
+                          int nrhs, float *part, size_t pcap, uint32_t *Bk, int *err, cudaStream_t s)
+{
+    const int64_t nks = gu_nks(K);
+    for (int c0 = 0; c0 < nrhs;) {
+        const int b = (nrhs - c0) >= 32 ? 32 : 16;
+        int js;
+        int64_t cs;
+        gu_chunking(M, nks, pcap, b, js, cs);
+        const int64_t tot = nks * GKU * b;
+        dim3 grid((unsigned)gu_tiles(M), (unsigned)js);
+        if (b == 32) {
+            gu_bsplit_kernel<32><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X + c0 * ldx, ldx, K, nks, Bk);
+            const int smem = GNST * GStage<32>::BYTES;
+            cudaFuncSetAttribute(gemm32u_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            gemm32u_kernel<4><<<grid, GUT, smem, s>>>(Atl, M, nks, Bk, part, cs, err);
+        } else {
+            gu_bsplit_kernel<16><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X + c0 * ldx, ldx, K, nks, Bk);
+            const int smem = GNST * GStage<16>::BYTES;
+            cudaFuncSetAttribute(gemm32u_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            gemm32u_kernel<2><<<grid, GUT, smem, s>>>(Atl, M, nks, Bk, part, cs, err);
+        }
+        const int64_t te = M * b;
+        gemm_finish<float><<<(unsigned)((te + 255) / 256), 256, 0, s>>>(
+            part, js, b, M, Y ? Y + c0 * ldy : nullptr, ldy, O + c0 * ldo, ldo, alpha, beta);
+        c0 += b;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tcgen05 apply product");
+    return AFN_OK;
 }
 
 static int gemm_js(int64_t M, int64_t K)
@@ -457,9 +603,19 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
                         (size_t)std::max<int64_t>(k, 1);
     const T *r1 = r, *r2 = r + k;
     T *s1 = s, *s2 = s + k;
+    // tcgen05 W products (mixed handles with tiled images, 16 or 32 columns a piece)
+    const bool tc = std::is_same<T, float>::value && h->Wu1.p && h->Wu2.p && nrhs % 16 == 0 &&
+                    use_apply_tc() &&
+                    (size_t)32 * (size_t)std::max(nr, k) <= pcap;
+    uint32_t *Bk = reinterpret_cast<uint32_t *>(part + pcap + nr * nrhs);
+    int *err = h->status.as<int>() + 3;
     if (k > 0) prod<T, false, 1>(Linv, k, k, k, r1, n, nullptr, 0, zp, k, (T)1, (T)0, nrhs, part, pcap, st);
     if (nr > 0) {
-        if (k > 0) prod<T, false, 0>(Wt, k, nr, k, zp, k, r2, n, t, nr, (T)-1, (T)1, nrhs, part, pcap, st);
+        if (k > 0 && tc) {
+            if constexpr (std::is_same<T, float>::value)
+                AFN_TRY(prod_tc(h->Wu1.as<float>(), nr, k, zp, k, r2, n, t, nr, -1.f, 1.f, nrhs, part,
+                                pcap, Bk, err, st));
+        } else if (k > 0) prod<T, false, 0>(Wt, k, nr, k, zp, k, r2, n, t, nr, (T)-1, (T)1, nrhs, part, pcap, st);
         else {
             int64_t tot = nr * nrhs;
             copy_cols_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r2, n, t, nr, nr, nrhs);
@@ -483,7 +639,11 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
         }
     }
     if (k > 0) {
-        if (nr > 0) {
+        if (nr > 0 && tc) {
+            if constexpr (std::is_same<T, float>::value)
+                AFN_TRY(prod_tc(h->Wu2.as<float>(), k, nr, s2, n, zp, k, u, k, -1.f, 1.f, nrhs, part,
+                                pcap, Bk, err, st));
+        } else if (nr > 0) {
             prod<T, true, 0>(Wt, k, k, nr, s2, n, zp, k, u, k, (T)-1, (T)1, nrhs, part, pcap, st);
         } else {
             int64_t tot = k * nrhs;

@@ -159,7 +159,7 @@ Profiler::~Profiler()
 
 int64_t Handle::device_bytes() const
 {
-    const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32,
+    const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32, &Wu1, &Wu2,
                          &pat, &G, &G32, &gt_ptr, &gt_row, &gt_slot, &status, &ws};
     int64_t s = 0;
     for (auto x : b) s += (int64_t)x->bytes;
@@ -765,10 +765,6 @@ afn_status afn_apply_precond(afn_handle *hh, const double *r, int32_t nrhs, doub
 {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h || !r || !s_out || nrhs < 1) { set_error("invalid argument"); return AFN_ERR_ARG; }
-    if (h->precision == AFN_PREC_MIXED) {
-        set_error("afn_apply_precond: FP64 handles only");
-        return AFN_ERR_ARG;
-    }
     cudaStream_t s = h->stream;
     StreamGuard sg(s);
     int64_t tot = h->n * nrhs;
@@ -777,6 +773,28 @@ afn_status afn_apply_precond(afn_handle *hh, const double *r, int32_t nrhs, doub
     AFN_TRY(to_device(r, tot, rin, &R, s));
     AFN_TRY(sd.alloc(sizeof(double) * tot));
     AFN_TRY(tmp.alloc(sizeof(double) * apply_tmp_elems(h, nrhs)));
+    if (h->precision == AFN_PREC_MIXED) {
+        // the FP32 apply of the mixed solve (tensor-core W products for 16k columns)
+        DevBuf r32, s32;
+        AFN_TRY(r32.alloc(sizeof(float) * tot));
+        AFN_TRY(s32.alloc(sizeof(float) * tot));
+        AFN_TRY(convert64to32(R, r32.as<float>(), tot, s));
+        if (nrhs % 16 == 0) AFN_TRY(apply_tc_prepare(h, s));
+        AFN_TRY(afn_apply<float>(h, h->Linv32.as<float>(), h->LinvT32.as<float>(),
+                                 h->Wt32.as<float>(), h->G32.as<float>(), r32.as<float>(), nrhs,
+                                 s32.as<float>(), tmp.as<float>(), s));
+        AFN_TRY(convert32to64(s32.as<float>(), sd.as<double>(), tot, s));
+        AFN_CUDA(cudaStreamSynchronize(s));
+        if (h->status.p) {
+            int hs[4];
+            AFN_CUDA(cudaMemcpy(hs, h->status.p, sizeof(hs), cudaMemcpyDeviceToHost));
+            if (hs[3] != 0) {
+                set_error("afn_apply_precond: a staged copy or MMA did not complete in time");
+                return AFN_ERR_TIMEOUT;
+            }
+        }
+        return copy_out(s_out, sd.p, sizeof(double) * tot);
+    }
     AFN_TRY(afn_apply<double>(h, h->Linv.as<double>(), h->LinvT.as<double>(), h->Wt.as<double>(),
                               h->G.as<double>(), R, nrhs, sd.as<double>(), tmp.as<double>(), s));
     AFN_CUDA(cudaStreamSynchronize(s));

@@ -489,17 +489,17 @@ static bool use_umma()
     return v == 1;
 }
 
-template <int DS, int NB, int KER, int VAR, int UH>
+template <int DS, int NB, int KER, int VAR, int UH, int UK = UK_DEF, bool P4 = false, int LEAN = 0>
 static void launch_u(const float *Xs, int64_t n, const float *Xpr, const uint32_t *Pk, float *part,
                      int js, int64_t chunk_st, int64_t nstage, int *err, cudaStream_t s)
 {
     // at least 80 KB of shared memory keeps residency at 2 CTAs per SM, the
     // number whose tensor-memory allocations fit together
     const int smem = std::max(UNST * UStage<DS, NB * 8, VAR>::BYTES, 80 * 1024);
-    cudaFuncSetAttribute(matvec32u_kernel<DS, NB, KER, VAR, UH>,
+    cudaFuncSetAttribute(matvec32u_kernel<DS, NB, KER, VAR, UH, UK, P4, LEAN>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     dim3 g((unsigned)((n + UR - 1) / UR), (unsigned)js);
-    matvec32u_kernel<DS, NB, KER, VAR, UH><<<g, umma_threads(UH), smem, s>>>(
+    matvec32u_kernel<DS, NB, KER, VAR, UH, UK, P4, LEAN><<<g, umma_threads(UH), smem, s>>>(
         Xs, n, Xpr, Pk, part, chunk_st, nstage, err);
 }
 
@@ -516,6 +516,12 @@ static int umma_variant()
         v = 0;   // UDIRECT, UH = 1
         if (e && strlen(e) == 2 && strchr("dnm", e[0]) && (e[1] == '1' || e[1] == '2'))
             v = (e[0] == 'd' ? 0 : e[0] == 'n' ? 2 : 4) + (e[1] - '1');
+        // e1: 16-point blocks; p1: the fourth product lo x lo; q1: both
+        if (e && strcmp(e, "e1") == 0) v = 6;
+        if (e && strcmp(e, "p1") == 0) v = 7;
+        if (e && strcmp(e, "q1") == 0) v = 8;
+        // l1..l7: LEAN bits (1 unrounded lo, 2 cvt hi, 4 two-level fold)
+        if (e && e[0] == 'l' && e[1] >= '1' && e[1] <= '7' && !e[2]) v = 8 + (e[1] - '0');
     }
     return v;
 }
@@ -530,7 +536,7 @@ static void launch_u_any(const float *Xs, int64_t n, float *Xpr, const uint32_t 
     const unsigned gb = (unsigned)((npad + 255) / 256);
     int v = 0;
     if constexpr (DS == 8 && NB == 4 && KER == 0) v = umma_variant();
-    const int form = v / 2 == 0 ? UDIRECT : v / 2 == 1 ? UNORM : UNORM2;
+    const int form = (v >= 6 || v / 2 == 0) ? UDIRECT : v / 2 == 1 ? UNORM : UNORM2;
     if (form == UDIRECT) upoints_kernel<UDIRECT><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
     else if (form == UNORM) upoints_kernel<UNORM><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
     else upoints_kernel<UNORM2><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
@@ -541,6 +547,16 @@ static void launch_u_any(const float *Xs, int64_t n, float *Xpr, const uint32_t 
         case 3: launch_u<DS, NB, KER, UNORM, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
         case 4: launch_u<DS, NB, KER, UNORM2, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
         case 5: launch_u<DS, NB, KER, UNORM2, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 6: launch_u<DS, NB, KER, UDIRECT, 1, 16, false>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 7: launch_u<DS, NB, KER, UDIRECT, 1, 32, true>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 8: launch_u<DS, NB, KER, UDIRECT, 1, 16, true>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 9: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 10: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 11: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 3>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 12: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 4>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 13: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 5>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 14: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 6>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
+        case 15: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 7>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
         default: break;
         }
     }

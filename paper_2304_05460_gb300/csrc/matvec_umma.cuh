@@ -38,7 +38,7 @@ namespace afn {
 
 static constexpr int UR = 128;   // rows per CTA (TMEM lanes)
 static constexpr int UJ = 64;    // points per staged tile
-static constexpr int UK = 32;    // points per A block (4 MMA k-steps)
+static constexpr int UK_DEF = 32;   // points per A block (4 MMA k-steps)
 static constexpr int UNST = 3;   // staged tile buffers
 static constexpr int UTMEM = 256;   // tensor-memory columns per CTA
 
@@ -98,6 +98,16 @@ __device__ __forceinline__ void umma_tf32(uint32_t dt, uint32_t at, uint64_t bde
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(dt),
                  "r"(at), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+// D (+)= A B with both operands described in shared memory
+__device__ __forceinline__ void umma_tf32_ss(uint32_t dt, uint64_t adesc, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
                  : "memory");
 }
 
@@ -193,6 +203,23 @@ __device__ __forceinline__ bool mbar_wait_abort_warp(uint64_t *bar, uint32_t par
     return __all_sync(0xffffffffu, got);
 }
 
+// x = hi + lo for the three-pass product.  LEAN & 1: lo is passed unrounded
+// (the tensor core reads its leading tf32 bits: a truncation, unbiased
+// because lo has either sign); LEAN & 2: hi by cvt.rna.tf32.f32.
+template <int LEAN>
+__device__ __forceinline__ void umma_split(float x, uint32_t &hi, uint32_t &lo)
+{
+    if constexpr ((LEAN & 3) == 0) {
+        tf32_split(x, hi, lo);
+    } else {
+        if constexpr (LEAN & 2) hi = tf32_bits(x);
+        else hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+        const float l = x - __uint_as_float(hi);
+        if constexpr (LEAN & 1) lo = __float_as_uint(l);
+        else lo = (__float_as_uint(l) + 0x1000u) & 0xffffe000u;
+    }
+}
+
 // Kahan fold of C accumulator columns (packed pairs) into acc / cmp
 template <int C>
 __device__ __forceinline__ void umma_fold(const uint32_t (&v)[C], f2_t *acc, f2_t *cmp)
@@ -219,7 +246,7 @@ __device__ __forceinline__ void umma_fold(const uint32_t (&v)[C], f2_t *acc, f2_
 //        (c%8)4 + jj%4 for point jj of the stage and column c).
 // Row sums of rows [row0, row0 + 128) leave through part (column-major per
 // chunk, leading dimension n).
-template <int DS, int NB, int KER, int VAR, int UH>
+template <int DS, int NB, int KER, int VAR, int UH, int UK, bool P4, int LEAN>
 __global__ void __launch_bounds__(umma_threads(UH), 2)
     matvec32u_kernel(const float *__restrict__ Xs, int64_t n, const float *__restrict__ Xpr,
                      const uint32_t *__restrict__ Pk, float *__restrict__ part, int64_t chunk_st,
@@ -307,7 +334,12 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                     const uint32_t off = (uint32_t)(((c % BPS) * (UK / 4) + 2 * q) * 128);
                     const uint64_t dh = umma_desc(phi + off, 128, (UJ / 4) * 128);
                     const uint64_t dl = umma_desc(plo + off, 128, (UJ / 4) * 128);
-                    umma_tf32(dcol, a_lo + 8 * q, dh, IDESC, q > 0);
+                    if constexpr (P4) {
+                        umma_tf32(dcol, a_lo + 8 * q, dl, IDESC, q > 0);
+                        umma_tf32(dcol, a_lo + 8 * q, dh, IDESC, 1);
+                    } else {
+                        umma_tf32(dcol, a_lo + 8 * q, dh, IDESC, q > 0);
+                    }
                     umma_tf32(dcol, a_hi + 8 * q, dl, IDESC, 1);
                     umma_tf32(dcol, a_hi + 8 * q, dh, IDESC, 1);
                 }
@@ -345,14 +377,41 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
         const f2_t ni2 = f2_pack(ni, ni);
         const f2_t m2 = f2_pack(-2.f, -2.f);
         f2_t acc[FC / 2], cmp[FC / 2];
+        // LEAN & 4: blocks are first summed in plain FP32 (acc1), and every
+        // FOLD2 blocks acc1 is folded into the Kahan sum
+        constexpr int FOLD2 = 4;
+        f2_t acc1[(LEAN & 4) ? FC / 2 : 1];
 #pragma unroll
         for (int h = 0; h < FC / 2; ++h) acc[h] = cmp[h] = 0ull;
+#pragma unroll
+        for (int h = 0; h < ((LEAN & 4) ? FC / 2 : 1); ++h) acc1[h] = 0ull;
+        auto kahan = [&](int h, f2_t tv) {
+            const f2_t y = f2_sub(tv, cmp[h]);
+            const f2_t sm = f2_add(acc[h], y);
+            cmp[h] = f2_sub(f2_sub(sm, acc[h]), y);
+            acc[h] = sm;
+        };
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         auto fold = [&](int c) -> bool {
             if (!mbar_wait_abort_warp(&bdone[c & 1], (uint32_t)(c >> 1) & 1u, abort)) return false;
             tm_fence_after();
             const uint32_t dcol = tbase + lane_off + COL_D + (c & 1) * NR + hf * FC;
-            if constexpr (FC % 16 == 0) {
+            if constexpr ((LEAN & 4) != 0) {
+                static_assert(FC % 16 == 0, "two-level fold width");
+                const bool first = (c % FOLD2) == 0;
+                const bool flush = (c % FOLD2) == FOLD2 - 1 || c == nblk - 1;
+#pragma unroll
+                for (int h = 0; h < FC / 16; ++h) {
+                    uint32_t v[16];
+                    tm_ld16(dcol + 16 * h, v);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const f2_t tv = f2_pack(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+                        acc1[8 * h + e] = first ? tv : f2_add(acc1[8 * h + e], tv);
+                        if (flush) kahan(8 * h + e, acc1[8 * h + e]);
+                    }
+                }
+            } else if constexpr (FC % 16 == 0) {
 #pragma unroll
                 for (int h = 0; h < FC / 16; ++h) {
                     uint32_t v[16];
@@ -411,7 +470,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                                 dot = __fmaf_rn(xi[q + 3], v.w, dot);
                             }
                             const float r2 = fmaxf(__fmaf_rn(-2.f, dot, __fadd_rn(ni, njs[e])), 0.f);
-                            tf32_split(kernel32_scaled<KER>(r2), vh[4 * m4 + e], vl[4 * m4 + e]);
+                            umma_split<LEAN>(kernel32_scaled<KER>(r2), vh[4 * m4 + e], vl[4 * m4 + e]);
                         }
                     }
                 } else {
@@ -445,8 +504,8 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                             r0 = fmaxf(r0, 0.f);
                             r1 = fmaxf(r1, 0.f);
                         }
-                        tf32_split(kernel32_scaled<KER>(r0), vh[2 * m], vl[2 * m]);
-                        tf32_split(kernel32_scaled<KER>(r1), vh[2 * m + 1], vl[2 * m + 1]);
+                        umma_split<LEAN>(kernel32_scaled<KER>(r0), vh[2 * m], vl[2 * m]);
+                        umma_split<LEAN>(kernel32_scaled<KER>(r1), vh[2 * m + 1], vl[2 * m + 1]);
                     }
                 }
                 tm_st16(a_hi + 16 * g16, vh);

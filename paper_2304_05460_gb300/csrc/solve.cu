@@ -312,6 +312,7 @@ static afn_status apply64(Handle *h, const double *r, int nrhs, double *z, void 
 
 static afn_status apply32(Handle *h, const float *r, int nrhs, float *z, void *tmp)
 {
+    if (nrhs % 16 == 0) AFN_TRY(apply_tc_prepare(h, h->stream));
     Scope sc(&h->prof, K_APPLY32);
     return afn_apply<float>(h, h->Linv32.as<float>(), h->LinvT32.as<float>(), h->Wt32.as<float>(),
                             h->G32.as<float>(), r, nrhs, z, static_cast<float *>(tmp), h->stream);

@@ -180,6 +180,33 @@ def test_build_mixed_close_to_oracle(afn):
     assert _cmp(Gv, ref["G"], 0) <= 1e-2                      # FP32 Schur blocks
 
 
+@pytest.mark.parametrize("n,k,nrhs", [(3001, 300, 32), (2600, 130, 16), (3001, 300, 48)])
+def test_mixed_apply_tensor_core_products(afn, monkeypatch, n, k, nrhs):
+    # the FP32 apply of a mixed handle with the W products on the tcgen05
+    # tensor cores (three-pass tf32, opt-in) against the same apply on the CUDA cores
+    # and against the oracle's FP64 apply of the oracle's own build; ragged k
+    # and n - k (not multiples of the 32-element stages or 128-row tiles)
+    X = inputs.normal_points(n, 8, 800 + n)
+    h = afn.afn_build(X, G, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED)
+    bi = h.info
+    assert bi.k == k and bi.nr == n - k
+    r = inputs.rhs(n, nrhs, 900 + n)
+    before = afn.afn_get_build_info(h).device_bytes
+    monkeypatch.setenv("AFN_APPLY_TC", "1")
+    s_tc = afn.afn_apply_precond(h, r)
+    grown = afn.afn_get_build_info(h).device_bytes - before
+    assert grown >= 2 * 4 * k * (n - k)            # the two tiled images of W were built
+    monkeypatch.setenv("AFN_APPLY_TC", "0")
+    s_cc = afn.afn_apply_precond(h, r)
+    assert np.all(np.isfinite(s_tc))
+    assert _cmp(s_tc, s_cc, 0) <= 2e-5
+    # FP32 apply of an FP32-built preconditioner against the FP64 oracle
+    ref = oracle.afn_build(X, G, 1.0, 1e-2, k, 32)
+    s_ref = np.stack([oracle.afn_apply(ref, r[:, c]) for c in range(3)], 1)
+    assert _cmp(s_tc[:, :3], s_ref, 0) <= 1e-2
+    afn.afn_free(h)
+
+
 def test_not_spd_reported(afn):
     # duplicated landmarks make K11 singular; mu tiny keeps K11 + mu I at the
     # edge -- with mu = 1e-300 the Cholesky pivot underflows to <= 0
