@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--only", default="",
                     help="'batched' or 'serving': run that workload alone (profiling)")
+    ap.add_argument("--sequential", action="store_true",
+                    help="build and solve the systems of a step one after another (default: "
+                         "concurrently, one stream and host thread per system)")
     ap.add_argument("--ls", default="0.5,1,2,4",
                     help="length-scales of one step (a subset profiles a single system)")
     ap.add_argument("--batched", type=int, default=512,
@@ -412,25 +415,27 @@ def main():
     Xd = torch.tensor(s.X, device="cuda")
     Bd = torch.tensor(np.ascontiguousarray(s.B), device="cuda")
 
-    def opts(profile):
+    def opts(profile, st=None):
         return afn.options(precision=afn.PREC_MIXED, rank_mode=afn.RANK_ESTIMATE,
-                           rank_subsample=1000, seed=SEED, profile=profile, stream=stream,
-                           max_iter=MAXIT)
+                           rank_subsample=1000, seed=SEED, profile=profile,
+                           stream=stream if st is None else st, max_iter=MAXIT)
 
     stats = {}
     iters_seen = []
+    lock = threading.Lock()
+    # the systems of a step are independent: by default each is built and solved on its own
+    # stream from its own host thread, so the FP32-bound matvecs of one system overlap the
+    # memory- and latency-bound apply and build kernels of the others
+    streams = [torch.cuda.Stream() for _ in LS] if not args.sequential else []
 
-    def step(profile, host=False):
-        for l in LS:
-            if host:
-                h = afn.afn_build(s.X, afn.GAUSSIAN, l, MU, KMAX, W, opts(profile))
-                x, info = afn.afn_solve(h, s.B, TOL)
-            else:
-                h = afn.afn_build(Xd, afn.GAUSSIAN, l, MU, KMAX, W, opts(profile))
-                x, info = afn.afn_solve(h, Bd, TOL)
-            if info["converged"] != args.nrhs:
-                raise RuntimeError("l=%g: %d/%d columns reached tol (relres max %.3e)"
-                                   % (l, info["converged"], args.nrhs, info["relres"].max()))
+    def one(l, profile, host, st):
+        src_X, src_B = (s.X, s.B) if host else (Xd, Bd)
+        h = afn.afn_build(src_X, afn.GAUSSIAN, l, MU, KMAX, W, opts(profile, st))
+        x, info = afn.afn_solve(h, src_B, TOL)
+        if info["converged"] != args.nrhs:
+            raise RuntimeError("l=%g: %d/%d columns reached tol (relres max %.3e)"
+                               % (l, info["converged"], args.nrhs, info["relres"].max()))
+        with lock:
             iters_seen.append(int(info["iters"].max()))
             if profile:
                 for nm in ("matvec32", "matvec64", "apply32", "fps", "knn", "chol", "trsm",
@@ -439,7 +444,30 @@ def main():
                     a = stats.setdefault(nm, [0, 0.0])
                     a[0] += c
                     a[1] += ms
-            afn.afn_free(h)
+        afn.afn_free(h)
+
+    def step(profile, host=False):
+        if args.sequential:
+            for l in LS:
+                one(l, profile, host, None)
+            return
+        errs = []
+
+        def run(l, st):
+            try:
+                with torch.cuda.stream(st):
+                    one(l, profile, host, st)
+                st.synchronize()
+            except BaseException as e:   # re-raised on the main thread
+                errs.append(e)
+
+        ts = [threading.Thread(target=run, args=(l, st)) for l, st in zip(LS, streams)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        if errs:
+            raise errs[0]
 
     for _ in range(args.warmup):
         step(0)
@@ -497,6 +525,29 @@ def main():
         roof["eval_bound"] = {"pairs_per_s": pairs_s, "peak_pairs_per_s": eval_peak,
                               "frac": pairs_s / eval_peak,
                               "basis": "FP32 pipe, 2d+1 lane-ops per kernel value (derived)"}
+    if not args.sequential and mv_cnt:
+        # the timed region runs the systems concurrently, so its launch durations include
+        # the SMs shared with the other systems' kernels; the same matvec timed alone
+        # (whole afn_kernel_matvec calls: p split, points, kernel, finish) for comparison
+        torch.cuda.synchronize()
+        for _ in range(2):
+            afn.afn_kernel_matvec(Xd, afn.GAUSSIAN, 2.0, MU, Bd, precision=afn.PREC_MIXED,
+                                  stream=stream)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        c0.record(stream)
+        for _ in range(reps):
+            afn.afn_kernel_matvec(Xd, afn.GAUSSIAN, 2.0, MU, Bd, precision=afn.PREC_MIXED,
+                                  stream=stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        iso_ms = c0.elapsed_time(c1) / reps
+        iso = flops_per_launch / (iso_ms / 1e3) / 1e12
+        roof["isolated"] = {"avg_call_ms": iso_ms, "achieved": iso, "frac": iso / peak,
+                            "basis": "afn_kernel_matvec alone, same points and 32 columns, "
+                                     "CUDA events over %d calls" % reps}
+        roof["note"] = ("timed-region launch durations include SMs shared with the "
+                        "concurrently solved systems")
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in stats.items()}
     step_ms = ms / args.steps
 
@@ -542,10 +593,20 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic", "config": config(args.n, args.nrhs),
+                "schedule": ("sequential: the systems of a step one after another"
+                             if args.sequential else
+                             "concurrent: each system of a step built and solved on its own "
+                             "stream and host thread"),
                 "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-                "kernels": kernels, "fp64_gpu": fp64,
+                "kernels": kernels,
+                "kernels_note": ("per-class device time summed over launches (CUDA events); "
+                                 "with the concurrent schedule the classes of different "
+                                 "systems overlap, so the sums exceed the step time"
+                                 if not args.sequential else
+                                 "per-class device time summed over launches (CUDA events)"),
+                "fp64_gpu": fp64,
                 "pcg_iters_max": iters_seen[-len(LS):] if iters_seen else None,
                 "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
