@@ -58,6 +58,11 @@ def _L():
                 "orc_kernel_eval": (dbl, [P, P, i32, i32, dbl]),
                 "orc_kernel_matrix": (None, [P, i64, P, i64, i32, i32, dbl, P]),
                 "orc_matvec": (None, [P, i64, i32, i32, dbl, dbl, P, i32, P]),
+                "orc_jacobi_eig": (None, [P, i64, P, P]),
+                "orc_nystrom_build": (i32, [P, i64, i32, i32, dbl, i64, P, P, P]),
+                "orc_nystrom_apply": (None, [i64, i64, i64, P, P, dbl, P, P]),
+                "orc_pcg_nystrom": (i32, [P, i64, i32, i32, dbl, dbl, i64, i64, P, P, P, dbl, i32,
+                                          i32, P, P, P]),
                 "orc_fps": (i32, [P, i64, i32, i64, i64, P]),
                 "orc_fps_centroid_start": (i64, [P, i64, i32]),
                 "orc_splitmix64_next": (u64, [P]),
@@ -327,6 +332,92 @@ def pcg(f, b, tol, max_iter=500, max_restarts=3, identity=False):
     if one:
         return X[:, 0], int(its[0]), float(rel[0]), int(sts[0])
     return X, its, rel, sts
+
+
+def jacobi_eig(A):
+    """Cyclic Jacobi (Golub & Van Loan Alg. 8.5.3): eigenvalues w and
+    eigenvectors V (columns) of the symmetric matrix A."""
+    A = np.array(A, dtype=np.float64, order="C")
+    m = A.shape[0]
+    V = np.empty((m, m))
+    w = np.empty(m)
+    _L().orc_jacobi_eig(_p(A), m, _p(V), _p(w))
+    return w, V
+
+
+def nystrom_build(X, kernel, l, mu, k, landmarks=None, mode="fps", start=0, seed=0):
+    """Column-sampling Nystrom preconditioner (Sec. 2) in the orthonormal form
+    of eq. (nystrom1-smw): U (n x r, permuted order, landmarks first) and
+    Lambda (r) with U Lambda U^T = K_nys.  Raises LinAlgError if K_SS is not SPD."""
+    X = _f64(X)
+    n, d = X.shape
+    k = int(min(max(k, 0), n))
+    lm = landmarks_for(X, k, mode, start, seed) if landmarks is None else np.asarray(landmarks, np.int64)
+    lm = np.ascontiguousarray(lm, dtype=np.int64)
+    perm = np.empty(n, dtype=np.int64)
+    _L().orc_permutation(n, _p(lm), k, _p(perm))
+    Xp = np.ascontiguousarray(X[perm])
+    U = np.zeros((n, max(k, 1)))
+    lam = np.zeros(max(k, 1))
+    r = C.c_int64(0)
+    st = _L().orc_nystrom_build(_p(Xp), n, d, _kid(kernel), float(l), k, _p(U), _p(lam),
+                                C.byref(r))
+    if st == ERR_NOT_SPD:
+        raise np.linalg.LinAlgError("oracle nystrom_build: K_SS + nu I not SPD")
+    r = int(r.value)
+    return dict(precond="nystrom", perm=perm, Xp=Xp, U=U[:, :max(k, 1)], lam=lam, k=k, r=r,
+                landmarks=lm.copy(), kernel=_kid(kernel), l=float(l), mu=float(mu))
+
+
+def nystrom_apply(f, rv):
+    """eq. (nystrom1-smw): s = U (Lambda + mu I)^{-1} U^T r + (r - U U^T r) / mu, permuted order."""
+    rv = _f64(rv)
+    s = np.empty_like(rv)
+    n = f["Xp"].shape[0]
+    _L().orc_nystrom_apply(n, max(f["k"], 1), f["r"], _p(_f64(f["U"])), _p(_f64(f["lam"])),
+                           float(f["mu"]), _p(rv), _p(s))
+    return s
+
+
+def pcg_nystrom(f, b, tol, max_iter=500, max_restarts=3):
+    """PCG with the Nystrom preconditioner of ``f`` (Alg. 5, k < 2000 branch),
+    b in ORIGINAL point order; returns (x, iters, relres, status) per column."""
+    Xp = _f64(f["Xp"])
+    n, d = Xp.shape
+    perm = f["perm"]
+    b = np.asarray(b, dtype=np.float64)
+    one = b.ndim == 1
+    B = b.reshape(n, -1)
+    X = np.zeros_like(B)
+    its = np.zeros(B.shape[1], dtype=np.int64)
+    rel = np.zeros(B.shape[1])
+    sts = np.zeros(B.shape[1], dtype=np.int64)
+    for c in range(B.shape[1]):
+        bp = np.ascontiguousarray(B[perm, c])
+        xp = np.empty(n)
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        st = _L().orc_pcg_nystrom(_p(Xp), n, d, f["kernel"], f["l"], f["mu"], max(f["k"], 1),
+                                  f["r"], _p(_f64(f["U"])), _p(_f64(f["lam"])), _p(bp),
+                                  float(tol), int(max_iter), int(max_restarts), _p(xp),
+                                  C.byref(it), C.byref(rr))
+        X[perm, c] = xp
+        its[c], rel[c], sts[c] = it.value, rr.value, st
+    if one:
+        return X[:, 0], int(its[0]), float(rel[0]), int(sts[0])
+    return X, its, rel, sts
+
+
+def strategy(X, kernel, l, mu, k_max, w, m=1000, seed=0, threshold=2000):
+    """Alg. 5: estimate k by Alg. 4; k < threshold (2000 in the paper): the
+    Nystrom preconditioner with k landmarks, else AFN.  Returns the factors
+    (``precond`` = "nystrom" or "afn")."""
+    k = rank_estimate(X, kernel, l, mu, m=m, seed=seed, k_max=k_max)[0]
+    if k < threshold:
+        return nystrom_build(X, kernel, l, mu, k)
+    f = afn_build(X, kernel, l, mu, k, w)
+    f["precond"] = "afn"
+    return f
 
 
 def dense_solve(X, kernel, l, mu, b):

@@ -25,6 +25,10 @@
  * 3 a matrix that must be SPD is not (a Cholesky pivot <= 0),
  * 4 PCG did not reach the tolerance within max_iter.
  *
+ * The Nystrom preconditioner of Alg. 5's small-rank branch (Sec. 2, eq.
+ * (nystrom1-smw)) is built literally in its orthonormal form, with a cyclic
+ * Jacobi eigendecomposition; PCG takes either preconditioner.
+ *
  * Parity: every function here is pinned by the CPU tests (closed forms,
  * brute force on tiny inputs, the paper's invariants); see the test files.
  */
@@ -591,13 +595,30 @@ void orc_dense_M_expanded(const double *Xp, int64_t n, int d, int kernel, double
 /* (plain CG).  iters = number of products with K + mu I inside the loops.   */
 /* Returns 0, or 4 when max_iter is reached first.                           */
 /* ------------------------------------------------------------------------ */
-int orc_pcg(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
-            int64_t k, int w, const double *L, const double *K12, const int32_t *pat,
-            const double *G, const double *b, double tol, int max_iter, int max_restarts,
-            double *x, int *iters, double *relres)
+/* the preconditioner of one PCG run: s = M^{-1} r (identity when apply is NULL) */
+typedef struct {
+    void (*apply)(const void *ctx, const double *r, double *s);
+    const void *ctx;
+} precond_t;
+
+typedef struct {
+    int64_t k, nr;
+    int w;
+    const double *L, *K12, *G;
+    const int32_t *pat;
+} afn_ctx_t;
+
+static void afn_apply_cb(const void *c, const double *r, double *s)
 {
-    int64_t nr = n - k;
-    int ident = (L == NULL && G == NULL);
+    const afn_ctx_t *a = (const afn_ctx_t *)c;
+    orc_afn_apply(a->k, a->nr, a->w, a->L, a->K12, a->pat, a->G, r, s);
+}
+
+static int pcg_core(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
+                    precond_t pc, const double *b, double tol, int max_iter, int max_restarts,
+                    double *x, int *iters, double *relres)
+{
+    int ident = (pc.apply == NULL);
     double *Kd = NULL;
     if (n <= 4096) {
         Kd = (double *)malloc(sizeof(double) * (size_t)(n * n));
@@ -619,7 +640,7 @@ int orc_pcg(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
         if (Kd) dense_matvec1(Kd, n, mu, x, q); else free_matvec1(Xp, n, d, kernel, l, mu, x, q);
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
         if (ident) memcpy(z, r, sizeof(double) * (size_t)n);
-        else orc_afn_apply(k, nr, w, L, K12, pat, G, r, z);
+        else pc.apply(pc.ctx, r, z);
         memcpy(p, z, sizeof(double) * (size_t)n);
         double rho = 0.0;
         for (int64_t i = 0; i < n; ++i) rho = rho + r[i] * z[i];
@@ -636,7 +657,7 @@ int orc_pcg(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
             for (int64_t i = 0; i < n; ++i) rn = rn + r[i] * r[i];
             if (sqrt(rn) <= tol * bn) { conv = 1; break; }
             if (ident) memcpy(z, r, sizeof(double) * (size_t)n);
-            else orc_afn_apply(k, nr, w, L, K12, pat, G, r, z);
+            else pc.apply(pc.ctx, r, z);
             double rho1 = 0.0;
             for (int64_t i = 0; i < n; ++i) rho1 = rho1 + r[i] * z[i];
             double beta = rho1 / rho;
@@ -655,6 +676,178 @@ int orc_pcg(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
     *relres = rel;
     free(Kd); free(r); free(z); free(p); free(q);
     return status;
+}
+
+/* PCG with the AFN preconditioner (L == NULL and G == NULL: plain CG) */
+int orc_pcg(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
+            int64_t k, int w, const double *L, const double *K12, const int32_t *pat,
+            const double *G, const double *b, double tol, int max_iter, int max_restarts,
+            double *x, int *iters, double *relres)
+{
+    afn_ctx_t a = {k, n - k, w, L, K12, G, pat};
+    precond_t pc = {NULL, NULL};
+    if (!(L == NULL && G == NULL)) { pc.apply = afn_apply_cb; pc.ctx = &a; }
+    return pcg_core(Xp, n, d, kernel, l, mu, pc, b, tol, max_iter, max_restarts, x, iters, relres);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cyclic Jacobi eigendecomposition of a symmetric m x m matrix (Golub &     */
+/* Van Loan, Matrix Computations, Alg. 8.5.3 with the symmetric Schur        */
+/* rotation of Alg. 8.5.1): A (row-major, overwritten) -> eigenvalues w[m]  */
+/* and eigenvectors as the columns of V (row-major m x m).  Sweeps until    */
+/* off(A) <= 1e-15 ||A||_F (at most 60 sweeps).                              */
+/* ------------------------------------------------------------------------ */
+void orc_jacobi_eig(double *A, int64_t m, double *V, double *w)
+{
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j) V[i * m + j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (int64_t i = 0; i < m * m; ++i) fro = fro + A[i] * A[i];
+    fro = sqrt(fro);
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int64_t p = 0; p < m; ++p)
+            for (int64_t q = p + 1; q < m; ++q) off = off + 2.0 * A[p * m + q] * A[p * m + q];
+        if (sqrt(off) <= 1e-15 * fro) break;
+        for (int64_t p = 0; p < m - 1; ++p)
+            for (int64_t q = p + 1; q < m; ++q) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                /* symmetric Schur: c, s annihilating A[p][q] */
+                double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int64_t i = 0; i < m; ++i) {
+                    double aip = A[i * m + p], aiq = A[i * m + q];
+                    A[i * m + p] = c * aip - sn * aiq;
+                    A[i * m + q] = sn * aip + c * aiq;
+                }
+                for (int64_t j = 0; j < m; ++j) {
+                    double apj = A[p * m + j], aqj = A[q * m + j];
+                    A[p * m + j] = c * apj - sn * aqj;
+                    A[q * m + j] = sn * apj + c * aqj;
+                }
+                for (int64_t i = 0; i < m; ++i) {
+                    double vip = V[i * m + p], viq = V[i * m + q];
+                    V[i * m + p] = c * vip - sn * viq;
+                    V[i * m + q] = sn * vip + c * viq;
+                }
+            }
+    }
+    for (int64_t i = 0; i < m; ++i) w[i] = A[i * m + i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Column-sampling Nystrom preconditioner (Sec. 2, eq. (sampling-based-     */
+/* nystrom)) in the orthonormal form of eq. (nystrom1-smw).                  */
+/* Reading: K_nys = Y K_SS^+ Y^T with Y = K(X, X_S) (n x k) is formed as      */
+/* B B^T, B = Y L^{-T}, L = chol(K_SS + nu I), nu = n 2^-52 (the shift makes */
+/* the pseudoinverse of a numerically singular K_SS a Cholesky factor); the  */
+/* thin SVD B = U Sigma V^T comes from the eigendecomposition of B^T B       */
+/* (Jacobi above): Lambda = Sigma^2, U = B V Sigma^{-1}, keeping the         */
+/* eigenpairs with sigma^2 > 1e-14 max sigma^2 (rank r <= k).               */
+/* Xp: points in the permuted order, landmarks first.  U: n x k row-major   */
+/* (first r columns used), lam[k].  Returns 0, or 3 if K_SS + nu I is not    */
+/* positive definite.                                                         */
+/* ------------------------------------------------------------------------ */
+int orc_nystrom_build(const double *Xp, int64_t n, int d, int kernel, double l, int64_t k,
+                      double *U, double *lam, int64_t *rank)
+{
+    *rank = 0;
+    if (k == 0) return 0;
+    const double nu = (double)n * ldexp(1.0, -52);
+    double *A = (double *)malloc(sizeof(double) * (size_t)(k * k));
+    double *L = (double *)malloc(sizeof(double) * (size_t)(k * k));
+    orc_kernel_matrix(Xp, k, Xp, k, d, kernel, l, A);
+    for (int64_t i = 0; i < k; ++i) A[i * k + i] = A[i * k + i] + nu;
+    int st = orc_cholesky(A, k, L);
+    if (st) { free(A); free(L); return st; }
+    /* B (n x k): row i = L^{-1} K(X_S, x_i), by forward substitution */
+    double *B = (double *)malloc(sizeof(double) * (size_t)(n * k));
+#pragma omp parallel
+    {
+        double *col = (double *)malloc(sizeof(double) * (size_t)k);
+#pragma omp for
+        for (int64_t i = 0; i < n; ++i) {
+            for (int64_t t = 0; t < k; ++t)
+                col[t] = orc_kernel_eval(Xp + t * d, Xp + i * d, d, kernel, l);
+            orc_forward(L, k, col, B + i * k);
+        }
+        free(col);
+    }
+    /* B^T B (k x k), then its eigendecomposition */
+    for (int64_t a = 0; a < k; ++a)
+        for (int64_t c = 0; c < k; ++c) {
+            double v = 0.0;
+            for (int64_t i = 0; i < n; ++i) v = v + B[i * k + a] * B[i * k + c];
+            A[a * k + c] = v;
+        }
+    double *V = (double *)malloc(sizeof(double) * (size_t)(k * k));
+    double *w = (double *)malloc(sizeof(double) * (size_t)k);
+    orc_jacobi_eig(A, k, V, w);
+    double wmax = 0.0;
+    for (int64_t j = 0; j < k; ++j) wmax = fmax(wmax, w[j]);
+    int64_t r = 0;
+    for (int64_t j = 0; j < k; ++j) {
+        if (!(w[j] > 1e-14 * wmax)) continue;
+        /* column r of U = B v_j / sigma_j */
+        double sig = sqrt(w[j]);
+        for (int64_t i = 0; i < n; ++i) {
+            double v = 0.0;
+            for (int64_t t = 0; t < k; ++t) v = v + B[i * k + t] * V[t * k + j];
+            U[i * k + r] = v / sig;
+        }
+        lam[r] = w[j];
+        ++r;
+    }
+    *rank = r;
+    free(A); free(L); free(B); free(V); free(w);
+    return 0;
+}
+
+/* eq. (nystrom1-smw): s = U (Lambda + mu I)^{-1} U^T r + (r - U U^T r) / mu  */
+void orc_nystrom_apply(int64_t n, int64_t k, int64_t r, const double *U, const double *lam,
+                       double mu, const double *rin, double *s)
+{
+    double *y = (double *)malloc(sizeof(double) * (size_t)(r > 0 ? r : 1));
+    for (int64_t j = 0; j < r; ++j) {
+        double v = 0.0;
+        for (int64_t i = 0; i < n; ++i) v = v + U[i * k + j] * rin[i];
+        y[j] = v;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double a = 0.0, b = 0.0;
+        for (int64_t j = 0; j < r; ++j) {
+            a = a + U[i * k + j] * (y[j] / (lam[j] + mu));
+            b = b + U[i * k + j] * y[j];
+        }
+        s[i] = a + (rin[i] - b) / mu;
+    }
+    free(y);
+}
+
+typedef struct {
+    int64_t n, k, r;
+    const double *U, *lam;
+    double mu;
+} nys_ctx_t;
+
+static void nys_apply_cb(const void *c, const double *r, double *s)
+{
+    const nys_ctx_t *a = (const nys_ctx_t *)c;
+    orc_nystrom_apply(a->n, a->k, a->r, a->U, a->lam, a->mu, r, s);
+}
+
+/* PCG with the Nystrom preconditioner (Alg. 5, the k < 2000 branch) */
+int orc_pcg_nystrom(const double *Xp, int64_t n, int d, int kernel, double l, double mu,
+                    int64_t k, int64_t r, const double *U, const double *lam, const double *b,
+                    double tol, int max_iter, int max_restarts, double *x, int *iters,
+                    double *relres)
+{
+    nys_ctx_t a = {n, k, r, U, lam, mu};
+    precond_t pc = {nys_apply_cb, &a};
+    return pcg_core(Xp, n, d, kernel, l, mu, pc, b, tol, max_iter, max_restarts, x, iters, relres);
 }
 
 /* Direct solve (K + mu I) x = b by a dense Cholesky factorisation, for the

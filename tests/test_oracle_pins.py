@@ -432,3 +432,81 @@ def test_rank_estimate_extremes():
     # cap
     k, r, br = oracle.rank_estimate(X, G, 1e-4, 1e-2, m=100, seed=1, k_max=500)
     assert k == 500
+
+
+# ----------------------------------------------- Nystrom branch (Alg. 5) ---
+def test_jacobi_eig_against_eigvalsh():
+    A = inputs.rng(41).standard_normal((30, 30))
+    A = A + A.T
+    w, V = oracle.jacobi_eig(A)
+    assert np.allclose(V.T @ V, np.eye(30), atol=1e-13)
+    assert np.allclose(A @ V, V * w, atol=1e-11)
+    assert np.allclose(np.sort(w), np.linalg.eigvalsh(A), atol=1e-11)
+
+
+def _nys_dense(f):
+    # K_nys = Y (K_SS + nu I)^{-1} Y^T written out with library solves
+    Xp, k = f["Xp"], f["k"]
+    n = Xp.shape[0]
+    Y = oracle.kernel_matrix(Xp, Xp[:k], f["kernel"], f["l"])
+    Kss = Y[:k] + n * 2.0 ** -52 * np.eye(k)
+    return Y @ np.linalg.solve(Kss, Y.T)
+
+
+@pytest.mark.parametrize("ker,l,k", [(G, 0.3, 40), (M32, 0.5, 25)])
+def test_nystrom_factors_closed_form(ker, l, k):
+    X = pts(200, 3, 43)
+    f = oracle.nystrom_build(X, ker, l, 1e-2, k)
+    U, lam, r = f["U"][:, :f["r"]], f["lam"][:f["r"]], f["r"]
+    assert r == k                                    # FPS landmarks: K_SS well conditioned
+    assert np.allclose(U.T @ U, np.eye(r), atol=1e-10)
+    Kn = _nys_dense(f)
+    assert np.abs(U @ np.diag(lam) @ U.T - Kn).max() <= 1e-9 * np.abs(Kn).max()
+    # the landmark rows are reproduced: K_nys[S, :] = K[S, :] (up to the shift)
+    K = oracle.kernel_matrix(f["Xp"], f["Xp"], ker, l)
+    assert np.abs(Kn[:k] - K[:k]).max() <= 1e-8
+
+
+@pytest.mark.parametrize("mu", [1e-1, 1e-3])
+def test_nystrom_apply_inverts_M(mu):
+    # eq. (nystrom1-smw) against the direct inverse of K_nys + mu I
+    X = pts(150, 2, 44)
+    f = oracle.nystrom_build(X, G, 0.25, mu, 30)
+    Kn = _nys_dense(f)
+    r = inputs.rhs(150, 1, 45)[:, 0]
+    s = oracle.nystrom_apply(f, r)
+    ref = np.linalg.solve(Kn + mu * np.eye(150), r)
+    assert np.abs(s - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_nystrom_all_landmarks_one_step():
+    # k = n: K_nys = K (up to the shift), so M = K + mu I and PCG needs one product
+    X = pts(60, 3, 46)
+    f = oracle.nystrom_build(X, G, 0.15, 1e-2, 60)
+    b = inputs.rhs(60, 1, 47)[:, 0]
+    x, it, rel, st = oracle.pcg_nystrom(f, b, 1e-10)
+    assert st == 0 and it <= 2 and rel <= 1e-10
+
+
+def test_pcg_nystrom_reaches_dense_solution():
+    X = pts(400, 3, 48)
+    f = oracle.nystrom_build(X, M32, 0.4, 1e-2, 60)
+    b = inputs.rhs(400, 1, 49)[:, 0]
+    x, it, rel, st = oracle.pcg_nystrom(f, b, 1e-10, max_iter=400)
+    xd = oracle.dense_solve(X, M32, 0.4, 1e-2, b)
+    assert st == 0 and rel <= 1e-10
+    assert np.abs(x - xd).max() <= 1e-8 * np.abs(xd).max()
+    # and it is a better preconditioner than none
+    fa = oracle.afn_build(X, M32, 0.4, 1e-2, 0, 1)
+    _, it_cg, _, _ = oracle.pcg(fa, b, 1e-10, max_iter=400, identity=True)
+    assert it < it_cg
+
+
+def test_strategy_threshold_selects_branch():
+    X = pts(300, 3, 50)
+    k = oracle.rank_estimate(X, G, 0.3, 1e-2, m=100, seed=3, k_max=300)[0]
+    assert 0 < k < 300
+    below = oracle.strategy(X, G, 0.3, 1e-2, 300, 16, m=100, seed=3, threshold=k + 1)
+    above = oracle.strategy(X, G, 0.3, 1e-2, 300, 16, m=100, seed=3, threshold=k)
+    assert below["precond"] == "nystrom" and below["k"] == k
+    assert above["precond"] == "afn" and above["k"] == k
