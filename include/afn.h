@@ -72,6 +72,15 @@ typedef enum {
     AFN_RANK_ESTIMATE = 1      /* k = Alg. 4 estimate clipped to [1, min(k_max, n)] */
 } afn_rank_mode;
 
+typedef enum {
+    AFN_PRECOND_AFN = 0,       /* the AFN preconditioner (Alg. 2, applied by Alg. 3) */
+    AFN_PRECOND_NYSTROM = 1,   /* the column-sampling Nystrom preconditioner (Sec. 2), applied
+                                  as eq. (nystrom1-smw): (K_nys + mu I)^{-1} */
+    AFN_PRECOND_AUTO = 2       /* Alg. 5: estimate k by Alg. 4 (rank_mode is then taken as
+                                  AFN_RANK_ESTIMATE); Nystrom with k landmarks when
+                                  k < precond_threshold, else AFN */
+} afn_precond;
+
 typedef struct {
     int32_t precision;         /* afn_precision, default AFN_PREC_FP64 */
     int32_t landmarks;         /* afn_landmark_policy, default AFN_LM_AUTO */
@@ -87,6 +96,9 @@ typedef struct {
     int32_t check_every;       /* iterations between host convergence polls; default 4 */
     int32_t profile;           /* 1 = time every launch with CUDA events (afn_get_kernel_stats) */
     void *stream;              /* cudaStream_t; NULL = default stream */
+    int32_t precond;           /* afn_precond, default AFN_PRECOND_AFN; the batched and
+                                  served solves take AFN only */
+    int32_t precond_threshold; /* Alg. 5's rank threshold; 0 = 2000 */
 } afn_options;
 
 typedef struct afn_handle afn_handle;   /* opaque; owns every device buffer of one system */
@@ -97,7 +109,7 @@ typedef struct {
     int32_t kernel, precision;
     int64_t rank_r;            /* Alg. 4: the subsample Nystrom rank r (0 if not estimated) */
     int32_t rank_branch;       /* Alg. 4: 0 = k from r n / m, 1 = eigenvalue count, -1 = fixed k */
-    int32_t pad_;
+    int32_t precond;           /* afn_precond built (AFN or NYSTROM) */
     double l, mu;
     double build_ms;           /* wall time of the build (it ends synchronised) */
     int64_t device_bytes;      /* device memory held by the handle */

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "AFN_OK", 1: "AFN_ERR_ARG", 2: "AFN_ERR_OOM", 3: "AFN_ERR_NOT
                 4: "AFN_ERR_NO_CONVERGE", 5: "AFN_ERR_TIMEOUT", 6: "AFN_ERR_CUDA", 7: "AFN_ERR_BUSY"}
 GAUSSIAN, MATERN32 = 0, 1
 PREC_FP64, PREC_MIXED, PREC_DF, PREC_AUTO = 0, 1, 2, 3
+PRECOND_AFN, PRECOND_NYSTROM, PRECOND_AUTO = 0, 1, 2
 MATVEC_DF = PREC_DF        # afn_kernel_matvec: FP64-accurate double-float
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
@@ -38,13 +39,14 @@ class afn_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("landmarks", C.c_int32), ("rank_mode", C.c_int32),
                 ("rank_subsample", C.c_int32), ("fps_start", C.c_int64), ("seed", C.c_uint64),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("inner_tol", C.c_double),
-                ("check_every", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
+                ("check_every", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
+                ("precond", C.c_int32), ("precond_threshold", C.c_int32)]
 
 
 class afn_build_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nr", C.c_int64), ("k", C.c_int64), ("d", C.c_int32),
                 ("w", C.c_int32), ("kernel", C.c_int32), ("precision", C.c_int32),
-                ("rank_r", C.c_int64), ("rank_branch", C.c_int32), ("pad_", C.c_int32),
+                ("rank_r", C.c_int64), ("rank_branch", C.c_int32), ("precond", C.c_int32),
                 ("l", C.c_double), ("mu", C.c_double), ("build_ms", C.c_double),
                 ("device_bytes", C.c_int64), ("rho32", C.c_double)]
 

@@ -109,6 +109,12 @@ struct Handle {
     DevBuf Wt;        // double [nr*k]  (FP64 handles)
     DevBuf Wt32;      // float  [nr*k]  (mixed handles)
     DevBuf Wu1, Wu2;  // float tiled images of W^T and W for the tcgen05 apply (built on first use)
+    // Nystrom preconditioner (precond == AFN_PRECOND_NYSTROM): L = chol(K11 + nu I),
+    // B = K(X, X_S) L^{-T} (n x k row-major, permuted order), Lc = chol(mu I + B^T B)
+    int precond = AFN_PRECOND_AFN;
+    DevBuf Bn, Bn32;          // double / float [n*k]
+    DevBuf LcInv, LcInvT;     // double [k*k] lower / upper
+    DevBuf LcInv32, LcInvT32; // float  [k*k]
     bool wu_tried = false;
     DevBuf pat;       // int32 [nr*w]
     DevBuf G;         // double [nr*w]
@@ -230,6 +236,10 @@ size_t apply_tmp_elems(const Handle *h, int nrhs);
 // tiled images of W for the tcgen05 apply of a mixed handle (no-op when they
 // exist, the handle has no W, or AFN_APPLY_TC=1 is not set)
 afn_status apply_tc_prepare(Handle *h, cudaStream_t s);
+// the Nystrom factors of a handle whose L (chol(K11 + nu I)) and Bn are set:
+// Lc = chol(mu I + B^T B) and its triangular inverses (FP32 copies for mixed
+// handles)
+afn_status nystrom_factor(Handle *h, cudaStream_t s);
 
 // ---- grouped steps (many systems per launch; group.cuh describes the group)
 struct GDev;

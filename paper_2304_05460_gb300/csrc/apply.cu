@@ -121,11 +121,11 @@ __global__ void __launch_bounds__(CT) colmul_kernel(const T *__restrict__ A, int
     for (int c = 0; c < NC; ++c) part[((int64_t)blockIdx.y * NC + c) * ncols + i] = acc[c];
 }
 
-// out[i,c] = y[i,c] - sum_js part[js][c][i]
+// out[i,c] = beta y[i,c] + alpha sum_js part[js][c][i]  (y not read when beta == 0)
 template <class T>
 __global__ void colmul_finish(const T *__restrict__ part, int js, int nc, int64_t ncols,
                               const T *__restrict__ Y, int64_t ldy, T *__restrict__ O,
-                              int64_t ldo)
+                              int64_t ldo, T alpha, T beta)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ncols * nc) return;
@@ -133,7 +133,8 @@ __global__ void colmul_finish(const T *__restrict__ part, int js, int nc, int64_
     int64_t i = e % ncols;
     T s = 0;
     for (int q = 0; q < js; ++q) s += part[((int64_t)q * nc + c) * ncols + i];
-    O[c * ldo + i] = Y[c * ldy + i] - s;
+    const T base = (beta != (T)0) ? beta * Y[c * ldy + i] : (T)0;
+    O[c * ldo + i] = base + alpha * s;
 }
 
 // ELL product y = G t  (row i: sum_p G[i,p] t[pat[i,p]])
@@ -569,7 +570,7 @@ static void prod(const T *A, int64_t lda, int64_t M, int64_t K, const T *X, int6
         if (!TA) {
             rowmul<T, TRI>(A, lda, M, K, x, ldx, y, ldy, o, ldo, alpha, beta, b, s);
         } else {
-            // transposed tail: split-K column kernel, then o = y - sum (alpha = -1, beta = 1)
+            // transposed tail: split-K column kernel, then o = beta y + alpha sum
             int js = colmul_js(K, M);
             js = (int)std::max<int64_t>(1, std::min<int64_t>(js, (int64_t)(part_cap / ((size_t)b * M))));
             int64_t chunk = (K + js - 1) / js;
@@ -582,16 +583,102 @@ static void prod(const T *A, int64_t lda, int64_t M, int64_t K, const T *X, int6
             }
             int64_t tot = M * b;
             colmul_finish<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, js, b, M, y, ldy, o,
-                                                                           ldo);
+                                                                           ldo, alpha, beta);
         }
         c0 += b;
     }
+}
+
+// ------------------------------------------------------- Nystrom branch ----
+template <class T>
+__global__ void scale_cols_kernel(const T *__restrict__ a, int64_t n, int nrhs, int64_t ld, T f,
+                                  T *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nrhs) return;
+    const int64_t c = e / n, i = e % n;
+    out[c * ld + i] = a[c * ld + i] * f;
+}
+
+__global__ void add_diag_kernel(double *C, int64_t k, double v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) C[i * k + i] += v;
+}
+
+afn_status nystrom_factor(Handle *h, cudaStream_t s)
+{
+    const int64_t n = h->n, k = h->k;
+    if (k == 0) return AFN_OK;
+    // C = B^T B from the row-major B and a column-major copy, then mu on the diagonal
+    DevBuf bcm, part;
+    AFN_TRY(bcm.alloc(sizeof(double) * (size_t)(n * k)));
+    dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+    rm_to_cm_kernel<double><<<tg, tb, 0, s>>>(h->Bn.as<double>(), n, (int)k, bcm.as<double>(), n);
+    const size_t pcap = (size_t)GEMM_JS_MAX * 32 * (size_t)k;
+    AFN_TRY(part.alloc(sizeof(double) * pcap));
+    DevBuf Cm;
+    AFN_TRY(Cm.alloc(sizeof(double) * (size_t)(k * k)));
+    prod<double, true, 0>(h->Bn.as<double>(), k, k, n, bcm.as<double>(), n, nullptr, 0,
+                          Cm.as<double>(), k, 1.0, 0.0, (int)k, part.as<double>(), pcap, s);
+    add_diag_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(Cm.as<double>(), k, h->mu);
+    AFN_TRY(cholesky64(Cm.as<double>(), k, h->status.as<int>(), s, -1.0));
+    AFN_TRY(sync_status(h, "Cholesky of mu I + B^T B"));
+    AFN_TRY(h->LcInv.alloc(sizeof(double) * (size_t)(k * k)));
+    AFN_TRY(h->LcInvT.alloc(sizeof(double) * (size_t)(k * k)));
+    AFN_TRY(tri_inverse64(Cm.as<double>(), k, h->LcInv.as<double>(), h->LcInvT.as<double>(), s));
+    if (h->precision == AFN_PREC_MIXED) {
+        AFN_TRY(h->Bn32.alloc(sizeof(float) * (size_t)(n * k)));
+        AFN_TRY(h->LcInv32.alloc(sizeof(float) * (size_t)(k * k)));
+        AFN_TRY(h->LcInvT32.alloc(sizeof(float) * (size_t)(k * k)));
+        AFN_TRY(convert64to32(h->Bn.as<double>(), h->Bn32.as<float>(), n * k, s));
+        AFN_TRY(convert64to32(h->LcInv.as<double>(), h->LcInv32.as<float>(), k * k, s));
+        AFN_TRY(convert64to32(h->LcInvT.as<double>(), h->LcInvT32.as<float>(), k * k, s));
+    }
+    AFN_CUDA(cudaStreamSynchronize(s));   // the temporaries go out of scope
+    return AFN_OK;
+}
+
+// s = (K_nys + mu I)^{-1} r = (r - B Lc^{-T} Lc^{-1} B^T r) / mu  (eq. (nystrom1-smw) through
+// the SMW identity), vectors in the permuted order
+template <class T>
+static afn_status nystrom_apply(const Handle *h, const T *r, int nrhs, T *s, T *tmp, cudaStream_t st)
+{
+    const int64_t n = h->n, k = h->k, nr = h->nr;
+    const T f = (T)(1.0 / h->mu);
+    if (k > 0) {
+        const bool dbl = std::is_same<T, double>::value;
+        const T *B = reinterpret_cast<const T *>(dbl ? h->Bn.p : h->Bn32.p);
+        const T *Li = reinterpret_cast<const T *>(dbl ? h->LcInv.p : h->LcInv32.p);
+        const T *LiT = reinterpret_cast<const T *>(dbl ? h->LcInvT.p : h->LcInvT32.p);
+        if (!B || !Li || !LiT) {
+            set_error("nystrom apply: factors missing for this precision");
+            return AFN_ERR_ARG;
+        }
+        T *y = tmp, *v = tmp + k * nrhs;
+        T *part = tmp + 2 * k * nrhs + 2 * nr * nrhs;
+        const size_t pcap = (size_t)std::max(colmul_js(nr, k), GEMM_JS_MAX) * 32 *
+                            (size_t)std::max<int64_t>(k, 1);
+        prod<T, true, 0>(B, k, k, n, r, n, nullptr, 0, y, k, (T)1, (T)0, nrhs, part, pcap, st);
+        prod<T, false, 1>(Li, k, k, k, y, k, nullptr, 0, v, k, (T)1, (T)0, nrhs, part, pcap, st);
+        prod<T, false, 2>(LiT, k, k, k, v, k, nullptr, 0, y, k, (T)1, (T)0, nrhs, part, pcap, st);
+        prod<T, false, 0>(B, k, n, k, y, k, r, n, s, n, (T)-1, (T)1, nrhs, part, pcap, st);
+        const int64_t tot = n * nrhs;
+        scale_cols_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(s, n, nrhs, n, f, s);
+    } else {
+        const int64_t tot = n * nrhs;
+        scale_cols_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, n, nrhs, n, f, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "nystrom apply launch");
+    return AFN_OK;
 }
 
 template <class T>
 afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt, const T *G,
                      const T *r, int nrhs, T *s, T *tmp, cudaStream_t st)
 {
+    if (h->precond == AFN_PRECOND_NYSTROM) return nystrom_apply<T>(h, r, nrhs, s, tmp, st);
     const int64_t n = h->n, k = h->k, nr = h->nr;
     const int w = h->w;
     T *zp = tmp;                       // k x nrhs

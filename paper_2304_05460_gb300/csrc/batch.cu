@@ -748,6 +748,11 @@ afn_status afn_build_batched(const afn_system *systems, int32_t nsys, const afn_
     afn_options o;
     afn_default_options(&o);
     if (opt) o = *opt;
+    if (o.precond != AFN_PRECOND_AFN) {
+        set_error("afn_build_batched: grouped solves take the AFN preconditioner only (precond=%d)",
+                  o.precond);
+        return AFN_ERR_ARG;
+    }
     Batch *b = new Batch();
     cudaGetDevice(&b->dev);
     b->opt = o;

@@ -160,6 +160,7 @@ Profiler::~Profiler()
 int64_t Handle::device_bytes() const
 {
     const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32, &Wu1, &Wu2,
+                         &Bn, &Bn32, &LcInv, &LcInvT, &LcInv32, &LcInvT32,
                          &pat, &G, &G32, &gt_ptr, &gt_row, &gt_slot, &status, &ws};
     int64_t s = 0;
     for (auto x : b) s += (int64_t)x->bytes;
@@ -336,7 +337,7 @@ static afn_status build_impl(Handle *h, const double *points)
 
     // k (Alg. 4 or fixed)
     int64_t k = std::min<int64_t>(h->k, n);
-    if (h->opt.rank_mode == AFN_RANK_ESTIMATE) {
+    if (h->opt.rank_mode == AFN_RANK_ESTIMATE || h->opt.precond == AFN_PRECOND_AUTO) {
         Scope sc(&h->prof, K_RANK);
         int64_t r = 0;
         int br = 0;
@@ -348,6 +349,12 @@ static afn_status build_impl(Handle *h, const double *points)
     h->k = k;
     h->nr = n - k;
     const int64_t nr = h->nr;
+    // Alg. 5: the Nystrom preconditioner when the estimated rank is below the threshold
+    h->precond = h->opt.precond;
+    if (h->precond == AFN_PRECOND_AUTO) {
+        const int thr = h->opt.precond_threshold > 0 ? h->opt.precond_threshold : 2000;
+        h->precond = k < thr ? AFN_PRECOND_NYSTROM : AFN_PRECOND_AFN;
+    }
     h->w = (int)std::max<int64_t>(1, std::min<int64_t>(h->w_req, std::max<int64_t>(nr, 1)));
 
     // landmarks (Alg. 2: FPS when d <= 10, uniform otherwise, or forced)
@@ -408,6 +415,34 @@ static afn_status build_impl(Handle *h, const double *points)
         AFN_TRY(make_points_df(h->X64.as<double>(), n, d, ds, h->kernel, h->l, h->Xdf.as<float2>(), s));
     }
 
+    if (h->precond == AFN_PRECOND_NYSTROM) {
+        // column-sampling Nystrom (Sec. 2): L = chol(K_SS + nu I), nu = n 2^-52, B = K(X, X_S)
+        // L^{-T} for all n points, then Lc = chol(mu I + B^T B); the apply is eq.
+        // (nystrom1-smw) through the SMW identity (K_nys + mu I)^{-1} = (I - B (mu I +
+        // B^T B)^{-1} B^T) / mu, the same operator without an eigendecomposition
+        if (k > 0) {
+            {
+                Scope sc(&h->prof, K_CHOL);
+                AFN_TRY(h->L.alloc(sizeof(double) * (size_t)(k * k)));
+                AFN_TRY(kernel_block(Xk, k, Xk, k, d, kp, (double)n * 0x1p-52, h->L.as<double>(), k, s));
+                AFN_TRY(cholesky64(h->L.as<double>(), k, st, s, -1.0));
+            }
+            AFN_TRY(sync_status(h, "Cholesky of K_SS + nu I"));
+            {
+                Scope sc(&h->prof, K_TRSM);
+                AFN_TRY(h->Bn.alloc(sizeof(double) * (size_t)(n * k)));
+                AFN_TRY(kernel_block(Xk, n, Xk, k, d, kp, 0.0, h->Bn.as<double>(), k, s));
+                AFN_TRY(trsm_right_lt64(h->L.as<double>(), k, h->Bn.as<double>(), n, s));
+            }
+            {
+                Scope sc(&h->prof, K_CHOL);
+                AFN_TRY(nystrom_factor(h, s));
+            }
+        }
+        AFN_CUDA(cudaStreamSynchronize(s));
+        log.mark("nystrom");
+        return AFN_OK;
+    }
     if (k > 0) {
         {
             Scope sc(&h->prof, K_CHOL);
@@ -490,6 +525,10 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         !std::isfinite(l) || !(mu > 0) || !std::isfinite(mu) || k_max < 0 || fsai_nnz < 1) {
         set_error("afn_build: invalid argument (n=%lld d=%d kernel=%d l=%g mu=%g k_max=%d w=%d)",
                   (long long)n, d, kernel, l, mu, k_max, fsai_nnz);
+        return AFN_ERR_ARG;
+    }
+    if (o.precond < AFN_PRECOND_AFN || o.precond > AFN_PRECOND_AUTO || o.precond_threshold < 0) {
+        set_error("bad precond %d / precond_threshold %d", o.precond, o.precond_threshold);
         return AFN_ERR_ARG;
     }
     if (o.precision < AFN_PREC_FP64 || o.precision > AFN_PREC_AUTO) {
@@ -611,6 +650,8 @@ void afn_default_options(afn_options *o)
     o->check_every = 4;
     o->profile = 0;
     o->stream = nullptr;
+    o->precond = AFN_PRECOND_AFN;
+    o->precond_threshold = 0;
 }
 
 const char *afn_last_error(void) { return g_err; }
@@ -708,6 +749,7 @@ afn_status afn_get_build_info(const afn_handle *hh, afn_build_info *info)
     info->precision = h->precision;
     info->rank_r = h->rank_r;
     info->rank_branch = h->rank_branch;
+    info->precond = h->precond;
     info->l = h->l;
     info->mu = h->mu;
     info->build_ms = h->build_ms;
@@ -741,6 +783,7 @@ afn_status afn_get_G(const afn_handle *hh, int32_t *pattern, double *values)
 {
     const Handle *h = reinterpret_cast<const Handle *>(hh);
     if (!h) { set_error("NULL argument"); return AFN_ERR_ARG; }
+    if (h->precond != AFN_PRECOND_AFN) { set_error("afn_get_G: not an AFN handle"); return AFN_ERR_ARG; }
     if (pattern) AFN_TRY(copy_out(pattern, h->pat.p, sizeof(int32_t) * h->nr * h->w));
     if (values) AFN_TRY(copy_out(values, h->G.p, sizeof(double) * h->nr * h->w));
     return AFN_OK;
@@ -750,6 +793,7 @@ afn_status afn_get_W(const afn_handle *hh, double *Wt)
 {
     const Handle *h = reinterpret_cast<const Handle *>(hh);
     if (!h || !Wt) { set_error("NULL argument"); return AFN_ERR_ARG; }
+    if (h->precond != AFN_PRECOND_AFN) { set_error("afn_get_W: not an AFN handle"); return AFN_ERR_ARG; }
     int64_t cnt = h->nr * h->k;
     if (cnt == 0) return AFN_OK;
     if (h->precision != AFN_PREC_MIXED) return copy_out(Wt, h->Wt.p, sizeof(double) * cnt);

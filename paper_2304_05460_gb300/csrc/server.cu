@@ -398,6 +398,11 @@ afn_status afn_server_create(const afn_server_config *cfg, afn_server **out)
     afn_server_config c;
     afn_server_default_config(&c);
     if (cfg) c = *cfg;
+    if (c.opt.precond != AFN_PRECOND_AFN) {
+        set_error("afn_server_create: served solves take the AFN preconditioner only (precond=%d)",
+                  c.opt.precond);
+        return AFN_ERR_ARG;
+    }
     if (c.opt.precision < AFN_PREC_FP64 || c.opt.precision > AFN_PREC_AUTO) {
         set_error("afn_server_create: bad precision %d", c.opt.precision);
         return AFN_ERR_ARG;

@@ -315,3 +315,65 @@ def test_rank_estimate_normal_8d_full(afn):
     kg = afn.afn_rank_estimate(s.X, G, 2.0, 1e-2, m=1000, seed=s.seed, k_max=4000)
     ko = oracle.rank_estimate(s.X, G, 2.0, 1e-2, m=1000, seed=s.seed, k_max=4000)
     assert kg == ko
+
+
+# ------------------------------------------------------ Nystrom branch ---
+NYS = 1   # afn.PRECOND_NYSTROM
+
+
+@pytest.mark.parametrize("n,d,ker,l,mu,k", [(600, 3, G, 0.4, 1e-2, 60), (900, 2, M32, 0.5, 1e-3, 45),
+                                            (500, 5, G, 1.5, 1e-2, 0)])
+def test_nystrom_apply_parity(afn, n, d, ker, l, mu, k):
+    # eq. (nystrom1-smw): the GPU applies (K_nys + mu I)^{-1} through the SMW identity with a
+    # Cholesky of mu I + B^T B; the oracle literally, with an eigendecomposition
+    X = inputs.uniform_points(n, d, 1100 + n)
+    h = afn.afn_build(X, ker, l, mu, k, 16, precision=afn.PREC_FP64, precond=NYS)
+    assert h.info.precond == NYS and h.info.k == k
+    ref = oracle.nystrom_build(X, ker, l, mu, k)
+    assert np.array_equal(afn.afn_get_perm(h), ref["perm"])
+    r = inputs.rhs(n, 3, 1200 + n)
+    s_gpu = afn.afn_apply_precond(h, r)
+    s_ref = np.stack([oracle.nystrom_apply(ref, r[:, c]) for c in range(3)], 1)
+    assert _cmp(s_gpu, s_ref, 0) <= 1e-9
+    afn.afn_free(h)
+
+
+def test_nystrom_solve_iterations_match_oracle(afn):
+    X = inputs.uniform_points(1500, 3, 1300)
+    b = inputs.rhs(1500, 1, 1301)[:, 0]
+    ref = oracle.nystrom_build(X, G, 0.3, 1e-2, 100)
+    _, it_ref, rel_ref, st_ref = oracle.pcg_nystrom(ref, b, 1e-6, max_iter=500)
+    assert st_ref == 0
+    h = afn.afn_build(X, G, 0.3, 1e-2, 100, 16, precision=afn.PREC_FP64, precond=NYS, max_iter=500)
+    x, info = afn.afn_solve(h, b, 1e-6)
+    assert info["converged"] == 1
+    assert abs(int(info["iters"][0]) - it_ref) <= 2
+    assert oracle.true_relres(X, G, 0.3, 1e-2, x, b) <= 1e-6
+    afn.afn_free(h)
+
+
+def test_nystrom_mixed_multi_rhs_reaches_tol(afn):
+    X = inputs.normal_points(4000, 8, 1400)
+    B = inputs.rhs(4000, 32, 1401)
+    h = afn.afn_build(X, G, 4.0, 1e-2, 300, 32, precision=afn.PREC_MIXED, precond=NYS, max_iter=3000)
+    x, info = afn.afn_solve(h, B, 1e-6)
+    assert info["converged"] == 32
+    rel = oracle.true_relres(X, G, 4.0, 1e-2, x[:, :2], B[:, :2])
+    assert np.all(rel <= 1e-6)
+    afn.afn_free(h)
+
+
+def test_alg5_strategy_branch(afn):
+    # Alg. 5: the branch follows the Alg. 4 estimate against the threshold, as in the oracle
+    X = inputs.uniform_points(3000, 3, 1500)
+    k = oracle.rank_estimate(X, G, 0.5, 1e-2, m=200, seed=7, k_max=3000)[0]
+    for thr, want in ((k + 1, NYS), (k, 0)):
+        h = afn.afn_build(X, G, 0.5, 1e-2, 3000, 16, precision=afn.PREC_FP64,
+                          precond=afn.PRECOND_AUTO, precond_threshold=thr, rank_subsample=200,
+                          seed=7)
+        assert h.info.k == k and h.info.precond == want
+        afn.afn_free(h)
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build_batched([dict(points=X[:300], kernel=G, l=0.5, mu=1e-2, k_max=30,
+                                    fsai_nnz=8)], precond=NYS)
+    assert e.value.status == afn.AFN_ERR_ARG
