@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--only", default="",
                     help="'batched' or 'serving': run that workload alone (profiling)")
+    ap.add_argument("--alg5-steps", type=int, default=1,
+                    help="steps of the workload under the paper's Alg. 5 strategy (0 = skip)")
     ap.add_argument("--sequential", action="store_true",
                     help="build and solve the systems of a step one after another (default: "
                          "concurrently, one stream and host thread per system)")
@@ -415,10 +417,15 @@ def main():
     Xd = torch.tensor(s.X, device="cuda")
     Bd = torch.tensor(np.ascontiguousarray(s.B), device="cuda")
 
+    precond_mode = [afn.PRECOND_AFN]   # the headline: AFN on every system
+
     def opts(profile, st=None):
         return afn.options(precision=afn.PREC_MIXED, rank_mode=afn.RANK_ESTIMATE,
                            rank_subsample=1000, seed=SEED, profile=profile,
-                           stream=stream if st is None else st, max_iter=MAXIT)
+                           stream=stream if st is None else st, max_iter=MAXIT,
+                           precond=precond_mode[0])
+
+    alg5_seen = []
 
     stats = {}
     iters_seen = []
@@ -436,6 +443,11 @@ def main():
             raise RuntimeError("l=%g: %d/%d columns reached tol (relres max %.3e)"
                                % (l, info["converged"], args.nrhs, info["relres"].max()))
         with lock:
+            if precond_mode[0] != afn.PRECOND_AFN:
+                alg5_seen.append((l, "nystrom" if h.info.precond == afn.PRECOND_NYSTROM else "afn",
+                                  int(h.info.k), int(info["iters"].max())))
+                afn.afn_free(h)
+                return
             iters_seen.append(int(info["iters"].max()))
             if profile:
                 for nm in ("matvec32", "matvec64", "apply32", "fps", "knn", "chol", "trsm",
@@ -500,6 +512,28 @@ def main():
     e2e_val = args.nrhs * len(LS) * args.e2e_steps * world / e2e_s
     h2d = len(LS) * (s.X.nbytes + s.B.nbytes)
     d2h = len(LS) * s.B.nbytes
+
+    # the paper's full scheme (Alg. 5): the same workload with the preconditioner chosen per
+    # system by the Alg. 4 estimate (Nystrom below k = 2000, AFN above)
+    alg5 = None
+    if args.alg5_steps > 0:
+        precond_mode[0] = afn.PRECOND_AUTO
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.alg5_steps):
+            step(0)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        a_ms = job_time_ms(a0.elapsed_time(a1), dist, "cuda")
+        precond_mode[0] = afn.PRECOND_AFN
+        per = sorted(set(alg5_seen))
+        alg5 = {"value": job_throughput(args.nrhs * len(LS) * args.alg5_steps, world, a_ms),
+                "unit": "solves/s", "ms_per_step": a_ms / args.alg5_steps,
+                "steps": args.alg5_steps,
+                "systems": [{"l": l, "precond": pc, "k": k, "iters": it} for l, pc, k, it in per],
+                "note": "Alg. 5: Nystrom preconditioner (eq. nystrom1-smw) when the Alg. 4 "
+                        "estimate is below 2000, AFN otherwise; same schedule and tolerance"}
 
     # roofline of the dominant kernel (FP32 matvec): FP32-pipe bound
     mv_cnt, mv_ms = stats.get("matvec32", [0, 0.0])
@@ -600,6 +634,7 @@ def main():
                 "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "alg5": alg5,
                 "kernels": kernels,
                 "kernels_note": ("per-class device time summed over launches (CUDA events); "
                                  "with the concurrent schedule the classes of different "
