@@ -770,8 +770,6 @@ __device__ __forceinline__ bool group_live_ap(const GSys &S, int cg)
     return false;
 }
 
-static constexpr int GAP_TR = GemmShape<GC>::TR;   // threads along rows (128)
-
 // MODE 0: zp = L^{-1} r1; 1: t = r2 - W^T zp; 2: W s2 partials; 3: s1 = L^{-T} u
 template <int MODE>
 __global__ void __launch_bounds__(256) gap_gemm_kernel(const GDev *__restrict__ gd)
@@ -869,14 +867,6 @@ __global__ void __launch_bounds__(256) gap_sparse_kernel(const GDev *__restrict_
             S.z32[((int64_t)tl.cg * GC + c) * S.n + S.k + i] = acc;
         }
     }
-}
-
-static int sm_count()
-{
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
 }
 
 int group_sparse_rows() { return 256 / GC; }

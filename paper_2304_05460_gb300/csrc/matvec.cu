@@ -308,38 +308,10 @@ __global__ void __launch_bounds__(NT) matvec32p_kernel(const float *__restrict__
     }
 }
 
-// Single-system tensor-core kernel: CTA = 128 rows x one j-chunk, one
-// partial per (chunk, column), summed in order by matvec_finish.
-template <int DS, int NB, int KER>
-__global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MINB : 2)
-    matvec32tc_kernel(const float *__restrict__ Xs, int64_t n, const float *__restrict__ P,
-                      int64_t ldp, float *__restrict__ part, int64_t chunk)
-{
-    constexpr int NR = NB * 8;
-    __shared__ __align__(16) f2_t xsd[TCJ * (DS + 2)];
-    __shared__ __align__(16) uint32_t phi[TCJ * TcPS<NB>::v];
-    __shared__ __align__(16) uint32_t plo[TCJ * TcPS<NB>::v];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int64_t ia = (int64_t)blockIdx.x * TCR + warp * 16 + g;
-    const int64_t ib = ia + 8;
-    const int64_t j0 = (int64_t)blockIdx.y * chunk;
-    const int64_t j1 = min(n, j0 + chunk);
-    float acc[NB][4];
-    mv32tc_rows<DS, NB, KER>(Xs, n, P, ldp, (int64_t)blockIdx.x * TCR, j0, j1, xsd, phi, plo, acc);
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int c = b * 8 + 2 * t;
-        float *p0 = part + ((int64_t)blockIdx.y * NR + c) * n;
-        float *p1 = p0 + n;
-        if (ia < n) { p0[ia] = acc[b][0]; p1[ia] = acc[b][1]; }
-        if (ib < n) { p0[ib] = acc[b][2]; p1[ib] = acc[b][3]; }
-    }
-}
-
-
-// The same CTA with TMA-staged, double-buffered tiles (mv32tc_rows_async)
-// read from the prepared Xdup / Psp arrays.
+// Single-system mma.sync tensor-core kernel: CTA = 128 rows x one j-chunk with
+// TMA-staged, double-buffered tiles (mv32tc_rows_async) read from the prepared
+// Xdup / Psp arrays; one partial per (chunk, column), summed in order by
+// matvec_finish.
 template <int DS, int NB, int KER>
 __global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MINB : 2)
     matvec32tca_kernel(const float *__restrict__ Xs, int64_t n, const f2_t *__restrict__ Xdup,
