@@ -73,3 +73,16 @@ def test_default_options():
     o = afn.options()
     assert (o.precision, o.landmarks, o.rank_mode, o.max_iter, o.max_outer) == (0, 0, 0, 500, 10)
     assert o.inner_tol == 0.01 and o.fps_start == 0
+    # Alg. 5 fields sit after the stream pointer; AFN is the default preconditioner
+    assert (o.precond, o.precond_threshold) == (afn.PRECOND_AFN, 0)
+    assert ctypes.sizeof(afn.afn_options) == 72
+    assert ctypes.sizeof(afn.afn_build_info) == 96
+
+
+def test_bad_precond_rejected_without_gpu():
+    from paper_2304_05460_gb300 import afn
+    X = np.zeros((4, 3))
+    for kw in (dict(precond=3), dict(precond=-1), dict(precond=afn.PRECOND_AUTO, precond_threshold=-5)):
+        with pytest.raises(afn.AfnError) as e:
+            afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, 2, **kw)
+        assert e.value.status == afn.AFN_ERR_ARG
