@@ -120,6 +120,23 @@ def test_matvec_fp32(afn, n, d, ker, nrhs):
     assert err.max() <= 2e-5, err.max()
 
 
+@pytest.mark.parametrize("which", ["normal_8d", "clusters_3d"])
+def test_matvec_fp32_tensor_core_full_size(afn, which):
+    # the launch configuration the benchmark times (32-column pieces on the tcgen05 kernel):
+    # n = 50k, d = 8, Gaussian, 32 columns; n = 200k, d = 3, Matern-3/2, 64 columns
+    if which == "normal_8d":
+        s = inputs.normal_8d(l=2.0, nrhs=32)
+        ker, l, mu = G, 2.0, 1e-2
+    else:
+        s = inputs.clusters_3d(nrhs=64)
+        ker, l, mu = s.kernel, s.l, s.mu
+    rows = inputs.rng(11).choice(s.n, 48, replace=False)
+    q = afn.afn_kernel_matvec(s.X, ker, l, mu, s.B, precision=afn.PREC_MIXED)
+    ref = oracle.matvec_rows(s.X, ker, l, mu, s.B, rows)
+    absb = oracle.matvec_rows(s.X, ker, l, mu, np.abs(s.B), rows)
+    assert np.all(np.abs(q[rows] - ref) <= 2e-5 * absb)
+
+
 def test_matvec_sampled_rows_full_size(afn):
     s = inputs.normal_8d(l=2.0, nrhs=2)
     rows = inputs.rng(9).choice(s.n, 64, replace=False)
