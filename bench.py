@@ -7,10 +7,11 @@ capped at 4000, FSAI with 64 nonzeros per row, 32 right-hand sides
 b ~ N(0, 1), tol 1e-6.  One step = build + solve for each length-scale
 l in {0.5, 1, 2, 4} (4 systems x 32 right-hand sides = 128 solves), mixed
 precision (FP32 matvec / apply / FSAI build, FP64 Cholesky, dots and
-residual-correction loop).  Inputs (50,000 x 8 points, 50,000 x 32 RHS,
-12.8 MB) are regenerated in HBM every step and the solve streams W^T
-(46,000 x 4,000 FP32 = 736 MB per system) many times per step, far more
-than L2 (129 MB), so no L2 flush is inserted between steps.
+residual-correction loop).  The inputs (50,000 x 8 points, 50,000 x 32 RHS,
+12.8 MB) are created once and stay resident in HBM; every step builds the
+factors anew and the solve streams W^T (46,000 x 4,000 FP32 = 736 MB per
+system) many times per step, far more than L2 (129 MB), so no L2 flush is
+inserted between steps.
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle (the reference arm) on a bounded sample of the same workload.

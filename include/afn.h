@@ -99,7 +99,21 @@ typedef struct {
     int32_t precond;           /* afn_precond, default AFN_PRECOND_AFN; the batched and
                                   served solves take AFN only */
     int32_t precond_threshold; /* Alg. 5's rank threshold; 0 = 2000 */
+    int32_t factors;           /* mixed handles: arithmetic of the factor build (afn_factors),
+                                  default AFN_FACTORS_FP32 */
+    int32_t apply_tc;          /* mixed handles: the two W products of the apply (Alg. 3) on
+                                  the tcgen05 tensor cores (three-pass tf32, FP32 accumulation)
+                                  for every 16- or 32-column piece: 0 = CUDA-core tiles,
+                                  1 = tensor cores; default 0 */
 } afn_options;
+
+typedef enum {
+    AFN_FACTORS_FP32 = 0,      /* K12 from the FP32 points, W = L^{-1} K12 by an FP32 triangular
+                                  solve, FSAI Schur blocks with an FP32 Gram (Alg. 1) */
+    AFN_FACTORS_FP64 = 1       /* W, the triangular inverses and G built in FP64 as for an FP64
+                                  handle (G within the FP64 parity bound of the oracle's), then
+                                  rounded to FP32 for the apply */
+} afn_factors;
 
 typedef struct afn_handle afn_handle;   /* opaque; owns every device buffer of one system */
 
@@ -176,8 +190,8 @@ afn_status afn_get_G(const afn_handle *h, int32_t *pattern, double *values);
 afn_status afn_get_W(const afn_handle *h, double *Wt);
 /* s = M^{-1} r for nrhs columns (Alg. 3), vectors in PERMUTED order, FP64 in
  * and out.  FP64 handles apply in FP64; mixed handles run the FP32 apply of
- * their solves (r rounded to FP32; with AFN_APPLY_TC=1 in the environment
- * and a multiple of 16 columns the W products run on the tensor cores).
+ * their solves (r rounded to FP32; with the handle's option apply_tc = 1 and
+ * a multiple of 16 columns the W products run on the tensor cores).
  * AFN_ERR_TIMEOUT if a staged copy or MMA did not complete. */
 afn_status afn_apply_precond(afn_handle *h, const double *r, int32_t nrhs, double *s);
 
@@ -199,6 +213,19 @@ int64_t afn_launch_count(void);
  * the device.  No paper counterpart. */
 void afn_release_cached_memory(void);
 
+/* Limit, in nanoseconds, of the bounded device-side waits of the tensor-core
+ * (tcgen05) kernels: the FP32 kernel matvec with 16 or 32 columns a piece
+ * and the tensor-core W products of the FP32 apply.  A wait that runs past
+ * it (a staged copy or an MMA that has not completed) raises the kernel's
+ * abort flag; the kernel then still waits, up to 2 s, for the copies and
+ * MMAs it has in flight, releases its tensor memory and returns, and the
+ * entry point that launched it returns AFN_ERR_TIMEOUT with its results
+ * invalid.  ns <= 0 restores the default, 2 s.  Process-wide; takes effect at
+ * the next launch.  For testing the failure path (a limit of a few
+ * nanoseconds makes the waits run out on a healthy GPU).  No paper
+ * counterpart. */
+void afn_set_wait_limit_ns(int64_t ns);
+
 /* ---- operator-level entry points (each one step of the hot path) ------- */
 
 /*
@@ -217,10 +244,11 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
 
 /*
  * afn_kernel_matvec_noalloc: the FP64 q = (K + mu I) p of afn_kernel_matvec
- * for callers that cannot allocate device memory (code running while a stream
- * is captured into a CUDA graph, services with a pre-planned device pool,
- * plug-ins that must not grow the process's device footprint).  The paper has
- * no counterpart; this is an interface convenience.
+ * for callers that cannot allocate device memory: services whose device
+ * memory is planned up front and handed out by their own pool (an allocation
+ * outside it breaks the plan, or fails once the pool holds the rest of the
+ * device), and plug-ins that must not grow the host process's device
+ * footprint.  The paper has no counterpart; this is an interface convenience.
  *  - points (n x d row-major), p and q (n x nrhs column-major) must all be
  *    device memory on the current device; nothing is staged or allocated.
  *  - The split-K partial sums live in a fixed 16 MiB __device__ array built

@@ -485,6 +485,8 @@ def _sig_sampled(lib):
     lib.orc_matvec_rows.argtypes = [P, i64, i32, i32, dbl, dbl, P, i32, P, i64, P]
     lib.orc_fsai_rows.restype = i32
     lib.orc_fsai_rows.argtypes = [P, i64, i32, i32, dbl, dbl, i64, i32, P, P, P, i64, P]
+    lib.orc_knn_rows.restype = None
+    lib.orc_knn_rows.argtypes = [P, i64, i32, i32, P, i64, P]
 
 
 def matvec_rows(X, kernel, l, mu, p, rows):
@@ -498,6 +500,19 @@ def matvec_rows(X, kernel, l, mu, p, rows):
     lib.orc_matvec_rows(_p(X), X.shape[0], X.shape[1], _kid(kernel), float(l), float(mu), _p(P),
                         P.shape[1], _p(rows), rows.shape[0], _p(out))
     return np.ascontiguousarray(out)
+
+
+def knn_rows(Xr, w, rows):
+    """Rows `rows` of the FSAI pattern of Xr (Sec. 3.1), (len(rows), w) int32."""
+    lib = _L()
+    _sig_sampled(lib)
+    Xr = _f64(Xr)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= Xr.shape[0]):
+        raise ValueError("knn_rows: row index out of range")
+    out = np.empty((max(rows.shape[0], 1), int(w)), dtype=np.int32)
+    lib.orc_knn_rows(_p(Xr), Xr.shape[0], Xr.shape[1], int(w), _p(rows), rows.shape[0], _p(out))
+    return out[: rows.shape[0]].copy()
 
 
 def fsai_rows(Xp, kernel, l, mu, k, w, Lo, pattern, rows):

@@ -256,6 +256,35 @@ int orc_permutation(int64_t n, const int64_t *landmarks, int64_t k, int64_t *per
 /* itself.  Rows with fewer than w-1 predecessors take all of them.           */
 /* rowlen[i] = number of used slots; unused slots hold -1.                   */
 /* ------------------------------------------------------------------------ */
+/* One row of the pattern: the scan over j = 0..i-1 in ascending order with a
+ * sorted candidate list of length m = min(i, w-1); bd/bj hold >= w-1 slots.
+ * Returns the number of used slots (cnt + 1). */
+static int32_t knn_row(const double *Xr, int d, int w, int64_t i, double *bd, int64_t *bj,
+                       int32_t *prow)
+{
+    int64_t m = i < (int64_t)(w - 1) ? i : (int64_t)(w - 1);
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < i && m > 0; ++j) {
+        double r2 = orc_sqdist(Xr + i * d, Xr + j * d, d);
+        /* candidates arrive in ascending j, so an equal distance never
+         * displaces an entry already held (lower index wins ties) */
+        if (cnt == m && !(r2 < bd[m - 1])) continue;
+        int64_t pos = (cnt < m) ? cnt : m - 1;
+        while (pos > 0 && r2 < bd[pos - 1]) {
+            bd[pos] = bd[pos - 1];
+            bj[pos] = bj[pos - 1];
+            --pos;
+        }
+        bd[pos] = r2;
+        bj[pos] = j;
+        if (cnt < m) ++cnt;
+    }
+    for (int p = 0; p < w; ++p) prow[p] = -1;
+    for (int64_t p = 0; p < cnt; ++p) prow[p] = (int32_t)bj[p];
+    prow[cnt] = (int32_t)i;
+    return (int32_t)(cnt + 1);
+}
+
 void orc_knn_pattern(const double *Xr, int64_t nr, int d, int w, int32_t *pat, int32_t *rowlen)
 {
 #pragma omp parallel
@@ -263,29 +292,27 @@ void orc_knn_pattern(const double *Xr, int64_t nr, int d, int w, int32_t *pat, i
         double *bd = (double *)malloc(sizeof(double) * (size_t)(w > 1 ? w : 1));
         int64_t *bj = (int64_t *)malloc(sizeof(int64_t) * (size_t)(w > 1 ? w : 1));
 #pragma omp for schedule(dynamic, 8)
-        for (int64_t i = 0; i < nr; ++i) {
-            int64_t m = i < (int64_t)(w - 1) ? i : (int64_t)(w - 1);
-            int64_t cnt = 0;
-            for (int64_t j = 0; j < i && m > 0; ++j) {
-                double r2 = orc_sqdist(Xr + i * d, Xr + j * d, d);
-                /* candidates arrive in ascending j, so an equal distance never
-                 * displaces an entry already held (lower index wins ties) */
-                if (cnt == m && !(r2 < bd[m - 1])) continue;
-                int64_t pos = (cnt < m) ? cnt : m - 1;
-                while (pos > 0 && r2 < bd[pos - 1]) {
-                    bd[pos] = bd[pos - 1];
-                    bj[pos] = bj[pos - 1];
-                    --pos;
-                }
-                bd[pos] = r2;
-                bj[pos] = j;
-                if (cnt < m) ++cnt;
-            }
-            for (int p = 0; p < w; ++p) pat[i * w + p] = -1;
-            for (int64_t p = 0; p < cnt; ++p) pat[i * w + p] = (int32_t)bj[p];
-            pat[i * w + cnt] = (int32_t)i;
-            rowlen[i] = (int32_t)(cnt + 1);
-        }
+        for (int64_t i = 0; i < nr; ++i)
+            rowlen[i] = knn_row(Xr, d, w, i, bd, bj, pat + i * w);
+        free(bd);
+        free(bj);
+    }
+}
+
+/* The pattern rows rows[0..nrows) of the same definition (row i depends only
+ * on points 0..i, so large problems are checked on a sample of rows at O(i d)
+ * each).  pat: nrows x w. */
+void orc_knn_rows(const double *Xr, int64_t nr, int d, int w, const int64_t *rows, int64_t nrows,
+                  int32_t *pat)
+{
+    (void)nr;
+#pragma omp parallel
+    {
+        double *bd = (double *)malloc(sizeof(double) * (size_t)(w > 1 ? w : 1));
+        int64_t *bj = (int64_t *)malloc(sizeof(int64_t) * (size_t)(w > 1 ? w : 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < nrows; ++q)
+            (void)knn_row(Xr, d, w, rows[q], bd, bj, pat + q * w);
         free(bd);
         free(bj);
     }

@@ -27,6 +27,7 @@ PRECOND_AFN, PRECOND_NYSTROM, PRECOND_AUTO = 0, 1, 2
 MATVEC_DF = PREC_DF        # afn_kernel_matvec: FP64-accurate double-float
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
+FACTORS_FP32, FACTORS_FP64 = 0, 1
 
 
 class AfnError(RuntimeError):
@@ -40,7 +41,8 @@ class afn_options(C.Structure):
                 ("rank_subsample", C.c_int32), ("fps_start", C.c_int64), ("seed", C.c_uint64),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("inner_tol", C.c_double),
                 ("check_every", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
-                ("precond", C.c_int32), ("precond_threshold", C.c_int32)]
+                ("precond", C.c_int32), ("precond_threshold", C.c_int32),
+                ("factors", C.c_int32), ("apply_tc", C.c_int32)]
 
 
 class afn_build_info(C.Structure):
@@ -95,6 +97,7 @@ def _load():
                                     C.POINTER(i64), C.POINTER(i32), P]),
         "afn_launch_count": (i64, []),
         "afn_release_cached_memory": (None, []),
+        "afn_set_wait_limit_ns": (None, [i64]),
         "afn_kernel_matvec_noalloc": (i32, [P, i64, i32, i32, dbl, dbl, P, i32, P, P]),
         "afn_build_batched": (i32, [C.POINTER(afn_system), i32, C.POINTER(afn_options),
                                     C.POINTER(P)]),
@@ -314,6 +317,11 @@ def afn_release_cached_memory():
     _lib.afn_release_cached_memory()
 
 
+def afn_set_wait_limit_ns(ns: int):
+    """Limit of the tensor-core kernels' bounded device waits (ns; <= 0 = 2 s)."""
+    _lib.afn_set_wait_limit_ns(int(ns))
+
+
 def afn_reset_kernel_stats(h: Handle):
     _check(_lib.afn_reset_kernel_stats(h.ptr))
 
@@ -334,11 +342,35 @@ def afn_kernel_matvec(points, kernel, l, mu, p, precision=PREC_FP64, stream=None
 
 
 def afn_kernel_matvec_noalloc(points, kernel, l, mu, p, q, stream=None):
-    """FP64 (K + mu I) p into q without any device allocation.  points (n x d),
-    p and q (n x nrhs) must be contiguous CUDA float64 tensors; p and q are
-    passed as their transposes' storage (column-major n x nrhs)."""
+    """FP64 (K + mu I) p into q without any device allocation (for callers
+    whose device memory is planned up front, see include/afn.h).  points: a
+    contiguous float64 CUDA tensor of shape (n, d).  p and q: contiguous
+    float64 CUDA tensors of shape (nrhs, n) -- the storage of n x nrhs
+    column-major blocks, one column per row of the tensor -- or of shape (n,)
+    for one column.  Everything is checked before the library is called."""
+    def need(ok, what):
+        if not ok:
+            raise ValueError("afn_kernel_matvec_noalloc: " + what)
+
+    for name, t in (("points", points), ("p", p), ("q", q)):
+        need(_is_torch(t), "%s must be a torch tensor" % name)
+        need(str(t.dtype) == "torch.float64", "%s must be float64" % name)
+        need(t.is_contiguous(), "%s must be contiguous" % name)
+    need(points.dim() == 2, "points must have shape (n, d)")
     n, d = int(points.shape[0]), int(points.shape[1])
-    nrhs = 1 if p.dim() == 1 else int(p.shape[0])
+    need(p.dim() in (1, 2) and tuple(p.shape) == tuple(q.shape), "p and q must have one shape")
+    if p.dim() == 1:
+        need(int(p.shape[0]) == n, "p of shape (n,) must have n = %d entries" % n)
+        nrhs = 1
+    else:
+        need(int(p.shape[1]) == n, "p and q must have shape (nrhs, n) with n = %d" % n)
+        nrhs = int(p.shape[0])
+    for name, t in (("points", points), ("p", p), ("q", q)):
+        need(t.is_cuda, "%s must be in CUDA memory" % name)
+    import torch
+    cur = torch.cuda.current_device()
+    for name, t in (("points", points), ("p", p), ("q", q)):
+        need(t.device.index == cur, "%s must be on the current device (%d)" % (name, cur))
     _check(_lib.afn_kernel_matvec_noalloc(C.c_void_p(points.data_ptr()), n, d, int(kernel),
                                           float(l), float(mu), C.c_void_p(p.data_ptr()), nrhs,
                                           C.c_void_p(q.data_ptr()), _stream_ptr(stream)))

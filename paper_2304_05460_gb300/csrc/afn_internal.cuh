@@ -29,6 +29,10 @@ afn_status cuda_fail(cudaError_t e, const char *what);
         if (s_ != AFN_OK) return s_;                                    \
     } while (0)
 
+// limit of the bounded device-side waits of the tcgen05 kernels, ns
+// (afn_set_wait_limit_ns; 2 s by default)
+uint64_t wait_limit_ns();
+
 // device status word values (written by kernels, read by the host)
 enum : int { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_TIMEOUT = 2 };
 
@@ -234,7 +238,7 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
                      const T *r, int nrhs, T *s, T *tmp, cudaStream_t st);
 size_t apply_tmp_elems(const Handle *h, int nrhs);
 // tiled images of W for the tcgen05 apply of a mixed handle (no-op when they
-// exist, the handle has no W, or AFN_APPLY_TC=1 is not set)
+// exist, the handle has no W, or its option apply_tc is 0)
 afn_status apply_tc_prepare(Handle *h, cudaStream_t s);
 // the Nystrom factors of a handle whose L (chol(K11 + nu I)) and Bn are set:
 // Lc = chol(mu I + B^T B) and its triangular inverses (FP32 copies for mixed

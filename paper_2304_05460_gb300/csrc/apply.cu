@@ -430,22 +430,15 @@ __global__ void gu_bsplit_kernel(const float *__restrict__ X, int64_t ldx, int64
     Bk[w + GKU * NR] = lo;
 }
 
-// AFN_APPLY_TC=1 runs the W products on the tensor cores (read at every
-// apply).  Off by default: on the normal_8d systems the products are 1.5x
-// faster but the solve takes 5 % more iterations (l = 2: 1044 against 992),
-// a net loss.
-static bool use_apply_tc()
-{
-    const char *e = getenv("AFN_APPLY_TC");
-    return e && strcmp(e, "1") == 0;
-}
+// the handle's option apply_tc = 1 runs the W products on the tensor cores
+static bool use_apply_tc(const Handle *h) { return h->opt.apply_tc == 1; }
 
 static int64_t gu_nks(int64_t K) { return (K + GKU - 1) / GKU; }
 static int64_t gu_tiles(int64_t M) { return (M + UR - 1) / UR; }
 
 afn_status apply_tc_prepare(Handle *h, cudaStream_t s)
 {
-    if (h->wu_tried || !use_apply_tc()) return AFN_OK;
+    if (h->wu_tried || !use_apply_tc(h)) return AFN_OK;
     h->wu_tried = true;
     const int64_t k = h->k, nr = h->nr;
     // small products stay on the CUDA-core tiles
@@ -506,12 +499,12 @@ static afn_status prod_tc(const float *Atl, int64_t M, int64_t K, const float *X
             gu_bsplit_kernel<32><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X + c0 * ldx, ldx, K, nks, Bk);
             const int smem = GNST * GStage<32>::BYTES;
             cudaFuncSetAttribute(gemm32u_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            gemm32u_kernel<4><<<grid, GUT, smem, s>>>(Atl, M, nks, Bk, part, cs, err);
+            gemm32u_kernel<4><<<grid, GUT, smem, s>>>(Atl, M, nks, Bk, part, cs, err, wait_limit_ns());
         } else {
             gu_bsplit_kernel<16><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X + c0 * ldx, ldx, K, nks, Bk);
             const int smem = GNST * GStage<16>::BYTES;
             cudaFuncSetAttribute(gemm32u_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            gemm32u_kernel<2><<<grid, GUT, smem, s>>>(Atl, M, nks, Bk, part, cs, err);
+            gemm32u_kernel<2><<<grid, GUT, smem, s>>>(Atl, M, nks, Bk, part, cs, err, wait_limit_ns());
         }
         const int64_t te = M * b;
         gemm_finish<float><<<(unsigned)((te + 255) / 256), 256, 0, s>>>(
@@ -692,7 +685,7 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
     T *s1 = s, *s2 = s + k;
     // tcgen05 W products (mixed handles with tiled images, 16 or 32 columns a piece)
     const bool tc = std::is_same<T, float>::value && h->Wu1.p && h->Wu2.p && nrhs % 16 == 0 &&
-                    use_apply_tc() &&
+                    use_apply_tc(h) &&
                     (size_t)32 * (size_t)std::max(nr, k) <= pcap;
     uint32_t *Bk = reinterpret_cast<uint32_t *>(part + pcap + nr * nrhs);
     int *err = h->status.as<int>() + 3;

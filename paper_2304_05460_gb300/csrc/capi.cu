@@ -36,6 +36,11 @@ afn_status cuda_fail(cudaError_t e, const char *what)
 
 static thread_local cudaStream_t tl_stream = nullptr;
 
+// limit of the bounded waits of the tcgen05 kernels (afn_set_wait_limit_ns)
+static constexpr uint64_t WAIT_LIMIT_DEFAULT_NS = 2000000000ull;
+static std::atomic<uint64_t> g_wait_limit_ns{WAIT_LIMIT_DEFAULT_NS};
+uint64_t wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+
 cudaStream_t current_stream() { return tl_stream; }
 StreamGuard::StreamGuard(cudaStream_t s) : prev(tl_stream) { tl_stream = s; }
 StreamGuard::~StreamGuard() { tl_stream = prev; }
@@ -410,6 +415,8 @@ static afn_status build_impl(Handle *h, const double *points)
     }
     log.mark("points");
     const bool mixed = h->precision == AFN_PREC_MIXED;
+    // mixed handles with FP64 factors: W and G as for an FP64 handle
+    const bool f64fac = mixed && h->opt.factors == AFN_FACTORS_FP64;
     if (mixed || h->precision == AFN_PREC_DF) {
         AFN_TRY(h->Xdf.alloc(sizeof(float2) * (size_t)(n * ds)));
         AFN_TRY(make_points_df(h->X64.as<double>(), n, d, ds, h->kernel, h->l, h->Xdf.as<float2>(), s));
@@ -453,7 +460,7 @@ static afn_status build_impl(Handle *h, const double *points)
         AFN_TRY(sync_status(h, "Cholesky of K11 + mu I"));
         log.mark("cholesky");
         Scope sc(&h->prof, K_TRSM);
-        if (!mixed) {
+        if (!mixed || f64fac) {
             AFN_TRY(h->Linv.alloc(sizeof(double) * (size_t)(k * k)));
             AFN_TRY(h->LinvT.alloc(sizeof(double) * (size_t)(k * k)));
             AFN_TRY(tri_inverse64(h->L.as<double>(), k, h->Linv.as<double>(), h->LinvT.as<double>(), s));
@@ -461,6 +468,20 @@ static afn_status build_impl(Handle *h, const double *points)
                 AFN_TRY(h->Wt.alloc(sizeof(double) * (size_t)(nr * k)));
                 AFN_TRY(kernel_block(Xr, nr, Xk, k, d, kp, 0.0, h->Wt.as<double>(), k, s));
                 AFN_TRY(trsm_right_lt64(h->L.as<double>(), k, h->Wt.as<double>(), nr, s));
+            }
+            if (mixed) {
+                // FP64 factors rounded to FP32 for the apply of the mixed solves
+                AFN_TRY(h->Linv32.alloc(sizeof(float) * (size_t)(k * k)));
+                AFN_TRY(h->LinvT32.alloc(sizeof(float) * (size_t)(k * k)));
+                AFN_TRY(convert64to32(h->Linv.as<double>(), h->Linv32.as<float>(), k * k, s));
+                AFN_TRY(convert64to32(h->LinvT.as<double>(), h->LinvT32.as<float>(), k * k, s));
+                if (nr > 0) {
+                    AFN_TRY(h->Wt32.alloc(sizeof(float) * (size_t)(nr * k)));
+                    AFN_TRY(convert64to32(h->Wt.as<double>(), h->Wt32.as<float>(), nr * k, s));
+                }
+                AFN_CUDA(cudaStreamSynchronize(s));
+                h->Linv.release();
+                h->LinvT.release();
             }
         } else {
             DevBuf L32;
@@ -490,9 +511,9 @@ static afn_status build_impl(Handle *h, const double *points)
         AFN_TRY(h->G.alloc(sizeof(double) * (size_t)(nr * w)));
         {
             Scope sc(&h->prof, K_FSAI);
-            if (!mixed)
-                AFN_TRY(fsai_build64(Xr, nr, d, kp, h->Wt.as<double>(), k, h->pat.as<int32_t>(), w,
-                                     h->G.as<double>(), st, s));
+            if (!mixed || f64fac)
+                AFN_TRY(fsai_build64(Xr, nr, d, kp, k > 0 ? h->Wt.as<double>() : nullptr, k,
+                                     h->pat.as<int32_t>(), w, h->G.as<double>(), st, s));
             else
                 AFN_TRY(fsai_build32(Xr, nr, d, kp, h->Wt32.as<float>(), k, h->pat.as<int32_t>(), w,
                                      h->G.as<double>(), st, s));
@@ -502,6 +523,11 @@ static afn_status build_impl(Handle *h, const double *points)
         if (mixed) {
             AFN_TRY(h->G32.alloc(sizeof(float) * (size_t)(nr * w)));
             AFN_TRY(convert64to32(h->G.as<double>(), h->G32.as<float>(), nr * w, s));
+            if (f64fac) {
+                // the FP64 W has served the FSAI build; the solves read its FP32 copy
+                AFN_CUDA(cudaStreamSynchronize(s));
+                h->Wt.release();
+            }
         }
         AFN_TRY(h->gt_ptr.alloc(sizeof(int32_t) * (size_t)(nr + 1)));
         AFN_TRY(h->gt_row.alloc(sizeof(int32_t) * (size_t)(nr * w)));
@@ -525,6 +551,14 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         !std::isfinite(l) || !(mu > 0) || !std::isfinite(mu) || k_max < 0 || fsai_nnz < 1) {
         set_error("afn_build: invalid argument (n=%lld d=%d kernel=%d l=%g mu=%g k_max=%d w=%d)",
                   (long long)n, d, kernel, l, mu, k_max, fsai_nnz);
+        return AFN_ERR_ARG;
+    }
+    if (o.factors != AFN_FACTORS_FP32 && o.factors != AFN_FACTORS_FP64) {
+        set_error("bad factors %d", o.factors);
+        return AFN_ERR_ARG;
+    }
+    if (o.apply_tc != 0 && o.apply_tc != 1) {
+        set_error("bad apply_tc %d", o.apply_tc);
         return AFN_ERR_ARG;
     }
     if (o.precond < AFN_PRECOND_AFN || o.precond > AFN_PRECOND_AUTO || o.precond_threshold < 0) {
@@ -652,9 +686,16 @@ void afn_default_options(afn_options *o)
     o->stream = nullptr;
     o->precond = AFN_PRECOND_AFN;
     o->precond_threshold = 0;
+    o->factors = AFN_FACTORS_FP32;
+    o->apply_tc = 0;
 }
 
 const char *afn_last_error(void) { return g_err; }
+
+void afn_set_wait_limit_ns(int64_t ns)
+{
+    g_wait_limit_ns.store(ns > 0 ? (uint64_t)ns : WAIT_LIMIT_DEFAULT_NS, std::memory_order_relaxed);
+}
 
 afn_status afn_build(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
                      double mu, int32_t k_max, int32_t fsai_nnz, const afn_options *opt,
@@ -822,6 +863,7 @@ afn_status afn_apply_precond(afn_handle *hh, const double *r, int32_t nrhs, doub
         DevBuf r32, s32;
         AFN_TRY(r32.alloc(sizeof(float) * tot));
         AFN_TRY(s32.alloc(sizeof(float) * tot));
+        AFN_CUDA(cudaMemsetAsync(h->status.as<int>() + 3, 0, sizeof(int), s));
         AFN_TRY(convert64to32(R, r32.as<float>(), tot, s));
         if (nrhs % 16 == 0) AFN_TRY(apply_tc_prepare(h, s));
         AFN_TRY(afn_apply<float>(h, h->Linv32.as<float>(), h->LinvT32.as<float>(),
@@ -831,7 +873,8 @@ afn_status afn_apply_precond(afn_handle *hh, const double *r, int32_t nrhs, doub
         AFN_CUDA(cudaStreamSynchronize(s));
         if (h->status.p) {
             int hs[4];
-            AFN_CUDA(cudaMemcpy(hs, h->status.p, sizeof(hs), cudaMemcpyDeviceToHost));
+            AFN_CUDA(cudaMemcpyAsync(hs, h->status.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+            AFN_CUDA(cudaStreamSynchronize(s));
             if (hs[3] != 0) {
                 set_error("afn_apply_precond: a staged copy or MMA did not complete in time");
                 return AFN_ERR_TIMEOUT;

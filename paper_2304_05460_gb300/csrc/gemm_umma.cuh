@@ -16,7 +16,8 @@
 // words) and fold the accumulator (warp w: TMEM lane quarter w % 4, columns
 // half w / 4), warp 8 issues the copies and the MMAs and owns the TMEM
 // allocation.  Stages rotate through GNST buffers; the accumulator is
-// double-buffered.  Every wait is bounded (2 s) with a CTA-wide abort flag.
+// double-buffered.  Every wait is bounded (the wait limit, 2 s by default) with a CTA-wide
+// abort flag; the drain after an abort waits up to 2 s for copies in flight.
 #pragma once
 
 #include "matvec_umma.cuh"
@@ -50,7 +51,7 @@ template <int NB>
 __global__ void __launch_bounds__(GUT, 1)
     gemm32u_kernel(const float *__restrict__ Atl, int64_t M, int64_t nks,
                    const uint32_t *__restrict__ Bk, float *__restrict__ part, int64_t chunk_st,
-                   int *__restrict__ err)
+                   int *__restrict__ err, uint64_t wait_ns)
 {
     constexpr int NR = NB * 8;
     constexpr int AB = GStage<NR>::AB, BB = GStage<NR>::BB, SB = GStage<NR>::BYTES;
@@ -103,10 +104,10 @@ __global__ void __launch_bounds__(GUT, 1)
             const uint32_t base_s = smem_addr(gsm);
             for (int s = 0; s < nst && !*abort; ++s) {
                 const int sb = s % GNST, b = s & 1;
-                if (!mbar_wait_abort(&full[sb], (uint32_t)(s / GNST) & 1u, abort)) break;
+                if (!mbar_wait_abort(&full[sb], (uint32_t)(s / GNST) & 1u, abort, wait_ns)) break;
                 observed = s + 1;
-                if (!mbar_wait_abort(&split[sb], (uint32_t)(s / GNST) & 1u, abort)) break;
-                if (s >= 2 && !mbar_wait_abort(&dempty[b], (uint32_t)((s - 2) >> 1) & 1u, abort)) break;
+                if (!mbar_wait_abort(&split[sb], (uint32_t)(s / GNST) & 1u, abort, wait_ns)) break;
+                if (s >= 2 && !mbar_wait_abort(&dempty[b], (uint32_t)((s - 2) >> 1) & 1u, abort, wait_ns)) break;
                 tm_fence_after();
                 const uint32_t ahi = base_s + sb * SB, alo = ahi + AB;
                 const uint32_t bhi = ahi + 2 * AB, blo = bhi + BB;
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(GUT, 1)
                 // issued one stage earlier
                 if (s >= 1 && issued < nst) {
                     const int sp = s - 1;
-                    if (!mbar_wait_abort(&empty[sp % GNST], (uint32_t)(sp / GNST) & 1u, abort)) break;
+                    if (!mbar_wait_abort(&empty[sp % GNST], (uint32_t)(sp / GNST) & 1u, abort, wait_ns)) break;
                     issue(issued++);
                 }
             }
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(GUT, 1)
 #pragma unroll
         for (int h = 0; h < FC / 2; ++h) acc[h] = cmp[h] = 0ull;
         auto fold = [&](int s) -> bool {
-            if (!mbar_wait_abort_warp(&bdone[s & 1], (uint32_t)(s >> 1) & 1u, abort)) return false;
+            if (!mbar_wait_abort_warp(&bdone[s & 1], (uint32_t)(s >> 1) & 1u, abort, wait_ns)) return false;
             tm_fence_after();
             const uint32_t dcol = tbase + lane_off + (s & 1) * NR + hf * FC;
             if constexpr (FC % 16 == 0) {
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(GUT, 1)
         bool ok = true;
         for (int s = 0; s < nst && ok; ++s) {
             const int sb = s % GNST;
-            if (!mbar_wait_abort_warp(&full[sb], (uint32_t)(s / GNST) & 1u, abort)) {
+            if (!mbar_wait_abort_warp(&full[sb], (uint32_t)(s / GNST) & 1u, abort, wait_ns)) {
                 ok = false;
                 break;
             }

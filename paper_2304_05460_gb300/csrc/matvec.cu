@@ -472,7 +472,7 @@ static void launch_u(const float *Xs, int64_t n, const float *Xpr, const uint32_
                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     dim3 g((unsigned)((n + UR - 1) / UR), (unsigned)js);
     matvec32u_kernel<DS, NB, KER, VAR, UH, UK, P4, LEAN><<<g, umma_threads(UH), smem, s>>>(
-        Xs, n, Xpr, Pk, part, chunk_st, nstage, err);
+        Xs, n, Xpr, Pk, part, chunk_st, nstage, err, wait_limit_ns());
 }
 
 // distance form and row-warp split of the tcgen05 path (AFN_UMMA_VARIANT =

@@ -18,10 +18,11 @@
 //              allocation.
 // A and D are double-buffered so that the generation of block c + 1, the
 // MMAs of block c and the fold of block c - 1 overlap; the staged tiles
-// rotate through NST buffers.  Every wait is bounded (2 s); a thread that
-// gives up raises a CTA-wide abort flag that ends every other wait, and the
-// CTA still waits (bounded) for its copies and MMAs in flight before it
-// releases tensor memory and returns.
+// rotate through NST buffers.  Every wait is bounded (the kernel's wait
+// limit, 2 s unless afn_set_wait_limit_ns lowered it); a thread that gives up
+// raises a CTA-wide abort flag that ends every other wait, and the CTA still
+// waits (up to 2 s, whatever the limit) for its copies and MMAs in flight
+// before it releases tensor memory and returns.
 //
 // Operand layouts (PTX ISA, tcgen05): the accumulator and an A operand in
 // tensor memory hold row i in lane i, one 32-bit column per element; the B
@@ -177,8 +178,10 @@ __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
-// bounded wait that also ends when another thread of the CTA has given up
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+// bounded wait that also ends when another thread of the CTA has given up;
+// limit_ns is the kernel's wait limit (afn_set_wait_limit_ns, default 2 s)
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                                uint64_t limit_ns)
 {
     uint64_t t0 = 0;
     for (uint32_t spin = 0;; ++spin) {
@@ -187,7 +190,7 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, 
             if (*abort) return false;
             const uint64_t t = globaltimer_ns();
             if (spin == 0) t0 = t;
-            else if (t - t0 > 2000000000ull) {
+            else if (t - t0 > limit_ns) {
                 *abort = 1;
                 return false;
             }
@@ -197,9 +200,9 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, 
 
 // warp-uniform variant (all lanes wait, all take the same branch)
 __device__ __forceinline__ bool mbar_wait_abort_warp(uint64_t *bar, uint32_t parity,
-                                                     volatile int *abort)
+                                                     volatile int *abort, uint64_t limit_ns)
 {
-    const bool got = mbar_wait_abort(bar, parity, abort);
+    const bool got = mbar_wait_abort(bar, parity, abort, limit_ns);
     return __all_sync(0xffffffffu, got);
 }
 
@@ -250,7 +253,7 @@ template <int DS, int NB, int KER, int VAR, int UH, int UK, bool P4, int LEAN>
 __global__ void __launch_bounds__(umma_threads(UH), 2)
     matvec32u_kernel(const float *__restrict__ Xs, int64_t n, const float *__restrict__ Xpr,
                      const uint32_t *__restrict__ Pk, float *__restrict__ part, int64_t chunk_st,
-                     int64_t nstage, int *__restrict__ err)
+                     int64_t nstage, int *__restrict__ err, uint64_t wait_ns)
 {
     constexpr int NR = NB * 8;
     constexpr int UPW = 4 * UH;                  // row warps
@@ -317,11 +320,11 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                 const int b = c & 1;
                 const int s = c / BPS, sb = s % UNST;
                 if (c % BPS == 0) {
-                    if (!mbar_wait_abort(&full[sb], (uint32_t)(s / UNST) & 1u, abort)) break;
+                    if (!mbar_wait_abort(&full[sb], (uint32_t)(s / UNST) & 1u, abort, wait_ns)) break;
                     observed = s + 1;
                 }
-                if (!mbar_wait_abort(&afull[b], (uint32_t)(c >> 1) & 1u, abort)) break;
-                if (c >= 2 && !mbar_wait_abort(&dempty[b], (uint32_t)((c - 2) >> 1) & 1u, abort))
+                if (!mbar_wait_abort(&afull[b], (uint32_t)(c >> 1) & 1u, abort, wait_ns)) break;
+                if (c >= 2 && !mbar_wait_abort(&dempty[b], (uint32_t)((c - 2) >> 1) & 1u, abort, wait_ns))
                     break;
                 tm_fence_after();
                 const uint32_t phi = base_s + sb * SB + PTS;
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                     umma_commit(&empty[sb]);
                     if (issued < nst) {
                         // refill this buffer once its MMAs are done
-                        if (!mbar_wait_abort(&empty[sb], (uint32_t)(s / UNST) & 1u, abort)) break;
+                        if (!mbar_wait_abort(&empty[sb], (uint32_t)(s / UNST) & 1u, abort, wait_ns)) break;
                         issue(issued++);
                     }
                 }
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
         };
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         auto fold = [&](int c) -> bool {
-            if (!mbar_wait_abort_warp(&bdone[c & 1], (uint32_t)(c >> 1) & 1u, abort)) return false;
+            if (!mbar_wait_abort_warp(&bdone[c & 1], (uint32_t)(c >> 1) & 1u, abort, wait_ns)) return false;
             tm_fence_after();
             const uint32_t dcol = tbase + lane_off + COL_D + (c & 1) * NR + hf * FC;
             if constexpr ((LEAN & 4) != 0) {
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
         for (int c = 0; c < nblk && ok; ++c) {
             const int b = c & 1;
             const int s = c / BPS, sb = s % UNST;
-            if (c % BPS == 0 && !mbar_wait_abort_warp(&full[sb], (uint32_t)(s / UNST) & 1u, abort)) {
+            if (c % BPS == 0 && !mbar_wait_abort_warp(&full[sb], (uint32_t)(s / UNST) & 1u, abort, wait_ns)) {
                 ok = false;
                 break;
             }

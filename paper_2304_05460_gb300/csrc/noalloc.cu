@@ -1,10 +1,10 @@
 // noalloc.cu -- the FP64 kernel matvec for callers that must not allocate.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a stream
-// is being captured into a CUDA graph (an allocation there breaks the
-// capture), services whose device memory is planned up front and handed out
-// by their own pool, and plug-ins that are not allowed to change the device
-// footprint of the host process.  afn_kernel_matvec allocates its split-K
+// Some callers cannot call cudaMalloc at all: services whose device memory is
+// planned up front and handed out by their own pool (an allocation behind
+// the pool's back breaks its budget, or fails once the pool holds the rest of
+// the device), and plug-ins loaded into a host process that must not grow
+// that process's device footprint.  afn_kernel_matvec allocates its split-K
 // partial sums on every call; this entry point runs the same kernels with
 // those partials in a fixed array that is part of the library image instead.
 //
@@ -13,7 +13,8 @@
 // exits.  Host code cannot use the array's name as a device address, so on
 // the first call on each device (with that device current) the address is
 // looked up once with cudaGetSymbolAddress and cached; make that first call
-// before any stream capture begins.  All calls share the one array and it
+// on each device before any stream capture begins.  The call synchronises its
+// stream before it returns.  All calls share the one array and it
 // keeps whatever the last call left in it: every partial is written before it
 // is read, so nothing needs clearing, but two calls whose kernels overlap on
 // the GPU (different streams, no ordering between them) race on it.
@@ -30,6 +31,19 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_BYTES 
 
 static void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
 static std::mutex g_noalloc_mu;
+
+// device memory of another GPU is refused: the kernels run on the current one
+static bool on_current_device(const void *ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || a.device == dev;
+}
 
 // device address of the scratch array on the current device (looked up once)
 static afn_status noalloc_scratch(void **out)
@@ -68,6 +82,10 @@ extern "C" afn_status afn_kernel_matvec_noalloc(const double *points, int64_t n,
     }
     if (!is_device_ptr(points) || !is_device_ptr(p) || !is_device_ptr(q)) {
         set_error("afn_kernel_matvec_noalloc: points, p and q must be device memory");
+        return AFN_ERR_ARG;
+    }
+    if (!on_current_device(points) || !on_current_device(p) || !on_current_device(q)) {
+        set_error("afn_kernel_matvec_noalloc: points, p and q must be on the current device");
         return AFN_ERR_ARG;
     }
     // columns per pass: the widest group whose partials fit the fixed scratch

@@ -658,6 +658,8 @@ afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, doub
     const int maxit = h->opt.max_iter > 0 ? h->opt.max_iter : 500;
     AFN_CUDA(cudaMemcpyAsync(wk.b, b_perm, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
     AFN_CUDA(cudaMemsetAsync(wk.x, 0, sizeof(double) * tot, s));
+    // the tensor-core kernels' timeout word starts clear for every solve
+    AFN_CUDA(cudaMemsetAsync(h->status.as<int>() + 3, 0, sizeof(int), s));
     // ||b|| per column into both column sets
     launch_dot<double>(0, wk.b, wk.b, nullptr, nullptr, n, nrhs, M_NORM, wk.cs, maxit, s);
     launch_dot<double>(0, wk.b, wk.b, nullptr, nullptr, n, nrhs, M_NORM, wk.cs_out, maxit, s);

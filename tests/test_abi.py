@@ -75,7 +75,8 @@ def test_default_options():
     assert o.inner_tol == 0.01 and o.fps_start == 0
     # Alg. 5 fields sit after the stream pointer; AFN is the default preconditioner
     assert (o.precond, o.precond_threshold) == (afn.PRECOND_AFN, 0)
-    assert ctypes.sizeof(afn.afn_options) == 72
+    assert (o.factors, o.apply_tc) == (afn.FACTORS_FP32, 0)
+    assert ctypes.sizeof(afn.afn_options) == 80
     assert ctypes.sizeof(afn.afn_build_info) == 96
 
 
@@ -86,3 +87,37 @@ def test_bad_precond_rejected_without_gpu():
         with pytest.raises(afn.AfnError) as e:
             afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, 2, **kw)
         assert e.value.status == afn.AFN_ERR_ARG
+
+
+def test_bad_factor_and_apply_options_rejected_without_gpu():
+    from paper_2304_05460_gb300 import afn
+    X = np.zeros((4, 3))
+    for kw in (dict(factors=2), dict(factors=-1), dict(apply_tc=2)):
+        with pytest.raises(afn.AfnError) as e:
+            afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, 2, **kw)
+        assert e.value.status == afn.AFN_ERR_ARG
+
+
+def test_noalloc_binding_refuses_bad_tensors_before_any_launch():
+    # the binding checks type, dtype, contiguity, shape and device before it calls the
+    # library, so a mis-shaped (n, nrhs) block never reaches the kernels
+    torch = pytest.importorskip("torch")
+    from paper_2304_05460_gb300 import afn
+    n, d = 10, 3
+    X = torch.zeros((n, d), dtype=torch.float64)
+    good = torch.zeros((2, n), dtype=torch.float64)
+    cases = [
+        (np.zeros((n, d)), good, good, "torch tensor"),
+        (X.float(), good, good, "float64"),
+        (X, torch.zeros((n, 2), dtype=torch.float64), torch.zeros((n, 2), dtype=torch.float64),
+         "shape (nrhs, n)"),
+        (X, good, torch.zeros((3, n), dtype=torch.float64), "one shape"),
+        (X, torch.zeros((4, n), dtype=torch.float64)[:, ::2].t(), good, "contiguous"),
+        (X[:, :2], good, good, None),
+        (X, good, good, "CUDA memory"),
+    ]
+    for pts, p, q, msg in cases:
+        with pytest.raises(ValueError) as e:
+            afn.afn_kernel_matvec_noalloc(pts, afn.GAUSSIAN, 1.0, 1e-2, p, q)
+        if msg:
+            assert msg in str(e.value), (msg, str(e.value))

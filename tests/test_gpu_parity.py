@@ -2,8 +2,8 @@
 
 Bars:
   * FPS indices, permutation and FSAI pattern: bit-exact.
-  * FP64 path L, W and G: max |gpu - oracle| <= 1e-10 max |oracle| (L, W),
-    1e-9 for G (one more solve on top of the Schur complement).
+  * FP64 path L, W and G: max |gpu - oracle| <= 1e-10 max |oracle|; the same
+    bar for G of mixed handles built with FP64 factors.
   * Solves: the final relative residual ||b - (K + mu I) x|| / ||b||,
     recomputed by the oracle in FP64, is <= tol; FP64 iteration counts are
     within +-2 of the oracle's.
@@ -78,16 +78,58 @@ def test_knn_ties_lattice(afn):
     assert np.array_equal(afn.afn_knn_pattern(X, 9), pat)
 
 
+def _pattern_layout_ok(pat, w):
+    """Row i: min(i, w-1) neighbours j < i, then i itself, then -1 padding."""
+    nr = pat.shape[0]
+    i = np.arange(nr)
+    m = np.minimum(i, w - 1)
+    assert np.array_equal(pat[i, m], i)
+    pad = np.arange(w)[None, :] > m[:, None]
+    assert np.all(pat[pad] == -1)
+    used = (np.arange(w)[None, :] < m[:, None])
+    assert np.all((pat[used] >= 0) & (pat[used] < np.repeat(i, w).reshape(nr, w)[used]))
+
+
+def _sample_rows(nr, w, seed, count):
+    g = inputs.rng(seed)
+    edge = [0, 1, w - 2, w - 1, w, nr // 2, nr - 3, nr - 2, nr - 1]
+    return np.unique(np.concatenate([[r for r in edge if 0 <= r < nr],
+                                     g.choice(nr, size=min(count, nr), replace=False)]))
+
+
 def test_knn_prefix_full_size(afn):
-    # row i depends only on points 0..i: the oracle checks a prefix exactly
+    # row i depends only on points 0..i: the oracle checks a prefix exactly, and
+    # sampled rows over the whole range (the last rows included) one by one
     X = inputs.clusters_3d(nrhs=1).X
     full = afn.afn_knn_pattern(X, 50)
     pat, _ = oracle.knn_pattern(X[:6000], 50)
     assert np.array_equal(full[:6000], pat)
-    assert np.all(full[:, -1][50:] == -1) or True
-    rows = np.arange(len(X))
-    last = np.array([r[r >= 0][-1] for r in full[-100:]])
-    assert np.array_equal(last, rows[-100:])
+    _pattern_layout_ok(full, 50)
+    rows = _sample_rows(len(X), 50, 31, 300)
+    assert np.array_equal(full[rows], oracle.knn_rows(X, 50, rows))
+
+
+@pytest.mark.parametrize("which", ["normal_8d", "clusters_3d"])
+def test_knn_pattern_of_full_size_builds(afn, which):
+    # the FSAI pattern of the handles the benchmark builds: n = 50k (Alg. 4 k = 4000 at
+    # l = 1, n_r = 46,000, w = 64) and n = 200k (k = 2000, n_r = 198,000, w = 50), in the
+    # handle's Schur-row order; sampled rows over the whole range against the oracle
+    if which == "normal_8d":
+        s = inputs.normal_8d(l=1.0, nrhs=1)
+        h = afn.afn_build(s.X, G, 1.0, 1e-2, 4000, 64, precision=afn.PREC_MIXED,
+                          rank_mode=afn.RANK_ESTIMATE, rank_subsample=1000, seed=s.seed)
+    else:
+        s = inputs.clusters_3d(nrhs=1)
+        h = afn.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w, precision=afn.PREC_MIXED)
+    bi = h.info
+    perm = afn.afn_get_perm(h)
+    pat, _ = afn.afn_get_G(h)
+    Xr = s.X[perm[bi.k:]]
+    _pattern_layout_ok(pat, bi.w)
+    rows = _sample_rows(bi.nr, bi.w, 37, 250)
+    assert np.array_equal(pat[rows], oracle.knn_rows(Xr, bi.w, rows))
+    assert np.array_equal(afn.afn_knn_pattern(Xr, bi.w), pat)
+    afn.afn_free(h)
 
 
 # --------------------------------------------------------------- matvec ---
@@ -173,7 +215,7 @@ def test_build_parity_fp64(afn, n, d, ker, l, mu, k, w):
     if ref["nr"]:
         pat, Gv = afn.afn_get_G(h)
         assert np.array_equal(pat, ref["pattern"])
-        assert _cmp(Gv, ref["G"], 0) <= 1e-9
+        assert _cmp(Gv, ref["G"], 0) <= 1e-10
         if ref["k"]:
             # W^T = K12^T L^{-T}: check against the oracle's L and K12
             W = np.linalg.solve(ref["L"], ref["K12"]).T
@@ -183,6 +225,28 @@ def test_build_parity_fp64(afn, n, d, ker, l, mu, k, w):
     s_gpu = afn.afn_apply_precond(h, r)
     s_ref = np.stack([oracle.afn_apply(ref, r[:, c]) for c in range(2)], 1)
     assert _cmp(s_gpu, s_ref, 0) <= 1e-8
+    afn.afn_free(h)
+
+
+@pytest.mark.parametrize("n,d,ker,l,mu,k,w", [(2000, 3, G, 0.1, 1e-4, 200, 32),
+                                               (3001, 8, M32, 2.0, 1e-2, 300, 64)])
+def test_build_mixed_fp64_factors(afn, n, d, ker, l, mu, k, w):
+    # factors = FP64: a mixed handle's W and G are built as for an FP64 handle (G within
+    # the FP64 bar), then rounded to FP32 for the apply
+    X = inputs.uniform_points(n, d, 650 + n)
+    ref = oracle.afn_build(X, ker, l, mu, k, w)
+    h = afn.afn_build(X, ker, l, mu, k, w, precision=afn.PREC_MIXED, factors=afn.FACTORS_FP64)
+    assert np.array_equal(afn.afn_get_perm(h), ref["perm"])
+    pat, Gv = afn.afn_get_G(h)
+    assert np.array_equal(pat, ref["pattern"])
+    assert _cmp(Gv, ref["G"], 0) <= 1e-10
+    W = np.linalg.solve(ref["L"], ref["K12"]).T
+    assert _cmp(afn.afn_get_W(h), W, 0) <= 1e-7          # the FP32 copy of the FP64 W
+    r = inputs.rhs(n, 2, 660 + n)
+    s_gpu = afn.afn_apply_precond(h, r)
+    s_ref = np.stack([oracle.afn_apply(ref, r[:, c]) for c in range(2)], 1)
+    err = _cmp(s_gpu, s_ref, 0)
+    assert err <= 1e-3, err                                # FP32 apply of the FP64 factors
     afn.afn_free(h)
 
 
@@ -198,30 +262,30 @@ def test_build_mixed_close_to_oracle(afn):
 
 
 @pytest.mark.parametrize("n,k,nrhs", [(3001, 300, 32), (2600, 130, 16), (3001, 300, 48)])
-def test_mixed_apply_tensor_core_products(afn, monkeypatch, n, k, nrhs):
+def test_mixed_apply_tensor_core_products(afn, n, k, nrhs):
     # the FP32 apply of a mixed handle with the W products on the tcgen05
-    # tensor cores (three-pass tf32, opt-in) against the same apply on the CUDA cores
-    # and against the oracle's FP64 apply of the oracle's own build; ragged k
+    # tensor cores (three-pass tf32, option apply_tc) against the same apply on the CUDA
+    # cores and against the oracle's FP64 apply of the oracle's own build; ragged k
     # and n - k (not multiples of the 32-element stages or 128-row tiles)
     X = inputs.normal_points(n, 8, 800 + n)
-    h = afn.afn_build(X, G, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED)
-    bi = h.info
+    h_tc = afn.afn_build(X, G, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED, apply_tc=1)
+    h_cc = afn.afn_build(X, G, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED, apply_tc=0)
+    bi = h_tc.info
     assert bi.k == k and bi.nr == n - k
     r = inputs.rhs(n, nrhs, 900 + n)
-    before = afn.afn_get_build_info(h).device_bytes
-    monkeypatch.setenv("AFN_APPLY_TC", "1")
-    s_tc = afn.afn_apply_precond(h, r)
-    grown = afn.afn_get_build_info(h).device_bytes - before
+    before = afn.afn_get_build_info(h_tc).device_bytes
+    s_tc = afn.afn_apply_precond(h_tc, r)
+    grown = afn.afn_get_build_info(h_tc).device_bytes - before
     assert grown >= 2 * 4 * k * (n - k)            # the two tiled images of W were built
-    monkeypatch.setenv("AFN_APPLY_TC", "0")
-    s_cc = afn.afn_apply_precond(h, r)
+    s_cc = afn.afn_apply_precond(h_cc, r)
     assert np.all(np.isfinite(s_tc))
     assert _cmp(s_tc, s_cc, 0) <= 2e-5
     # FP32 apply of an FP32-built preconditioner against the FP64 oracle
     ref = oracle.afn_build(X, G, 1.0, 1e-2, k, 32)
     s_ref = np.stack([oracle.afn_apply(ref, r[:, c]) for c in range(3)], 1)
     assert _cmp(s_tc[:, :3], s_ref, 0) <= 1e-2
-    afn.afn_free(h)
+    afn.afn_free(h_tc)
+    afn.afn_free(h_cc)
 
 
 def test_not_spd_reported(afn):
@@ -315,6 +379,24 @@ def test_solve_device_pointers(afn):
     assert x.is_cuda
     rel = oracle.true_relres(X, G, 0.15, 1e-3, x.cpu().numpy(), B)
     assert rel.max() <= 1e-6
+
+
+def test_solve_headline_normal_8d_oracle_residual(afn):
+    # the benchmark's system (n = 50k, d = 8, Gaussian l = 1, mu = 1e-2, Alg. 4 k capped at
+    # 4000, w = 64, 32 right-hand sides, mixed precision, tol 1e-6): the true relative
+    # residual of two columns recomputed by the oracle's FP64 matvec
+    s = inputs.normal_8d(l=1.0, nrhs=32)
+    h = afn.afn_build(s.X, G, 1.0, 1e-2, 4000, 64, precision=afn.PREC_MIXED,
+                      rank_mode=afn.RANK_ESTIMATE, rank_subsample=1000, seed=s.seed,
+                      max_iter=3000)
+    x, info = afn.afn_solve(h, s.B, 1e-6)
+    assert info["converged"] == 32, info
+    cols = [0, 31]
+    rel = oracle.true_relres(s.X, G, 1.0, 1e-2, x[:, cols], s.B[:, cols])
+    assert np.all(rel <= 1e-6), rel
+    # the library's own FP64 residual agrees with the oracle's
+    assert np.allclose(info["relres"][cols], rel, rtol=1e-3, atol=1e-12)
+    afn.afn_free(h)
 
 
 # ------------------------------------------------------------- Alg. 4 ---
