@@ -213,17 +213,53 @@ def job_throughput(solves_per_rank, world, job_ms):
     return solves_per_rank * world / (job_ms / 1e3)
 
 
+def deal(costs, world):
+    """Independent systems dealt to ranks (replicas, no communication): the
+    most expensive first, each to the rank with the least work so far (ties
+    to the lower rank).  Returns one ascending index list per rank."""
+    load = [0.0] * world
+    share = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda j: (-costs[j], j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        share[r].append(i)
+        load[r] += costs[i]
+    return [sorted(x) for x in share]
+
+
+def job_sum(value, dist, device):
+    """Sum of a per-rank count over the ranks."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_gather(values, dist):
+    """Every rank's list of values, concatenated in rank order."""
+    if not dist:
+        return list(values)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, list(values))
+    return [v for p in parts for v in p]
+
+
 # ---------------------------------------------------------------- batched --
-def run_batched(afn, count, fp64_sample, stream):
+def run_batched(afn, count, fp64_sample, stream, rank=0, world=1, dist=None):
     """The batched workload: `count` systems (n log-uniform in [256, 8192],
     d in 2..16, N(0,I) points, Gaussian, l = median distance x log-uniform
     [0.1, 10], mu log-uniform [1e-4, 1e-1], k = min(n/4, 1000), w = 32, 8 RHS
     each), built and solved together (mixed precision, grouped kernels under
     CUDA graphs), against the plain FP64 GPU path run one system at a time on
-    a seeded sample of the systems."""
+    a seeded sample of the systems.  With several ranks the systems are dealt
+    to them (``deal``, cost n^2) and each rank solves its share; the job's
+    time is the slowest rank's."""
     import torch
     from paper_2304_05460_gb300 import inputs
     systems = inputs.batched_512(count=count)
+    if world > 1:
+        systems = [systems[i] for i in deal([float(x.n) ** 2 for x in systems], world)[rank]]
     args_ = [dict(points=torch.tensor(s.X, device="cuda"), kernel=s.kernel, l=s.l, mu=s.mu,
                   k_max=s.k, fsai_nnz=s.w) for s in systems]
     rhs = [torch.tensor(np.ascontiguousarray(s.B), device="cuda") for s in systems]
@@ -243,23 +279,32 @@ def run_batched(afn, count, fp64_sample, stream):
         return t1 - t0, t2 - t1, info
 
     once()                                   # warm-up (graph capture, pool growth)
+    if dist:
+        dist.barrier()
     bt, st, info = once()
+    if dist:
+        bt, st = job_time_ms(bt, dist, "cuda"), job_time_ms(st, dist, "cuda")
     # kernel-pair evaluations of the FP32 matvec: per system and column group,
     # n^2 pairs for every iteration in which one of its columns was active
     pairs = 0.0
     for s, its in zip(systems, info["iters"]):
         for g in range(0, len(its), 8):
             pairs += float(s.n) ** 2 * int(its[g:g + 8].max())
+    conv = info["converged"]
+    if dist:
+        cols = int(job_sum(cols, dist, "cuda"))
+        conv = int(job_sum(conv, dist, "cuda"))
+        pairs = job_sum(pairs, dist, "cuda")
     out = {"workload": "batched_512: %d systems, n log-uniform [256, 8192], d in 2..16, N(0,I), "
                        "Gaussian, l = median dist x logU[0.1, 10], mu logU[1e-4, 1e-1], "
                        "k = min(n/4, 1000), w = 32, 8 RHS, tol 1e-6" % count,
-           "systems": count, "columns": cols, "converged_columns": info["converged"],
+           "systems": count, "ranks": world, "columns": cols, "converged_columns": conv,
            "build_ms": bt * 1e3, "solve_ms": st * 1e3,
            "solves_per_s": cols / (bt + st), "solve_only_solves_per_s": cols / st,
            "iters_max": info["iters_max"], "graph_launches": info["graph_launches"],
            "group_ms": info["group_ms"], "df_systems": info["single_systems"],
            "df_ms": info["single_ms"], "matvec_pairs_per_s": pairs / st}
-    if fp64_sample > 0:
+    if fp64_sample > 0 and world == 1:
         g = np.random.Generator(np.random.PCG64(7))
         pick = sorted(g.choice(count, size=min(fp64_sample, count), replace=False).tolist())
         o64 = afn.options(precision=afn.PREC_FP64, seed=1004, max_iter=MAXIT, stream=stream)
@@ -287,18 +332,23 @@ def run_batched(afn, count, fp64_sample, stream):
 
 
 # ---------------------------------------------------------------- serving --
-def run_serving(afn, count, rate, fp64_sample):
+def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None):
     """The serving workload: `count` requests of the Poisson stream (n
     log-uniform in [1e3, 1e5], d in {3, 8, 16}, N(0,I) points, Gaussian or
     Matern-3/2 50/50, l and mu drawn as in the batched workload, k =
     min(n/4, 1000), w = 32, 1..16 RHS, tol 1e-6) replayed against the serving
     loop; latency is submit -> result.  rate 0 submits every request at once
     (saturation throughput).  The plain FP64 GPU path, one request at a time,
-    is timed on a seeded sample and scaled by sum(n^2)."""
+    is timed on a seeded sample and scaled by sum(n^2).  With several ranks
+    the requests are dealt to them (``deal``, cost n^2), each rank serves its
+    share at the share's own arrival times, and the job's makespan is the
+    slowest rank's."""
     import threading
     import torch
     from paper_2304_05460_gb300 import inputs
     reqs = inputs.serving_stream(count=count, rate=rate if rate > 0 else 1.0)
+    if world > 1:
+        reqs = [reqs[i] for i in deal([float(r["n"]) ** 2 for r in reqs], world)[rank]]
     systems = [inputs.serving_system(r) for r in reqs]
     args_ = [dict(points=s.X, kernel=s.kernel, l=s.l, mu=s.mu, k_max=s.k, fsai_nnz=s.w)
              for s in systems]
@@ -310,6 +360,8 @@ def run_serving(afn, count, rate, fp64_sample):
         pass
     srv.result(wid)
     ids = {}
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
 
     def feeder():
@@ -323,7 +375,7 @@ def run_serving(afn, count, rate, fp64_sample):
     th = threading.Thread(target=feeder)
     th.start()
     lat, conv, done = [], 0, 0
-    while done < count:
+    while done < len(reqs):
         for rid in srv.poll(wait_ms=50):
             x, info = srv.result(rid)
             lat.append(info["latency_ms"])
@@ -333,6 +385,11 @@ def run_serving(afn, count, rate, fp64_sample):
     th.join()
     st = srv.stats()
     srv.close()
+    if dist:
+        span = job_time_ms(span * 1e3, dist, "cuda") / 1e3
+        cols = int(job_sum(cols, dist, "cuda"))
+        conv = int(job_sum(conv, dist, "cuda"))
+        lat = job_gather(lat, dist)
     lat = np.sort(np.array(lat))
     out = {"workload": "serving_stream: %d requests, n log-uniform [1e3, 1e5], d in {3,8,16}, "
                        "N(0,I), Gaussian/Matern-3/2 50/50, l = median dist x logU[0.1, 10], "
@@ -340,13 +397,14 @@ def run_serving(afn, count, rate, fp64_sample):
                        "at most %d iterations; arrivals: %s"
                        % (count, SERVE_MAXIT, "Poisson %.3g/s" % rate if rate > 0 else
                           "all at t = 0 (saturation)"),
-           "requests": count, "columns": cols, "converged_columns": conv, "makespan_s": span,
+           "requests": count, "ranks": world, "columns": cols, "converged_columns": conv,
+           "makespan_s": span,
            "requests_per_s": count / span, "solves_per_s": cols / span,
            "latency_p50_ms": float(np.percentile(lat, 50)),
            "latency_p99_ms": float(np.percentile(lat, 99)),
            "peak_live": st["peak_live"], "graph_launches": st["graph_launches"],
            "peak_reserved_gb": st["peak_reserved_bytes"] / 2**30}
-    if fp64_sample > 0:
+    if fp64_sample > 0 and world == 1:
         # the FP64 path takes minutes on the largest requests: sample among
         # those with n <= 20,000 and scale by sum(n^2)
         g = np.random.Generator(np.random.PCG64(11))
@@ -610,16 +668,18 @@ def main():
                 "converged": int(info["converged"])}
         afn.afn_free(h)
 
+    # batched and serving: every rank solves the systems dealt to it (replicas)
     batched = None
-    if rank == 0 and args.batched > 0:
+    if args.batched > 0:
         try:
-            batched = run_batched(afn, args.batched, args.fp64_sample, stream)
+            batched = run_batched(afn, args.batched, args.fp64_sample, stream, rank, world, dist)
         except Exception as e:          # reported in the line, the headline stands
             batched = {"error": repr(e)}
     serving = None
-    if rank == 0 and args.serving > 0:
+    if args.serving > 0:
         try:
-            serving = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4))
+            serving = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4),
+                                  rank, world, dist)
         except Exception as e:
             serving = {"error": repr(e)}
 
