@@ -105,6 +105,11 @@ typedef struct {
                                   the tcgen05 tensor cores (three-pass tf32, FP32 accumulation)
                                   for every 16- or 32-column piece: 0 = CUDA-core tiles,
                                   1 = tensor cores; default 0 */
+    int32_t flexible;          /* mixed handles: 1 = flexible PCG, beta in the Polak-Ribiere
+                                  form r_{k+1}^T (z_{k+1} - z_k) / r_k^T z_k (Notay 2000), which
+                                  tolerates the FP32 apply being inexact; 0 = the textbook
+                                  Fletcher-Reeves beta; default 0 */
+    int32_t pad_;
 } afn_options;
 
 typedef enum {

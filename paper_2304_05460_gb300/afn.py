@@ -42,7 +42,8 @@ class afn_options(C.Structure):
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("inner_tol", C.c_double),
                 ("check_every", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
                 ("precond", C.c_int32), ("precond_threshold", C.c_int32),
-                ("factors", C.c_int32), ("apply_tc", C.c_int32)]
+                ("factors", C.c_int32), ("apply_tc", C.c_int32), ("flexible", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 class afn_build_info(C.Structure):

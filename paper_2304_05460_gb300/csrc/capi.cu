@@ -557,6 +557,10 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         set_error("bad factors %d", o.factors);
         return AFN_ERR_ARG;
     }
+    if (o.flexible != 0 && o.flexible != 1) {
+        set_error("bad flexible %d", o.flexible);
+        return AFN_ERR_ARG;
+    }
     if (o.apply_tc != 0 && o.apply_tc != 1) {
         set_error("bad apply_tc %d", o.apply_tc);
         return AFN_ERR_ARG;
@@ -688,6 +692,8 @@ void afn_default_options(afn_options *o)
     o->precond_threshold = 0;
     o->factors = AFN_FACTORS_FP32;
     o->apply_tc = 0;
+    o->flexible = 0;
+    o->pad_ = 0;
 }
 
 const char *afn_last_error(void) { return g_err; }

@@ -183,17 +183,14 @@ __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N)
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort,
                                                 uint64_t limit_ns)
 {
-    uint64_t t0 = 0;
-    for (uint32_t spin = 0;; ++spin) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((spin & 63u) == 0) {
-            if (*abort) return false;
-            const uint64_t t = globaltimer_ns();
-            if (spin == 0) t0 = t;
-            else if (t - t0 > limit_ns) {
-                *abort = 1;
-                return false;
-            }
+        if (*abort) return false;
+        if (globaltimer_ns() - t0 > limit_ns) {
+            *abort = 1;
+            return false;
         }
     }
 }

@@ -32,11 +32,12 @@ namespace afn {
 static constexpr int DB = 256;        // threads per dot block
 static constexpr int DMAXB = 512;     // max blocks per column
 
-enum DotMode { M_STORE = 0, M_ALPHA, M_RR, M_BETA, M_RHO0, M_NORM, M_RRU };
+enum DotMode { M_STORE = 0, M_ALPHA, M_RR, M_BETA, M_RHO0, M_NORM, M_RRU, M_SIGMA, M_BETA_PR };
 
 struct Cols {                 // device arrays, one entry per column
     double *rho, *alpha, *beta, *val, *bnorm, *tolabs, *part;
     double *rmax2;            // largest ||r||^2 since the last residual replacement
+    double *sigma;            // flexible PCG: r_{k+1}^T z_k
     int *active, *iters, *conv, *base;   // base: iters at the start of this inner solve
     int *flag;                // residual replacement requested
     unsigned int *cnt;
@@ -135,6 +136,18 @@ __global__ void __launch_bounds__(DB) dot_kernel(T *a, const T *b, T *x, const T
             cs.beta[c] = 0.0;
         }
         break;
+    case M_BETA_PR:
+        // flexible PCG (Polak-Ribiere form): beta = r_{k+1}^T (z_{k+1} - z_k) / rho_k
+        if (act) {
+            cs.beta[c] = (v - cs.sigma[c]) / cs.rho[c];
+            cs.rho[c] = v;
+        } else {
+            cs.beta[c] = 0.0;
+        }
+        break;
+    case M_SIGMA:
+        if (act) cs.sigma[c] = v;
+        break;
     case M_RHO0:
         if (act) cs.rho[c] = v;
         break;
@@ -205,7 +218,7 @@ template <class T> static T *carve(char *&p, size_t count)
 
 static size_t cols_bytes(int nrhs)
 {
-    return (size_t)nrhs * (8 * 8 + 4 * 5 + 4) + (size_t)nrhs * DMAXB * 8 + 8 * 256 + 12288;
+    return (size_t)nrhs * (9 * 8 + 4 * 5 + 4) + (size_t)nrhs * DMAXB * 8 + 8 * 256 + 12288 + 256;
 }
 
 static void carve_cols(char *&p, int nrhs, Cols &cs)
@@ -226,6 +239,7 @@ static void carve_cols(char *&p, int nrhs, Cols &cs)
     cs.rmax2 = carve<double>(p, nrhs);
     cs.flag = carve<int>(p, nrhs);
     cs.nflag = carve<int>(p, 1);
+    cs.sigma = carve<double>(p, nrhs);
 }
 
 static afn_status get_work(Handle *h, int nrhs, Work &wk)
@@ -586,6 +600,7 @@ static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int 
     cudaStream_t s = h->stream;
     const int64_t n = h->n, tot = n * nrhs;
     const double delta = h->opt.inner_tol > 0 ? h->opt.inner_tol : 0.05;
+    const bool flexible = h->opt.flexible == 1;
     const Cols &cs = wk.cs;
     ru_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(cs, nrhs, delta);
     AFN_CUDA(cudaMemsetAsync(wk.x, 0, sizeof(double) * tot, s));
@@ -634,10 +649,15 @@ static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int 
                 if (na == 0) break;
             }
         }
+        if (flexible) {
+            Scope sc(&h->prof, K_BLAS1);
+            launch_dot<float>(0, wk.r32, wk.z32, nullptr, nullptr, n, nrhs, M_SIGMA, cs, maxit, s);
+        }
         AFN_TRY(apply32(h, wk.r32, nrhs, wk.z32, wk.tmp));
         {
             Scope sc(&h->prof, K_BLAS1);
-            launch_dot<float>(0, wk.r32, wk.z32, nullptr, nullptr, n, nrhs, M_BETA, cs, maxit, s);
+            launch_dot<float>(0, wk.r32, wk.z32, nullptr, nullptr, n, nrhs,
+                              flexible ? M_BETA_PR : M_BETA, cs, maxit, s);
             launch_pupdate<float>(wk.p32, wk.z32, n, nrhs, cs, 0, s);
         }
     }

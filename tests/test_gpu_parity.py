@@ -359,6 +359,23 @@ def test_solve_fp64_and_mixed_multi_rhs(afn, ker, nrhs):
         afn.afn_free(h)
 
 
+def test_solve_mixed_flexible_pcg(afn):
+    # flexible PCG (Polak-Ribiere beta) on a mixed handle reaches tol as recomputed by the
+    # oracle, with iteration counts close to the textbook form's
+    X = inputs.uniform_points(2500, 3, 820)
+    B = inputs.rhs(2500, 16, 821)
+    its = {}
+    for flex in (0, 1):
+        h = afn.afn_build(X, G, 0.1, 1e-3, 250, 32, precision=afn.PREC_MIXED, flexible=flex)
+        x, info = afn.afn_solve(h, B, 1e-6)
+        assert info["converged"] == 16
+        rel = oracle.true_relres(X, G, 0.1, 1e-3, x[:, :3], B[:, :3])
+        assert np.all(rel <= 1e-6), rel
+        its[flex] = int(info["iters"].max())
+        afn.afn_free(h)
+    assert abs(its[1] - its[0]) <= max(4, its[0] // 10), its
+
+
 def test_solve_k_equals_n_one_iteration(afn):
     X = inputs.uniform_points(150, 2, 900)
     b = inputs.rhs(150, 1, 901)
