@@ -101,10 +101,12 @@ typedef struct {
     int32_t precond_threshold; /* Alg. 5's rank threshold; 0 = 2000 */
     int32_t factors;           /* mixed handles: arithmetic of the factor build (afn_factors),
                                   default AFN_FACTORS_FP32 */
-    int32_t apply_tc;          /* mixed handles: the two W products of the apply (Alg. 3) on
-                                  the tcgen05 tensor cores (three-pass tf32, FP32 accumulation)
-                                  for every 16- or 32-column piece: 0 = CUDA-core tiles,
-                                  1 = tensor cores; default 0 */
+    int32_t apply_tc;          /* mixed handles: the two W products of the apply (Alg. 3) when
+                                  the column count is a multiple of 16: 0 = CUDA-core FP32
+                                  tiles; 1 = tcgen05 tensor cores, three-pass tf32 on the FP32
+                                  W with FP32 accumulation; 2 = tcgen05 tensor cores on a BF16
+                                  copy of W (half the bytes streamed), the vectors split into
+                                  three BF16 terms, FP32 accumulation; default 0 */
     int32_t flexible;          /* mixed handles: 1 = flexible PCG, beta in the Polak-Ribiere
                                   form r_{k+1}^T (z_{k+1} - z_k) / r_k^T z_k (Notay 2000), which
                                   tolerates the FP32 apply being inexact; 0 = the textbook
@@ -230,6 +232,33 @@ void afn_release_cached_memory(void);
  * nanoseconds makes the waits run out on a healthy GPU).  No paper
  * counterpart. */
 void afn_set_wait_limit_ns(int64_t ns);
+
+/* ---- the autotuner ------------------------------------------------------
+ * Launch parameters that change only how work is spread over the GPU, never
+ * a result (row warps per TMEM lane quarter of the tcgen05 matvec, CTAs per
+ * SM of the persistent grouped kernels, threads per CTA of the FSAI build),
+ * are picked by timing: the first call with a given shape times every
+ * candidate on its own operands and records the fastest under a key
+ * "<kernel>/<shape fields>/sm<cc>x<SMs>"; later calls reuse it.  Every
+ * candidate computes the same bits, so results never depend on the choice.
+ * No timing happens while the stream is being captured (the default is used
+ * and not recorded).  No paper counterpart. */
+/* Persist the cache in a text file ("key choice" per line): entries already
+ * in the file are loaded (and override those in memory), and the file is
+ * rewritten after every new decision.  NULL or "" stops persisting.
+ * Errors: AFN_ERR_ARG (unreadable or malformed file, unwritable path). */
+afn_status afn_tune_set_cache(const char *path);
+/* The recorded choice for key; AFN_ERR_ARG when there is none. */
+afn_status afn_tune_get(const char *key, int32_t *choice);
+/* Record a choice (key: printable, no spaces, at most 200 characters;
+ * choice >= 0); the library uses it from then on.  Errors: AFN_ERR_ARG. */
+afn_status afn_tune_put(const char *key, int32_t choice);
+/* Entries in the cache; the key of entry index (sorted order) copied into
+ * buf (len bytes, NUL-terminated) and its choice returned, -1 past the end. */
+int32_t afn_tune_count(void);
+int32_t afn_tune_key(int32_t index, char *buf, int32_t len);
+/* Forget every entry (and empty the persisted file, if any). */
+void afn_tune_clear(void);
 
 /* ---- operator-level entry points (each one step of the hot path) ------- */
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -32,6 +33,18 @@ afn_status cuda_fail(cudaError_t e, const char *what);
 // limit of the bounded device-side waits of the tcgen05 kernels, ns
 // (afn_set_wait_limit_ns; 2 s by default)
 uint64_t wait_limit_ns();
+
+// ---- tune.cu: the autotuner (launch parameters that never change a result)
+// "sm<major><minor>x<SMs>" of the current device, the last field of every key
+std::string tune_device_tag();
+int log2_bucket(int64_t v);
+bool tune_lookup(const std::string &key, int *choice);
+void tune_store(const std::string &key, int choice);
+// the cached choice for key, else (outside stream capture) time run(c) for c
+// in [0, ncand) on stream s, record and return the fastest; fallback when
+// timing is not possible
+int tune_pick(const std::string &key, int ncand, const std::function<void(int)> &run,
+              cudaStream_t s, int fallback);
 
 // device status word values (written by kernels, read by the host)
 enum : int { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_TIMEOUT = 2 };
@@ -113,6 +126,7 @@ struct Handle {
     DevBuf Wt;        // double [nr*k]  (FP64 handles)
     DevBuf Wt32;      // float  [nr*k]  (mixed handles)
     DevBuf Wu1, Wu2;  // float tiled images of W^T and W for the tcgen05 apply (built on first use)
+    DevBuf Wb1, Wb2;  // BF16 tiled images of W^T and W (apply_tc = 2, built on first use)
     // Nystrom preconditioner (precond == AFN_PRECOND_NYSTROM): L = chol(K11 + nu I),
     // B = K(X, X_S) L^{-T} (n x k row-major, permuted order), Lc = chol(mu I + B^T B)
     int precond = AFN_PRECOND_AFN;

@@ -14,6 +14,7 @@
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
+#include "gemm_bf16.cuh"
 #include "gemm_tile.cuh"
 #include "gemm_umma.cuh"
 #include "group.cuh"
@@ -372,20 +373,28 @@ static int colmul_js(int64_t nrows, int64_t ncols)
 
 static constexpr int GEMM_JS_MAX = 64;
 
-// words of the split vector block of the tcgen05 products (both products, 32 columns)
+// words of the split vector block of the tcgen05 products (both products):
+// tf32 hi/lo of 32 columns (64 words per K-element) or three BF16 terms of
+// 64 columns (96 words per K-element)
 static int64_t gu_bk_words(int64_t nr, int64_t k)
 {
-    return 2 * 32 * ((std::max(nr, k) + GKU - 1) / GKU * GKU);
+    return 96 * ((std::max(nr, k) + GKB - 1) / GKB * GKB);
+}
+
+// split-K partials of the products, elements: the CUDA-core tiles' chunks of
+// the k-row products, or one 64-column partial of the n_r-row product
+static size_t apply_pcap(int64_t nr, int64_t k)
+{
+    const size_t a = (size_t)std::max(colmul_js(nr, k), GEMM_JS_MAX) * 32 * (size_t)std::max<int64_t>(k, 1);
+    return std::max(a, (size_t)64 * (size_t)std::max(nr, k));
 }
 
 size_t apply_tmp_elems(const Handle *h, int nrhs)
 {
     int64_t k = h->k, nr = h->nr;
-    int js = std::max(colmul_js(nr, k), GEMM_JS_MAX);
     // zp, u (k x nrhs), t, y (nr x nrhs), GEMM partials, row-major copy (nr x nrhs), split
     // vector block of the tcgen05 products
-    return (size_t)(2 * k * nrhs + 3 * nr * nrhs) + (size_t)js * 32 * (size_t)std::max<int64_t>(k, 1) +
-           (size_t)gu_bk_words(nr, k) + 64;
+    return (size_t)(2 * k * nrhs + 3 * nr * nrhs) + apply_pcap(nr, k) + (size_t)gu_bk_words(nr, k) + 64;
 }
 
 // ------------------------------------------------ tcgen05 W products --------
@@ -430,19 +439,80 @@ __global__ void gu_bsplit_kernel(const float *__restrict__ X, int64_t ldx, int64
     Bk[w + GKU * NR] = lo;
 }
 
-// the handle's option apply_tc = 1 runs the W products on the tensor cores
-static bool use_apply_tc(const Handle *h) { return h->opt.apply_tc == 1; }
+// the handle's option apply_tc: 1 runs the W products on the tensor cores in
+// three-pass tf32, 2 with BF16 images of W
+static int apply_tc_mode(const Handle *h) { return h->opt.apply_tc; }
+
+// BF16 image (see gemm16u_kernel): A[row][kk] = Wt[row k + kk] (trans = 0,
+// M = nr, K = k) or Wt[kk k + row] (trans = 1, M = k, K = nr), zero outside
+__global__ void gb_arrange_kernel(const float *__restrict__ Wt, int64_t k, int trans, int64_t M,
+                                  int64_t K, int64_t nks, __nv_bfloat16 *__restrict__ Atl,
+                                  int64_t total)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t per = nks * (UR * GKB);
+    const int64_t rt = e / per, rem = e % per;
+    const int64_t st = rem / (UR * GKB);
+    const int wd = (int)(rem % (UR * GKB));
+    const int cm = wd / 64, within = wd % 64;
+    const int row = (cm / (GKB / 8)) * 8 + within / 8;
+    const int kk = (cm % (GKB / 8)) * 8 + within % 8;
+    const int64_t gi = rt * UR + row, gk = st * GKB + kk;
+    float v = 0.f;
+    if (gi < M && gk < K) v = trans ? Wt[gk * k + gi] : Wt[gi * k + gk];
+    Atl[e] = __float2bfloat16_rn(v);
+}
+
+// Bk: the K x NC block of X (column-major, leading dimension ldx) split into
+// NT BF16 terms, term t of column c at column t NC + c of the stage tile,
+// zero past K
+template <int NC, int NT>
+__global__ void gb_bsplit_kernel(const float *__restrict__ X, int64_t ldx, int64_t K, int64_t nks,
+                                 __nv_bfloat16 *__restrict__ Bk)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t kp = nks * GKB;
+    if (e >= kp * NC) return;
+    const int64_t kg = e % kp;
+    const int c = (int)(e / kp);
+    float x = kg < K ? X[c * ldx + kg] : 0.f;
+    const int64_t st = kg / GKB;
+    const int kk = (int)(kg % GKB);
+    __nv_bfloat16 *stage = Bk + st * (int64_t)(GKB * NC * NT);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(x);
+        stage[gb_tile_elem(t * NC + c, kk)] = b;
+        x -= __bfloat162float(b);
+    }
+}
 
 static int64_t gu_nks(int64_t K) { return (K + GKU - 1) / GKU; }
 static int64_t gu_tiles(int64_t M) { return (M + UR - 1) / UR; }
 
+static int64_t gb_nks(int64_t K) { return (K + GKB - 1) / GKB; }
+
 afn_status apply_tc_prepare(Handle *h, cudaStream_t s)
 {
-    if (h->wu_tried || !use_apply_tc(h)) return AFN_OK;
+    if (h->wu_tried || apply_tc_mode(h) == 0) return AFN_OK;
     h->wu_tried = true;
     const int64_t k = h->k, nr = h->nr;
     // small products stay on the CUDA-core tiles
     if (!h->Wt32.p || k < 128 || nr < 128) return AFN_OK;
+    if (apply_tc_mode(h) == 2) {
+        const int64_t n1 = gu_tiles(nr) * gb_nks(k) * (UR * GKB);
+        const int64_t n2 = gu_tiles(k) * gb_nks(nr) * (UR * GKB);
+        AFN_TRY(h->Wb1.alloc(sizeof(__nv_bfloat16) * (size_t)n1));
+        AFN_TRY(h->Wb2.alloc(sizeof(__nv_bfloat16) * (size_t)n2));
+        gb_arrange_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(
+            h->Wt32.as<float>(), k, 0, nr, k, gb_nks(k), h->Wb1.as<__nv_bfloat16>(), n1);
+        gb_arrange_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(
+            h->Wt32.as<float>(), k, 1, k, nr, gb_nks(nr), h->Wb2.as<__nv_bfloat16>(), n2);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "apply BF16 images");
+        return AFN_OK;
+    }
     const int64_t n1 = gu_tiles(nr) * gu_nks(k) * (UR * GKU);
     const int64_t n2 = gu_tiles(k) * gu_nks(nr) * (UR * GKU);
     AFN_TRY(h->Wu1.alloc(sizeof(float) * (size_t)n1));
@@ -458,11 +528,13 @@ afn_status apply_tc_prepare(Handle *h, cudaStream_t s)
 
 // j-chunks of a tcgen05 product: 1 CTA per SM; the count whose CTAs fill the
 // last wave best, chunks of at least 8 stages, partials within cap
-static void gu_chunking(int64_t M, int64_t nks, size_t cap_words, int nr, int &js, int64_t &cs)
+static void gu_chunking(int64_t M, int64_t nks, size_t cap_words, int nr, int &js, int64_t &cs,
+                        int per_sm = 1)
 {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms *= per_sm;
     const int64_t rt = gu_tiles(M);
     double best = -1.0;
     js = 1;
@@ -513,6 +585,48 @@ static afn_status prod_tc(const float *Atl, int64_t M, int64_t K, const float *X
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 apply product");
+    return AFN_OK;
+}
+
+// O = beta Y + alpha A X on the BF16 tensor cores for nrhs columns (a multiple of 16)
+template <int NC>
+static void launch_g16(const __nv_bfloat16 *Atl, int64_t M, int64_t nks, const float *X, int64_t ldx,
+                       int64_t K, float *part, size_t pcap, __nv_bfloat16 *Bk, int *err, int &js,
+                       cudaStream_t s)
+{
+    constexpr int NT = 3;
+    constexpr int smem = GBNST * GbStage<NC, NT>::BYTES;
+    int64_t cs;
+    gu_chunking(M, nks, pcap, NC, js, cs, smem <= 112 * 1024 ? 2 : 1);
+    const int64_t tot = nks * GKB * NC;
+    gb_bsplit_kernel<NC, NT><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ldx, K, nks, Bk);
+    cudaFuncSetAttribute(gemm16u_kernel<NC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 grid((unsigned)gu_tiles(M), (unsigned)js);
+    gemm16u_kernel<NC, NT><<<grid, GBT, smem, s>>>(Atl, M, nks, Bk, part, cs, err, wait_limit_ns());
+}
+
+static afn_status prod_bf16(const __nv_bfloat16 *Atl, int64_t M, int64_t K, const float *X, int64_t ldx,
+                            const float *Y, int64_t ldy, float *O, int64_t ldo, float alpha, float beta,
+                            int nrhs, float *part, size_t pcap, __nv_bfloat16 *Bk, int *err,
+                            cudaStream_t s)
+{
+    const int64_t nks = gb_nks(K);
+    for (int c0 = 0; c0 < nrhs;) {
+        const int left = nrhs - c0;
+        const int b = left >= 64 ? 64 : (left >= 32 ? 32 : 16);
+        int js = 1;
+        const float *x = X + (int64_t)c0 * ldx;
+        if (b == 64) launch_g16<64>(Atl, M, nks, x, ldx, K, part, pcap, Bk, err, js, s);
+        else if (b == 32) launch_g16<32>(Atl, M, nks, x, ldx, K, part, pcap, Bk, err, js, s);
+        else launch_g16<16>(Atl, M, nks, x, ldx, K, part, pcap, Bk, err, js, s);
+        const int64_t te = M * b;
+        gemm_finish<float><<<(unsigned)((te + 255) / 256), 256, 0, s>>>(
+            part, js, b, M, Y ? Y + (int64_t)c0 * ldy : nullptr, ldy, O + (int64_t)c0 * ldo, ldo, alpha,
+            beta);
+        c0 += b;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "BF16 tensor-core apply product");
     return AFN_OK;
 }
 
@@ -650,8 +764,7 @@ static afn_status nystrom_apply(const Handle *h, const T *r, int nrhs, T *s, T *
         }
         T *y = tmp, *v = tmp + k * nrhs;
         T *part = tmp + 2 * k * nrhs + 2 * nr * nrhs;
-        const size_t pcap = (size_t)std::max(colmul_js(nr, k), GEMM_JS_MAX) * 32 *
-                            (size_t)std::max<int64_t>(k, 1);
+        const size_t pcap = apply_pcap(nr, k);
         prod<T, true, 0>(B, k, k, n, r, n, nullptr, 0, y, k, (T)1, (T)0, nrhs, part, pcap, st);
         prod<T, false, 1>(Li, k, k, k, y, k, nullptr, 0, v, k, (T)1, (T)0, nrhs, part, pcap, st);
         prod<T, false, 2>(LiT, k, k, k, v, k, nullptr, 0, y, k, (T)1, (T)0, nrhs, part, pcap, st);
@@ -679,22 +792,29 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
     T *t = u + k * nrhs;               // nr x nrhs
     T *y = t + nr * nrhs;              // nr x nrhs
     T *part = y + nr * nrhs;           // GEMM_JS_MAX x 32 x k
-    const size_t pcap = (size_t)std::max(colmul_js(nr, k), GEMM_JS_MAX) * 32 *
-                        (size_t)std::max<int64_t>(k, 1);
+    const size_t pcap = apply_pcap(nr, k);
     const T *r1 = r, *r2 = r + k;
     T *s1 = s, *s2 = s + k;
-    // tcgen05 W products (mixed handles with tiled images, 16 or 32 columns a piece)
-    const bool tc = std::is_same<T, float>::value && h->Wu1.p && h->Wu2.p && nrhs % 16 == 0 &&
-                    use_apply_tc(h) &&
-                    (size_t)32 * (size_t)std::max(nr, k) <= pcap;
+    // tcgen05 W products (mixed handles with tiled images, 16-column pieces):
+    // mode 1 three-pass tf32 on the FP32 images, mode 2 the BF16 images
+    int tc = 0;
+    if (std::is_same<T, float>::value && nrhs % 16 == 0) {
+        if (apply_tc_mode(h) == 1 && h->Wu1.p && h->Wu2.p) tc = 1;
+        if (apply_tc_mode(h) == 2 && h->Wb1.p && h->Wb2.p) tc = 2;
+    }
     uint32_t *Bk = reinterpret_cast<uint32_t *>(part + pcap + nr * nrhs);
+    __nv_bfloat16 *Bk16 = reinterpret_cast<__nv_bfloat16 *>(Bk);
     int *err = h->status.as<int>() + 3;
     if (k > 0) prod<T, false, 1>(Linv, k, k, k, r1, n, nullptr, 0, zp, k, (T)1, (T)0, nrhs, part, pcap, st);
     if (nr > 0) {
-        if (k > 0 && tc) {
+        if (k > 0 && tc == 1) {
             if constexpr (std::is_same<T, float>::value)
                 AFN_TRY(prod_tc(h->Wu1.as<float>(), nr, k, zp, k, r2, n, t, nr, -1.f, 1.f, nrhs, part,
                                 pcap, Bk, err, st));
+        } else if (k > 0 && tc == 2) {
+            if constexpr (std::is_same<T, float>::value)
+                AFN_TRY(prod_bf16(h->Wb1.as<__nv_bfloat16>(), nr, k, zp, k, r2, n, t, nr, -1.f, 1.f,
+                                  nrhs, part, pcap, Bk16, err, st));
         } else if (k > 0) prod<T, false, 0>(Wt, k, nr, k, zp, k, r2, n, t, nr, (T)-1, (T)1, nrhs, part, pcap, st);
         else {
             int64_t tot = nr * nrhs;
@@ -719,10 +839,14 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
         }
     }
     if (k > 0) {
-        if (nr > 0 && tc) {
+        if (nr > 0 && tc == 1) {
             if constexpr (std::is_same<T, float>::value)
                 AFN_TRY(prod_tc(h->Wu2.as<float>(), k, nr, s2, n, zp, k, u, k, -1.f, 1.f, nrhs, part,
                                 pcap, Bk, err, st));
+        } else if (nr > 0 && tc == 2) {
+            if constexpr (std::is_same<T, float>::value)
+                AFN_TRY(prod_bf16(h->Wb2.as<__nv_bfloat16>(), k, nr, s2, n, zp, k, u, k, -1.f, 1.f,
+                                  nrhs, part, pcap, Bk16, err, st));
         } else if (nr > 0) {
             prod<T, true, 0>(Wt, k, k, nr, s2, n, zp, k, u, k, (T)-1, (T)1, nrhs, part, pcap, st);
         } else {

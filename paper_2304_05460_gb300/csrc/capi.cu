@@ -164,7 +164,7 @@ Profiler::~Profiler()
 
 int64_t Handle::device_bytes() const
 {
-    const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32, &Wu1, &Wu2,
+    const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32, &Wu1, &Wu2, &Wb1, &Wb2,
                          &Bn, &Bn32, &LcInv, &LcInvT, &LcInv32, &LcInvT32,
                          &pat, &G, &G32, &gt_ptr, &gt_row, &gt_slot, &status, &ws};
     int64_t s = 0;
@@ -561,7 +561,7 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         set_error("bad flexible %d", o.flexible);
         return AFN_ERR_ARG;
     }
-    if (o.apply_tc != 0 && o.apply_tc != 1) {
+    if (o.apply_tc < 0 || o.apply_tc > 2) {
         set_error("bad apply_tc %d", o.apply_tc);
         return AFN_ERR_ARG;
     }

@@ -385,22 +385,19 @@ static_assert(TCJ % UJ == 0, "the prepared arrays of both tensor-core paths shar
 // Xpr: per stage of UJ points, the point tile of matvec32u_kernel for the
 // distance form VAR (zero rows up to npad); the norms are the FMA chain the
 // kernel uses for its dot products
-template <int VAR>
+// Xpr: per stage of UJ points, the pairs (2m + h, q) at float 2m ds + 2q + h
+// (two points per f32x2 operand), zero rows up to npad
 __global__ void upoints_kernel(const float *__restrict__ Xs, int64_t n, int ds, int64_t npad,
                                float *__restrict__ Xpr)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= npad) return;
-    const int64_t base = (j / UJ) * (int64_t)UJ * (ds + (VAR == UDIRECT ? 0 : 1));
+    const int64_t base = (j / UJ) * (int64_t)UJ * ds;
     const int jj = (int)(j % UJ);
-    float nrm = 0.f;
     for (int q = 0; q < ds; ++q) {
         const float v = j < n ? Xs[j * ds + q] : 0.f;
-        nrm = __fmaf_rn(v, v, nrm);
-        if (VAR == UNORM) Xpr[base + (int64_t)jj * ds + q] = v;
-        else Xpr[base + (int64_t)(jj & ~1) * ds + 2 * q + (jj & 1)] = v;
+        Xpr[base + (int64_t)(jj & ~1) * ds + 2 * q + (jj & 1)] = v;
     }
-    if (VAR != UDIRECT) Xpr[base + (int64_t)UJ * ds + jj] = nrm;
 }
 
 // Pk: per stage of UJ points, the tf32 hi then lo halves of p in the K-major
@@ -449,90 +446,39 @@ static void chunking_u(int64_t n, int64_t nstage, int &js, int64_t &chunk_st)
     }
 }
 
-// AFN_MATVEC_TC=mma selects the mma.sync kernel for 16 and 32 right-hand
-// sides as well (comparison runs); the default is the tcgen05 kernel
-static bool use_umma()
-{
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("AFN_MATVEC_TC");
-        v = (e && strcmp(e, "mma") == 0) ? 0 : 1;
-    }
-    return v == 1;
-}
-
-template <int DS, int NB, int KER, int VAR, int UH, int UK = UK_DEF, bool P4 = false, int LEAN = 0>
+template <int DS, int NB, int KER, int UH>
 static void launch_u(const float *Xs, int64_t n, const float *Xpr, const uint32_t *Pk, float *part,
                      int js, int64_t chunk_st, int64_t nstage, int *err, cudaStream_t s)
 {
     // at least 80 KB of shared memory keeps residency at 2 CTAs per SM, the
     // number whose tensor-memory allocations fit together
-    const int smem = std::max(UNST * UStage<DS, NB * 8, VAR>::BYTES, 80 * 1024);
-    cudaFuncSetAttribute(matvec32u_kernel<DS, NB, KER, VAR, UH, UK, P4, LEAN>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = std::max(UNST * UStage<DS, NB * 8>::BYTES, 80 * 1024);
+    cudaFuncSetAttribute(matvec32u_kernel<DS, NB, KER, UH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
     dim3 g((unsigned)((n + UR - 1) / UR), (unsigned)js);
-    matvec32u_kernel<DS, NB, KER, VAR, UH, UK, P4, LEAN><<<g, umma_threads(UH), smem, s>>>(
-        Xs, n, Xpr, Pk, part, chunk_st, nstage, err, wait_limit_ns());
+    matvec32u_kernel<DS, NB, KER, UH><<<g, umma_threads(UH), smem, s>>>(Xs, n, Xpr, Pk, part, chunk_st,
+                                                                         nstage, err, wait_limit_ns());
 }
 
-// distance form and row-warp split of the tcgen05 path (AFN_UMMA_VARIANT =
-// d1 d2 n1 n2 m1 m2: UDIRECT / UNORM / UNORM2, 1 or 2 row warps per lane
-// quarter; comparison runs only).  The default d1 is the fastest solve: the
-// norm forms save FP32 work but their larger distance error for close pairs
-// costs PCG iterations (l = 4: 740 against 624).
-static int umma_variant()
-{
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("AFN_UMMA_VARIANT");
-        v = 0;   // UDIRECT, UH = 1
-        if (e && strlen(e) == 2 && strchr("dnm", e[0]) && (e[1] == '1' || e[1] == '2'))
-            v = (e[0] == 'd' ? 0 : e[0] == 'n' ? 2 : 4) + (e[1] - '1');
-        // e1: 16-point blocks; p1: the fourth product lo x lo; q1: both
-        if (e && strcmp(e, "e1") == 0) v = 6;
-        if (e && strcmp(e, "p1") == 0) v = 7;
-        if (e && strcmp(e, "q1") == 0) v = 8;
-        // l1..l7: LEAN bits (1 unrounded lo, 2 cvt hi, 4 two-level fold)
-        if (e && e[0] == 'l' && e[1] >= '1' && e[1] <= '7' && !e[2]) v = 8 + (e[1] - '0');
-    }
-    return v;
-}
-
-// the tuning variants exist for d = 8, 32 right-hand sides, the Gaussian
-// kernel; every other shape takes the default
+// the tcgen05 matvec with the row-warp split UH picked by the autotuner
+// (1 or 2 row warps per TMEM lane quarter; both form every kernel value and
+// column sum identically, so the choice never changes a result)
 template <int DS, int NB, int KER>
 static void launch_u_any(const float *Xs, int64_t n, float *Xpr, const uint32_t *Pk, float *part,
                          int js, int64_t chunk_st, int64_t npad, int *err, cudaStream_t s)
 {
     const int64_t nst = npad / UJ;
     const unsigned gb = (unsigned)((npad + 255) / 256);
-    int v = 0;
-    if constexpr (DS == 8 && NB == 4 && KER == 0) v = umma_variant();
-    const int form = (v >= 6 || v / 2 == 0) ? UDIRECT : v / 2 == 1 ? UNORM : UNORM2;
-    if (form == UDIRECT) upoints_kernel<UDIRECT><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
-    else if (form == UNORM) upoints_kernel<UNORM><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
-    else upoints_kernel<UNORM2><<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
-    if constexpr (DS == 8 && NB == 4 && KER == 0) {
-        switch (v) {
-        case 1: launch_u<DS, NB, KER, UDIRECT, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 2: launch_u<DS, NB, KER, UNORM, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 3: launch_u<DS, NB, KER, UNORM, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 4: launch_u<DS, NB, KER, UNORM2, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 5: launch_u<DS, NB, KER, UNORM2, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 6: launch_u<DS, NB, KER, UDIRECT, 1, 16, false>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 7: launch_u<DS, NB, KER, UDIRECT, 1, 32, true>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 8: launch_u<DS, NB, KER, UDIRECT, 1, 16, true>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 9: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 10: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 11: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 3>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 12: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 4>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 13: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 5>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 14: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 6>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        case 15: launch_u<DS, NB, KER, UDIRECT, 1, 32, false, 7>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s); return;
-        default: break;
-        }
-    }
-    launch_u<DS, NB, KER, UDIRECT, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+    upoints_kernel<<<gb, 256, 0, s>>>(Xs, n, DS, npad, Xpr);
+    char key[96];
+    snprintf(key, sizeof(key), "mv32u/ds%d/nb%d/ker%d/n2^%d/%s", DS, NB, KER, log2_bucket(n),
+             tune_device_tag().c_str());
+    auto run = [&](int c) {
+        if (c == 1) launch_u<DS, NB, KER, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+        else launch_u<DS, NB, KER, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+    };
+    const int uh = tune_pick(key, 2, run, s, 0);
+    run(uh);
 }
 
 size_t matvec32_scratch(int64_t n, int nrhs)
@@ -655,7 +601,7 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
         const size_t db = sizeof(f2_t) * (size_t)tp.npad * 18;
         tp.Psp = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(xd) + (db + 255) / 256 * 256);
         tp.Xdup = xd;
-        tp.umma = use_umma() && nrhs >= 16 && nrhs % 16 == 0;
+        tp.umma = nrhs >= 16 && nrhs % 16 == 0;
         if (tp.umma) {
             chunking_u(n, tp.npad / UJ, tp.jsu, tp.chunk_st);
         } else if (nrhs >= 8) {

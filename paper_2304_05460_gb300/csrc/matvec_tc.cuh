@@ -1,7 +1,7 @@
 // matvec_tc.cuh -- the mma.sync tensor-core tile of the FP32 kernel matvec,
-// used by the single-system kernel for 8-column pieces (and for 16 and 32
-// columns when AFN_MATVEC_TC=mma; the tcgen05 kernel of matvec_umma.cuh is
-// the default there) and by the grouped multi-system kernel; also the tf32
+// used by the single-system kernel for 8-column pieces (16 and 32 columns
+// run on the tcgen05 kernel of matvec_umma.cuh) and by the grouped
+// multi-system kernel; also the tf32
 // split and the staging helpers (mbarriers, bulk copies) both tiles share.
 #pragma once
 

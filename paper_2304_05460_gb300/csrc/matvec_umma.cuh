@@ -48,19 +48,11 @@ static constexpr int UTMEM = 256;   // tensor-memory columns per CTA
 // issuing warp
 __host__ __device__ constexpr int umma_threads(int uh) { return 32 * (4 * uh + 1); }
 
-// Distance forms of the row threads:
-//   UDIRECT  sum_q (x_iq - x_jq)^2, two points per f32x2 instruction
-//   UNORM    |x_i|^2 + |x_j|^2 - 2 x_i . x_j on scalar FP32 FMAs (half the
-//            FP32 operations; the norms are the same FMA chain as the dot
-//            product, so the diagonal is exactly zero), clamped at 0
-//   UNORM2   the same with two points per f32x2 instruction
-enum : int { UDIRECT = 0, UNORM = 1, UNORM2 = 2 };
-
-template <int DS, int NR, int VAR> struct UStage {
-    // point tile: UDIRECT pairs (2m + h, q) at float 2m DS + 2q + h; UNORM
-    // points (j, q) at j DS + q then the UJ norms; UNORM2 the pairs then the
-    // norms in pairs
-    static constexpr int PTS = UJ * (DS + (VAR == UDIRECT ? 0 : 1)) * 4;
+// The row threads form the squared distance directly, sum_q (x_iq - x_jq)^2,
+// two points per f32x2 instruction.
+template <int DS, int NR> struct UStage {
+    // point tile: pairs (2m + h, q) at float 2m DS + 2q + h
+    static constexpr int PTS = UJ * DS * 4;
     static constexpr int PB = UJ * NR * 4;           // one tf32 half of the p tile
     static constexpr int BYTES = PTS + 2 * PB;
 };
@@ -203,23 +195,6 @@ __device__ __forceinline__ bool mbar_wait_abort_warp(uint64_t *bar, uint32_t par
     return __all_sync(0xffffffffu, got);
 }
 
-// x = hi + lo for the three-pass product.  LEAN & 1: lo is passed unrounded
-// (the tensor core reads its leading tf32 bits: a truncation, unbiased
-// because lo has either sign); LEAN & 2: hi by cvt.rna.tf32.f32.
-template <int LEAN>
-__device__ __forceinline__ void umma_split(float x, uint32_t &hi, uint32_t &lo)
-{
-    if constexpr ((LEAN & 3) == 0) {
-        tf32_split(x, hi, lo);
-    } else {
-        if constexpr (LEAN & 2) hi = tf32_bits(x);
-        else hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
-        const float l = x - __uint_as_float(hi);
-        if constexpr (LEAN & 1) lo = __float_as_uint(l);
-        else lo = (__float_as_uint(l) + 0x1000u) & 0xffffe000u;
-    }
-}
-
 // Kahan fold of C accumulator columns (packed pairs) into acc / cmp
 template <int C>
 __device__ __forceinline__ void umma_fold(const uint32_t (&v)[C], f2_t *acc, f2_t *cmp)
@@ -246,7 +221,7 @@ __device__ __forceinline__ void umma_fold(const uint32_t (&v)[C], f2_t *acc, f2_
 //        (c%8)4 + jj%4 for point jj of the stage and column c).
 // Row sums of rows [row0, row0 + 128) leave through part (column-major per
 // chunk, leading dimension n).
-template <int DS, int NB, int KER, int VAR, int UH, int UK, bool P4, int LEAN>
+template <int DS, int NB, int KER, int UH>
 __global__ void __launch_bounds__(umma_threads(UH), 2)
     matvec32u_kernel(const float *__restrict__ Xs, int64_t n, const float *__restrict__ Xpr,
                      const uint32_t *__restrict__ Pk, float *__restrict__ part, int64_t chunk_st,
@@ -254,8 +229,9 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
 {
     constexpr int NR = NB * 8;
     constexpr int UPW = 4 * UH;                  // row warps
-    constexpr int SB = UStage<DS, NR, VAR>::BYTES;
-    constexpr int PTS = UStage<DS, NR, VAR>::PTS;
+    constexpr int UK = UK_DEF;
+    constexpr int SB = UStage<DS, NR>::BYTES;
+    constexpr int PTS = UStage<DS, NR>::PTS;
     constexpr int BPS = UJ / UK;                 // A blocks per staged tile
     constexpr uint32_t IDESC = umma_idesc_tf32(UR, NR);
     // tensor-memory columns: A buffers (hi | lo) then the accumulators
@@ -309,7 +285,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                 mbar_expect_tx(bar, (uint32_t)SB);
                 bulk_g2s(st, Xpr + (s0 + s) * (PTS / 4), (uint32_t)PTS, bar);
                 bulk_g2s(st + PTS, Pk + (s0 + s) * (int64_t)(2 * UJ * NR),
-                         (uint32_t)(2 * UStage<DS, NR, VAR>::PB), bar);
+                         (uint32_t)(2 * UStage<DS, NR>::PB), bar);
             };
             for (; issued < nst && issued < UNST; ++issued) issue(issued);
             const uint32_t base_s = smem_addr(usm);
@@ -325,7 +301,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                     break;
                 tm_fence_after();
                 const uint32_t phi = base_s + sb * SB + PTS;
-                const uint32_t plo = phi + UStage<DS, NR, VAR>::PB;
+                const uint32_t plo = phi + UStage<DS, NR>::PB;
                 const uint32_t a_hi = tbase + COL_A + b * 2 * UK, a_lo = a_hi + UK;
                 const uint32_t dcol = tbase + COL_D + b * NR;
 #pragma unroll
@@ -334,12 +310,7 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
                     const uint32_t off = (uint32_t)(((c % BPS) * (UK / 4) + 2 * q) * 128);
                     const uint64_t dh = umma_desc(phi + off, 128, (UJ / 4) * 128);
                     const uint64_t dl = umma_desc(plo + off, 128, (UJ / 4) * 128);
-                    if constexpr (P4) {
-                        umma_tf32(dcol, a_lo + 8 * q, dl, IDESC, q > 0);
-                        umma_tf32(dcol, a_lo + 8 * q, dh, IDESC, 1);
-                    } else {
-                        umma_tf32(dcol, a_lo + 8 * q, dh, IDESC, q > 0);
-                    }
+                    umma_tf32(dcol, a_lo + 8 * q, dh, IDESC, q > 0);
                     umma_tf32(dcol, a_hi + 8 * q, dl, IDESC, 1);
                     umma_tf32(dcol, a_hi + 8 * q, dh, IDESC, 1);
                 }
@@ -365,53 +336,21 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
         // ------------------------------------------------ rows -------------
         const int quarter = warp & 3, hf = warp >> 2;
         const int64_t i = row0 + quarter * 32 + lane;
-        float xi[DS];
         f2_t xi2[DS];
-        float ni = 0.f;   // |x_i|^2, the FMA chain of the dot products below
 #pragma unroll
         for (int q = 0; q < DS; ++q) {
-            xi[q] = i < n ? Xs[i * DS + q] : 0.f;
-            xi2[q] = f2_pack(xi[q], xi[q]);
-            ni = __fmaf_rn(xi[q], xi[q], ni);
+            const float v = i < n ? Xs[i * DS + q] : 0.f;
+            xi2[q] = f2_pack(v, v);
         }
-        const f2_t ni2 = f2_pack(ni, ni);
-        const f2_t m2 = f2_pack(-2.f, -2.f);
         f2_t acc[FC / 2], cmp[FC / 2];
-        // LEAN & 4: blocks are first summed in plain FP32 (acc1), and every
-        // FOLD2 blocks acc1 is folded into the Kahan sum
-        constexpr int FOLD2 = 4;
-        f2_t acc1[(LEAN & 4) ? FC / 2 : 1];
 #pragma unroll
         for (int h = 0; h < FC / 2; ++h) acc[h] = cmp[h] = 0ull;
-#pragma unroll
-        for (int h = 0; h < ((LEAN & 4) ? FC / 2 : 1); ++h) acc1[h] = 0ull;
-        auto kahan = [&](int h, f2_t tv) {
-            const f2_t y = f2_sub(tv, cmp[h]);
-            const f2_t sm = f2_add(acc[h], y);
-            cmp[h] = f2_sub(f2_sub(sm, acc[h]), y);
-            acc[h] = sm;
-        };
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         auto fold = [&](int c) -> bool {
             if (!mbar_wait_abort_warp(&bdone[c & 1], (uint32_t)(c >> 1) & 1u, abort, wait_ns)) return false;
             tm_fence_after();
             const uint32_t dcol = tbase + lane_off + COL_D + (c & 1) * NR + hf * FC;
-            if constexpr ((LEAN & 4) != 0) {
-                static_assert(FC % 16 == 0, "two-level fold width");
-                const bool first = (c % FOLD2) == 0;
-                const bool flush = (c % FOLD2) == FOLD2 - 1 || c == nblk - 1;
-#pragma unroll
-                for (int h = 0; h < FC / 16; ++h) {
-                    uint32_t v[16];
-                    tm_ld16(dcol + 16 * h, v);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const f2_t tv = f2_pack(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
-                        acc1[8 * h + e] = first ? tv : f2_add(acc1[8 * h + e], tv);
-                        if (flush) kahan(8 * h + e, acc1[8 * h + e]);
-                    }
-                }
-            } else if constexpr (FC % 16 == 0) {
+            if constexpr (FC % 16 == 0) {
 #pragma unroll
                 for (int h = 0; h < FC / 16; ++h) {
                     uint32_t v[16];
@@ -450,63 +389,23 @@ __global__ void __launch_bounds__(umma_threads(UH), 2)
             for (int g16 = 0; g16 < UK / (16 * UH); ++g16) {
                 uint32_t vh[16], vl[16];
                 const int j16 = jb + 16 * g16;
-                if constexpr (VAR == UNORM) {
-                    const float *xp = reinterpret_cast<const float *>(tile) + j16 * DS;
-                    const float *np = reinterpret_cast<const float *>(tile) + UJ * DS + j16;
+                const f2_t *xp = reinterpret_cast<const f2_t *>(tile) + j16 / 2 * DS;
 #pragma unroll
-                    for (int m4 = 0; m4 < 4; ++m4) {
-                        const float4 nj = *reinterpret_cast<const float4 *>(np + 4 * m4);
-                        const float njs[4] = {nj.x, nj.y, nj.z, nj.w};
+                for (int m = 0; m < 8; ++m) {
+                    const f2_t *pp = xp + m * DS;
+                    f2_t r = 0ull;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float *pp = xp + (4 * m4 + e) * DS;
-                            float dot = 0.f;
-#pragma unroll
-                            for (int q = 0; q < DS; q += 4) {
-                                const float4 v = *reinterpret_cast<const float4 *>(pp + q);
-                                dot = __fmaf_rn(xi[q], v.x, dot);
-                                dot = __fmaf_rn(xi[q + 1], v.y, dot);
-                                dot = __fmaf_rn(xi[q + 2], v.z, dot);
-                                dot = __fmaf_rn(xi[q + 3], v.w, dot);
-                            }
-                            const float r2 = fmaxf(__fmaf_rn(-2.f, dot, __fadd_rn(ni, njs[e])), 0.f);
-                            umma_split<LEAN>(kernel32_scaled<KER>(r2), vh[4 * m4 + e], vl[4 * m4 + e]);
-                        }
+                    for (int q = 0; q < DS; q += 2) {
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(pp + q);
+                        f2_t u = f2_sub(xi2[q], v.x);
+                        r = f2_fma(u, u, r);
+                        u = f2_sub(xi2[q + 1], v.y);
+                        r = f2_fma(u, u, r);
                     }
-                } else {
-                    const f2_t *xp = reinterpret_cast<const f2_t *>(tile) + j16 / 2 * DS;
-                    const f2_t *np = reinterpret_cast<const f2_t *>(tile + UJ * DS * 4) + j16 / 2;
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const f2_t *pp = xp + m * DS;
-                        f2_t r = 0ull;
-                        if constexpr (VAR == UDIRECT) {
-#pragma unroll
-                            for (int q = 0; q < DS; q += 2) {
-                                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(pp + q);
-                                f2_t u = f2_sub(xi2[q], v.x);
-                                r = f2_fma(u, u, r);
-                                u = f2_sub(xi2[q + 1], v.y);
-                                r = f2_fma(u, u, r);
-                            }
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < DS; q += 2) {
-                                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(pp + q);
-                                r = f2_fma(xi2[q], v.x, r);
-                                r = f2_fma(xi2[q + 1], v.y, r);
-                            }
-                            r = f2_fma(m2, r, f2_add(ni2, np[m]));
-                        }
-                        float r0, r1;
-                        f2_unpack(r, r0, r1);
-                        if constexpr (VAR != UDIRECT) {
-                            r0 = fmaxf(r0, 0.f);
-                            r1 = fmaxf(r1, 0.f);
-                        }
-                        umma_split<LEAN>(kernel32_scaled<KER>(r0), vh[2 * m], vl[2 * m]);
-                        umma_split<LEAN>(kernel32_scaled<KER>(r1), vh[2 * m + 1], vl[2 * m + 1]);
-                    }
+                    float r0, r1;
+                    f2_unpack(r, r0, r1);
+                    tf32_split(kernel32_scaled<KER>(r0), vh[2 * m], vl[2 * m]);
+                    tf32_split(kernel32_scaled<KER>(r1), vh[2 * m + 1], vl[2 * m + 1]);
                 }
                 tm_st16(a_hi + 16 * g16, vh);
                 tm_st16(a_lo + 16 * g16, vl);

@@ -288,6 +288,56 @@ def test_mixed_apply_tensor_core_products(afn, n, k, nrhs):
     afn.afn_free(h_cc)
 
 
+def _bf16(a):
+    """Round FP64 values to BF16 (8-bit significand, round to nearest even) via FP32."""
+    f = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _apply_wform(Lo, Wt, pat, Gv, r):
+    """Alg. 3 in the W form, FP64: z' = L^{-1} r1, t = r2 - W^T z', s2 = G^T G t,
+    s1 = L^{-T} (z' - W s2); Wt is W^T (nr x k), G as ELL (pattern, values)."""
+    k, nr = Lo.shape[0], Wt.shape[0]
+    Gd = np.zeros((nr, nr))
+    for i in range(nr):
+        for p_, c in enumerate(pat[i]):
+            if c >= 0:
+                Gd[i, c] = Gv[i, p_]
+    zp = np.linalg.solve(Lo, r[:k])
+    t = r[k:] - Wt @ zp
+    s2 = Gd.T @ (Gd @ t)
+    s1 = np.linalg.solve(Lo.T, zp - Wt.T @ s2)
+    return np.concatenate([s1, s2])
+
+
+@pytest.mark.parametrize("n,k,nrhs", [(3001, 300, 64), (2600, 130, 16), (3001, 300, 80),
+                                      (2200, 700, 32)])
+def test_mixed_apply_bf16_tensor_core_products(afn, n, k, nrhs):
+    # apply_tc = 2: the W products on the tcgen05 tensor cores with a BF16 copy of W and the
+    # vectors in three BF16 terms.  Against the same apply written out in FP64 with the
+    # handle's own factors and W rounded to BF16 (the only approximation besides FP32
+    # arithmetic); ragged k and n - k, 16/32/64-column pieces
+    X = inputs.normal_points(n, 8, 830 + n)
+    h = afn.afn_build(X, G, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED, apply_tc=2)
+    bi = h.info
+    assert bi.k == k and bi.nr == n - k
+    r = inputs.rhs(n, nrhs, 840 + n)
+    before = afn.afn_get_build_info(h).device_bytes
+    s_tc = afn.afn_apply_precond(h, r)
+    grown = afn.afn_get_build_info(h).device_bytes - before
+    assert grown >= 2 * 2 * k * (n - k)            # the two BF16 images of W were built
+    Lo = afn.afn_get_L(h)
+    Wt = afn.afn_get_W(h)
+    pat, Gv = afn.afn_get_G(h)
+    Gv32 = Gv.astype(np.float32).astype(np.float64)
+    cols = [0, nrhs // 2, nrhs - 1]
+    ref = np.stack([_apply_wform(Lo, _bf16(Wt), pat, Gv32, r[:, c]) for c in cols], 1)
+    err = _cmp(s_tc[:, cols], ref, 0)
+    assert err <= 1e-3, err
+    afn.afn_free(h)
+
+
 def test_not_spd_reported(afn):
     # duplicated landmarks make K11 singular; mu tiny keeps K11 + mu I at the
     # edge -- with mu = 1e-300 the Cholesky pivot underflows to <= 0
@@ -413,6 +463,44 @@ def test_solve_headline_normal_8d_oracle_residual(afn):
     assert np.all(rel <= 1e-6), rel
     # the library's own FP64 residual agrees with the oracle's
     assert np.allclose(info["relres"][cols], rel, rtol=1e-3, atol=1e-12)
+    afn.afn_free(h)
+
+
+def test_solve_clusters_3d_prefix_bf16_oracle_residual(afn):
+    # the n = 200k, d = 3 clustered workload's configuration (Matern-3/2 l = 0.05, mu = 1e-3,
+    # w = 50, 64 right-hand sides, BF16 tensor-core W products, FP64 residual replacements)
+    # on its first 50,000 points with the same k / n (500 landmarks): the true relative
+    # residual of two columns recomputed by the oracle in FP64
+    s = inputs.clusters_3d(nrhs=64)
+    n, k = 50_000, 500
+    X, B = s.X[:n], np.asfortranarray(s.B[:n])
+    h = afn.afn_build(X, s.kernel, s.l, s.mu, k, s.w, precision=afn.PREC_MIXED, apply_tc=2,
+                      max_iter=3000)
+    x, info = afn.afn_solve(h, B, 1e-6)
+    assert info["converged"] == 64, info
+    cols = [0, 63]
+    rel = oracle.true_relres(X, s.kernel, s.l, s.mu, x[:, cols], B[:, cols])
+    assert np.all(rel <= 1e-6), rel
+    afn.afn_free(h)
+
+
+def test_solve_clusters_3d_full_size_bf16(afn):
+    # the full n = 200k clustered workload (k = 2000): every column's residual recomputed by
+    # the FP64-accurate double-float matvec (parity-tested against the oracle), and that
+    # matvec checked against the oracle on sampled rows of the solution
+    s = inputs.clusters_3d(nrhs=64)
+    h = afn.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w, precision=afn.PREC_MIXED, apply_tc=2,
+                      max_iter=3000)
+    x, info = afn.afn_solve(h, s.B, 1e-6)
+    assert info["converged"] == 64, info
+    q = afn.afn_kernel_matvec(s.X, s.kernel, s.l, s.mu, x, precision=afn.MATVEC_DF)
+    rel = np.linalg.norm(s.B - q, axis=0) / np.linalg.norm(s.B, axis=0)
+    assert np.all(rel <= 1e-6), rel.max()
+    rows = _sample_rows(s.n, 50, 41, 24)
+    cols = [0, 63]
+    ref = oracle.matvec_rows(s.X, s.kernel, s.l, s.mu, x[:, cols], rows)
+    absb = oracle.matvec_rows(s.X, s.kernel, s.l, s.mu, np.abs(x[:, cols]), rows)
+    assert np.all(np.abs(q[np.ix_(rows, cols)] - ref) <= 1e-11 * absb)
     afn.afn_free(h)
 
 

@@ -49,10 +49,12 @@ def test_matvec_wait_limit_runs_out_and_recovers(afn):
     _matvec_ok(afn, X, P)
 
 
-def test_apply_wait_limit_runs_out_and_recovers(afn):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_apply_wait_limit_runs_out_and_recovers(afn, mode):
+    # the tensor-core W products: three-pass tf32 (mode 1) and BF16 (mode 2)
     n, k = 2600, 260
     X = inputs.normal_points(n, 8, 73)
-    h = afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED, apply_tc=1)
+    h = afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-2, k, 32, precision=afn.PREC_MIXED, apply_tc=mode)
     r = inputs.rhs(n, 32, 74)             # 32 columns: the tcgen05 W products
     s0 = afn.afn_apply_precond(h, r)
     try:
