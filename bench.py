@@ -39,6 +39,7 @@ SERVE_MAXIT = 1000   # per request in the serving stream (a request past it repo
 METRIC = "AFN-PCG solves/s at rel. residual 1e-6 (mixed precision, 8-D normal, n=50k, 32 RHS)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES, MUFU_PER_SM, SM_MAX_MHZ = 152, 128, 16, 2070.0
+LANE_PEAK_TOPS = N_SM * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12    # FP32 lane operations / s
 # DRAM bytes read + written per launch of matvec32u_kernel<8, 4, Gaussian> at n = 50,000,
 # 32 columns, from one ncu capture of that launch; to be re-taken when the kernel changes
 MATVEC32_TRAFFIC_BYTES = 16048128 + 0
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--only", default="",
-                    help="'batched' or 'serving': run that workload alone (profiling)")
+                    help="'batched', 'serving' or 'clusters': run that workload alone")
     ap.add_argument("--alg5-steps", type=int, default=1,
                     help="steps of the workload under the paper's Alg. 5 strategy (0 = skip)")
     ap.add_argument("--sequential", action="store_true",
@@ -68,10 +69,15 @@ def parse():
                     help="systems of the batched workload (0 = skip)")
     ap.add_argument("--fp64-sample", type=int, default=24,
                     help="batched systems solved one at a time in plain FP64 for comparison")
-    ap.add_argument("--serving", type=int, default=32,
+    ap.add_argument("--serving", type=int, default=40,
                     help="requests of the serving stream (0 = skip)")
-    ap.add_argument("--serving-rate", type=float, default=0.0,
-                    help="Poisson arrival rate, requests/s (0 = all requests at t = 0)")
+    ap.add_argument("--serving-rate", type=float, default=-0.8,
+                    help="Poisson arrival rate, requests/s (0 = all requests at t = 0; "
+                         "negative: that multiple of the measured FP64 one-at-a-time rate)")
+    ap.add_argument("--clusters", type=int, default=1,
+                    help="1 = run the n = 200k clustered 64-RHS workload (0 = skip)")
+    ap.add_argument("--one-rhs", type=int, default=1,
+                    help="1 = run the n = 50k workload with one right-hand side (0 = skip)")
     return ap.parse_args()
 
 
@@ -332,20 +338,61 @@ def run_batched(afn, count, fp64_sample, stream, rank=0, world=1, dist=None):
 
 
 # ---------------------------------------------------------------- serving --
-def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None):
+def serving_fp64_baseline(afn, count, fp64_sample):
+    """The plain FP64 GPU path, one request at a time, on a seeded sample of the
+    serving stream's requests with n <= 20,000 (larger ones take minutes in
+    FP64), scaled to the whole stream by sum(n^2).  The FP64 matvec's cost is
+    n^2 per iteration but the iteration counts differ between requests, so the
+    scaled figure is an estimate; the sample and the scaling are reported."""
+    import torch
+    from paper_2304_05460_gb300 import inputs
+    reqs = inputs.serving_stream(count=count, rate=1.0)
+    small = [i for i, r in enumerate(reqs) if r["n"] <= 20_000]
+    g = np.random.Generator(np.random.PCG64(11))
+    pick = sorted(g.choice(small, size=min(fp64_sample, len(small)), replace=False).tolist())
+    o64 = afn.options(precision=afn.PREC_FP64, seed=1005, max_iter=SERVE_MAXIT)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for i in pick:
+        sy = inputs.serving_system(reqs[i])
+        h = afn.afn_build(sy.X, sy.kernel, sy.l, sy.mu, sy.k, sy.w, o64)
+        afn.afn_solve(h, sy.B, TOL)
+        afn.afn_free(h)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t1
+    n2 = sum(float(reqs[i]["n"]) ** 2 for i in pick)
+    n2_all = sum(float(r["n"]) ** 2 for r in reqs)
+    t_all = t64 * n2_all / n2
+    cols = sum(r["nrhs"] for r in reqs)
+    return {"solves_per_s": cols / t_all, "requests_per_s": count / t_all,
+            "sample_requests": len(pick), "sample_n": [int(reqs[i]["n"]) for i in pick],
+            "sample_s": t64,
+            "scaling": "sample (requests with n <= 20000) time x sum(n^2) / sum(n^2) of the "
+                       "sample; an estimate: iteration counts are not proportional to n^2"}
+
+
+def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None, fp64=None):
     """The serving workload: `count` requests of the Poisson stream (n
     log-uniform in [1e3, 1e5], d in {3, 8, 16}, N(0,I) points, Gaussian or
     Matern-3/2 50/50, l and mu drawn as in the batched workload, k =
     min(n/4, 1000), w = 32, 1..16 RHS, tol 1e-6) replayed against the serving
-    loop; latency is submit -> result.  rate 0 submits every request at once
-    (saturation throughput).  The plain FP64 GPU path, one request at a time,
-    is timed on a seeded sample and scaled by sum(n^2).  With several ranks
-    the requests are dealt to them (``deal``, cost n^2), each rank serves its
-    share at the share's own arrival times, and the job's makespan is the
-    slowest rank's."""
+    loop; latency is submit -> result.  rate > 0: Poisson arrivals at that
+    rate (requests/s); rate == 0: every request at once (saturation); rate < 0:
+    Poisson at -rate x the plain FP64 one-at-a-time throughput (measured first,
+    ``serving_fp64_baseline``).  With several ranks the requests are dealt to
+    them (``deal``, cost n^2), each rank serves its share at the share's own
+    arrival times, and the job's makespan is the slowest rank's."""
     import threading
     import torch
     from paper_2304_05460_gb300 import inputs
+    if fp64 is None and fp64_sample > 0 and world == 1:
+        fp64 = serving_fp64_baseline(afn, count, fp64_sample)
+    factor = None
+    if rate < 0:
+        if not fp64:
+            raise RuntimeError("a rate relative to FP64 needs the FP64 baseline")
+        factor = -rate
+        rate = factor * fp64["requests_per_s"]
     reqs = inputs.serving_stream(count=count, rate=rate if rate > 0 else 1.0)
     if world > 1:
         reqs = [reqs[i] for i in deal([float(r["n"]) ** 2 for r in reqs], world)[rank]]
@@ -374,11 +421,12 @@ def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None):
 
     th = threading.Thread(target=feeder)
     th.start()
-    lat, conv, done = [], 0, 0
+    lat, conv, done, qms = [], 0, 0, []
     while done < len(reqs):
         for rid in srv.poll(wait_ms=50):
             x, info = srv.result(rid)
             lat.append(info["latency_ms"])
+            qms.append(info["queue_ms"])
             conv += int(info["converged"])
             done += 1
     span = time.perf_counter() - t0
@@ -391,44 +439,175 @@ def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None):
         conv = int(job_sum(conv, dist, "cuda"))
         lat = job_gather(lat, dist)
     lat = np.sort(np.array(lat))
+    arrivals = ("Poisson %.3g/s (%.2f x the FP64 one-at-a-time rate)" % (rate, factor)
+                if factor else "Poisson %.3g/s" % rate if rate > 0 else "all at t = 0 (saturation)")
     out = {"workload": "serving_stream: %d requests, n log-uniform [1e3, 1e5], d in {3,8,16}, "
                        "N(0,I), Gaussian/Matern-3/2 50/50, l = median dist x logU[0.1, 10], "
                        "mu logU[1e-4, 1e-1], k = min(n/4, 1000), w = 32, 1-16 RHS, tol 1e-6, "
-                       "at most %d iterations; arrivals: %s"
-                       % (count, SERVE_MAXIT, "Poisson %.3g/s" % rate if rate > 0 else
-                          "all at t = 0 (saturation)"),
-           "requests": count, "ranks": world, "columns": cols, "converged_columns": conv,
-           "makespan_s": span,
+                       "at most %d iterations; arrivals: %s" % (count, SERVE_MAXIT, arrivals),
+           "requests": count, "ranks": world, "rate_per_s": rate, "columns": cols,
+           "converged_columns": conv, "makespan_s": span,
            "requests_per_s": count / span, "solves_per_s": cols / span,
            "latency_p50_ms": float(np.percentile(lat, 50)),
            "latency_p99_ms": float(np.percentile(lat, 99)),
+           "latency_max_ms": float(lat[-1]),
+           "queue_p50_ms": float(np.percentile(qms, 50)) if qms else None,
            "peak_live": st["peak_live"], "graph_launches": st["graph_launches"],
            "peak_reserved_gb": st["peak_reserved_bytes"] / 2**30}
-    if fp64_sample > 0 and world == 1:
-        # the FP64 path takes minutes on the largest requests: sample among
-        # those with n <= 20,000 and scale by sum(n^2)
-        g = np.random.Generator(np.random.PCG64(11))
-        small = [i for i, s in enumerate(systems) if s.n <= 20_000]
-        pick = sorted(g.choice(small, size=min(fp64_sample, len(small)), replace=False).tolist())
-        o64 = afn.options(precision=afn.PREC_FP64, seed=1005, max_iter=SERVE_MAXIT)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for i in pick:
-            s = systems[i]
-            h = afn.afn_build(s.X, s.kernel, s.l, s.mu, s.k, s.w, o64)
-            afn.afn_solve(h, s.B, TOL)
-            afn.afn_free(h)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t1
-        n2 = sum(float(systems[i].n) ** 2 for i in pick)
-        n2_all = sum(float(s.n) ** 2 for s in systems)
-        t_all = t64 * n2_all / n2
-        out["fp64_one_at_a_time"] = {"solves_per_s": cols / t_all, "requests_per_s": count / t_all,
-                                     "sample_requests": len(pick), "sample_s": t64,
-                                     "scaling": "sample (requests with n <= 20000) time x "
-                                                "sum(n^2) / sum(n^2) of the sample"}
-        out["speedup_vs_fp64"] = out["solves_per_s"] / out["fp64_one_at_a_time"]["solves_per_s"]
+    if fp64:
+        out["fp64_one_at_a_time"] = fp64
+        out["speedup_vs_fp64"] = out["solves_per_s"] / fp64["solves_per_s"]
     return out
+
+
+# ---------------------------------------------------- n = 200k clustered --
+def hbm_peak():
+    """(GB/s, basis) of the HBM roofline: the measured copy bandwidth."""
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def run_clusters(afn, stream):
+    """The clustered 3-D workload: n = 200,000 points (80 % in 3 Gaussian
+    clusters, centres U[0,1]^3, sigma = 0.1, 20 % uniform), Matern-3/2 l = 0.05,
+    mu = 1e-3, k = 2000 FPS landmarks, FSAI w = 50, 64 right-hand sides N(0,1),
+    mixed precision with the BF16 tensor-core W products and FP64 residual
+    replacements to tol 1e-6.  One build + solve timed with CUDA events after a
+    warm-up on the first 20,000 points.  Rooflines: the FP32 matvec (FP32
+    lane operations) and the apply (HBM bytes of its operators per apply)."""
+    import torch
+    from paper_2304_05460_gb300 import inputs
+    s = inputs.clusters_3d(nrhs=64)
+    Xd = torch.tensor(s.X, device="cuda")
+    Bd = torch.tensor(np.ascontiguousarray(s.B), device="cuda")
+    o = afn.options(precision=afn.PREC_MIXED, seed=1003, max_iter=MAXIT, stream=stream, profile=1)
+    h = afn.afn_build(Xd[:20000].contiguous(), s.kernel, s.l, s.mu, 200, s.w, o)
+    afn.afn_solve(h, Bd[:20000].contiguous(), TOL)
+    afn.afn_free(h)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    h = afn.afn_build(Xd, s.kernel, s.l, s.mu, s.k, s.w, o)
+    e[1].record(stream)
+    x, info = afn.afn_solve(h, Bd, TOL)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    bms, sms_ = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    st = {nm: afn.afn_get_kernel_stats(h, nm) for nm in
+          ("matvec32", "matvec64", "apply32", "blas1", "fps", "knn", "chol", "trsm", "fsai")}
+    bi = h.info
+    k, nr, w, n = int(bi.k), int(bi.nr), int(bi.w), int(bi.n)
+    afn.afn_free(h)
+    if info["converged"] != 64:
+        raise RuntimeError("clusters_3d: %d/64 columns reached tol" % info["converged"])
+    gbs, basis = hbm_peak()
+    ap_cnt, ap_ms = st["apply32"]
+    # algorithmic bytes of one 64-column apply: the BF16 W image read by each of the two
+    # products, G (FP32 value + int32 index) by each sparse product, the triangular L^-1 and
+    # L^-T (FP32), r read and s written once
+    ap_bytes = 2 * 2.0 * k * nr + 2 * 8.0 * nr * w + 2 * 4.0 * k * (k + 1) / 2 + 2 * 4.0 * n * 64
+    ap_avg = ap_ms / max(ap_cnt, 1)
+    mv_cnt, mv_ms = st["matvec32"]
+    mv_avg = mv_ms / max(mv_cnt, 1)          # one 64-column matvec = two 32-column launches
+    ops_pair = 2 * 4 + 4 + 32                # d-hat = 4: 2 d-hat + Matern's sqrt/scale + 32 columns
+    mv_ops = 2.0 * float(n) * n * ops_pair
+    return {"workload": "clusters_3d: n=200000 d=3 (3 clusters sigma=0.1 + 20%% uniform), "
+                        "Matern-3/2 l=0.05, mu=1e-3, k=2000 FPS, w=50, 64 RHS N(0,1), tol 1e-6, "
+                        "mixed precision, BF16 tensor-core W products",
+            "value": 64.0 / ((bms + sms_) / 1e3), "unit": "solves/s",
+            "solve_only_solves_per_s": 64.0 / (sms_ / 1e3), "build_ms": bms, "solve_ms": sms_,
+            "iters_max": int(info["iters"].max()), "iters_mean": float(info["iters"].mean()),
+            "residual_replacements": int(info["outer_steps"]),
+            "relres_max": float(info["relres"].max()),
+            "kernels": {a: {"launches": b[0], "ms": round(b[1], 3)} for a, b in st.items()},
+            "roofline_apply": {"bound": "hbm", "achieved": ap_bytes / (ap_avg / 1e3) / 1e9,
+                               "peak": gbs, "unit": "GB/s",
+                               "frac": ap_bytes / (ap_avg / 1e3) / 1e9 / gbs,
+                               "bytes_per_apply": ap_bytes, "avg_apply_ms": ap_avg,
+                               "applies": ap_cnt, "peak_basis": basis},
+            "roofline_matvec": {"bound": "alu", "achieved": mv_ops / (mv_avg / 1e3) / 1e12,
+                                "peak": LANE_PEAK_TOPS, "unit": "Tops/s",
+                                "frac": mv_ops / (mv_avg / 1e3) / 1e12 / LANE_PEAK_TOPS,
+                                "ops_per_pair": ops_pair, "avg_matvec_ms": mv_avg},
+            "fp64_gpu": None,
+            "fp64_note": "the plain FP64 GPU solve of this workload takes minutes (FP64 matvec "
+                         "at n = 200k, 64 columns); measured once outside the default run"}
+
+
+# ------------------------------------------------------------ one column --
+def run_one_rhs(afn, s, Xd, Bd, stream, opts):
+    """The n = 50k, d = 8 workload with one right-hand side per system: the four
+    length-scales built and solved concurrently (as the headline), one warm-up
+    step and one timed step; the 1-column matvec runs on the CUDA cores
+    (MUFU / FP32 bound) and its roofline is reported."""
+    import torch
+    st_ = [torch.cuda.Stream() for _ in LS]
+    stats, iters = {}, []
+    lock = threading.Lock()
+    b1 = Bd[:, :1].contiguous()
+
+    def one(l, st, prof):
+        with torch.cuda.stream(st):
+            h = afn.afn_build(Xd, afn.GAUSSIAN, l, MU, KMAX, W, opts(prof, st))
+            x, info = afn.afn_solve(h, b1, TOL)
+            st.synchronize()
+        with lock:
+            if info["converged"] != 1:
+                raise RuntimeError("1 RHS, l=%g did not converge" % l)
+            iters.append(int(info["iters"].max()))
+            if prof:
+                for nm in ("matvec32", "apply32"):
+                    c, ms = afn.afn_get_kernel_stats(h, nm)
+                    a = stats.setdefault(nm, [0, 0.0])
+                    a[0] += c
+                    a[1] += ms
+        afn.afn_free(h)
+
+    def step(prof):
+        errs = []
+
+        def run(l, st):
+            try:
+                one(l, st, prof)
+            except BaseException as e:
+                errs.append(e)
+        ts = [threading.Thread(target=run, args=(l, st)) for l, st in zip(LS, st_)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        if errs:
+            raise errs[0]
+
+    step(0)
+    iters.clear()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mv_cnt, mv_ms = stats.get("matvec32", [0, 0.0])
+    avg = mv_ms / max(mv_cnt, 1)
+    ops_pair = 2 * D + 1 + 1
+    n = s.X.shape[0]
+    ach = float(n) * n * ops_pair / (avg / 1e3) / 1e12
+    mufu_peak = N_SM * MUFU_PER_SM * SM_MAX_MHZ * 1e6          # pairs/s at one EX2 a pair
+    return {"workload": "normal_8d with 1 RHS per system (l in {0.5,1,2,4}, concurrent)",
+            "value": len(LS) / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms,
+            "pcg_iters_max": iters,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": LANE_PEAK_TOPS, "unit": "Tops/s",
+                         "frac": ach / LANE_PEAK_TOPS, "ops_per_pair": ops_pair,
+                         "kernel": "matvec32_kernel<D=8,NR=1,Gaussian> (CUDA cores)",
+                         "avg_launch_ms": avg, "launches": mv_cnt,
+                         "mufu_bound_pairs_per_s": mufu_peak,
+                         "pairs_per_s": float(n) * n / (avg / 1e3),
+                         "note": "FP32 lane operations 2d+1+1 per pair; the EX2 (MUFU, "
+                                 "16 per SM per cycle) bound is above the FP32 one at d = 8"}}
 
 
 # ------------------------------------------------------------------- main --
@@ -468,8 +647,12 @@ def main():
 
     stream = torch.cuda.current_stream()
     if args.only:
-        out = (run_batched(afn, args.batched, args.fp64_sample, stream) if args.only == "batched"
-               else run_serving(afn, args.serving, args.serving_rate, args.fp64_sample))
+        if args.only == "batched":
+            out = run_batched(afn, args.batched, args.fp64_sample, stream)
+        elif args.only == "clusters":
+            out = run_clusters(afn, stream)
+        else:
+            out = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4))
         print(json.dumps({"only": args.only, args.only: out}), flush=True)
         return
     s = workload(args.n, args.nrhs)
@@ -594,22 +777,26 @@ def main():
                 "note": "Alg. 5: Nystrom preconditioner (eq. nystrom1-smw) when the Alg. 4 "
                         "estimate is below 2000, AFN otherwise; same schedule and tolerance"}
 
-    # roofline of the dominant kernel (FP32 matvec): FP32-pipe bound
+    # roofline of the dominant kernel (FP32 matvec): FP32-pipe bound, counted in FP32
+    # lane operations per kernel-pair evaluation, 2d + 1 + nrhs (d subtractions, d
+    # multiply-adds for r^2, the scale, and one multiply-add per right-hand side)
     mv_cnt, mv_ms = stats.get("matvec32", [0, 0.0])
     n = args.n
     nr_piece = min(args.nrhs, 32)
-    flops_per_launch = float(n) * n * (3 * D + 2 * nr_piece)
+    ops_pair = 2 * D + 1 + nr_piece
+    ops_per_launch = float(n) * n * ops_pair
     avg_ms = mv_ms / max(mv_cnt, 1)
-    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if mv_cnt else None
-    peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    achieved = ops_per_launch / (avg_ms / 1e3) / 1e12 if mv_cnt else None
+    peak = LANE_PEAK_TOPS
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": MATVEC32_TRAFFIC_BYTES if (n == N and nr_piece == 32) else None,
-            "kernel": ("matvec32u_kernel<DS=8,NB=%d,Gaussian,direct> (tcgen05)" % (nr_piece // 8)
+            "kernel": ("matvec32u_kernel<DS=8,NB=%d,Gaussian> (tcgen05)" % (nr_piece // 8)
                        if nr_piece >= 16 else "matvec32tca_kernel<DS=8,NB=%d,Gaussian>" % (nr_piece // 8)),
-            "flops_per_pair": 3 * D + 2 * nr_piece,
+            "ops_per_pair": ops_pair,
             "pairs_per_launch": float(n) * n, "avg_launch_ms": avg_ms, "launches": mv_cnt,
-            "peak_basis": "FP32 pipe: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"}
+            "peak_basis": "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz, one lane operation per "
+                          "lane per cycle (derived); ops = FP32 lane operations, 2d+1+nrhs per pair"}
     if achieved and nr_piece >= 16:
         # the contraction runs on the tensor cores; the FP32 pipe still evaluates every
         # kernel value: d subtractions, d FMAs and the split, 2d + 1 lane-operations a pair
@@ -635,7 +822,7 @@ def main():
         c1.record(stream)
         torch.cuda.synchronize()
         iso_ms = c0.elapsed_time(c1) / reps
-        iso = flops_per_launch / (iso_ms / 1e3) / 1e12
+        iso = ops_per_launch / (iso_ms / 1e3) / 1e12
         roof["isolated"] = {"avg_call_ms": iso_ms, "achieved": iso, "frac": iso / peak,
                             "basis": "afn_kernel_matvec alone, same points and 32 columns, "
                                      "CUDA events over %d calls" % reps}
@@ -675,6 +862,18 @@ def main():
             batched = run_batched(afn, args.batched, args.fp64_sample, stream, rank, world, dist)
         except Exception as e:          # reported in the line, the headline stands
             batched = {"error": repr(e)}
+    clusters = None
+    if rank == 0 and args.clusters > 0:
+        try:
+            clusters = run_clusters(afn, stream)
+        except Exception as e:
+            clusters = {"error": repr(e)}
+    one_rhs = None
+    if rank == 0 and args.one_rhs > 0:
+        try:
+            one_rhs = run_one_rhs(afn, s, Xd, Bd, stream, opts)
+        except Exception as e:
+            one_rhs = {"error": repr(e)}
     serving = None
     if args.serving > 0:
         try:
@@ -704,7 +903,8 @@ def main():
                                  "per-class device time summed over launches (CUDA events)"),
                 "fp64_gpu": fp64,
                 "pcg_iters_max": iters_seen[-len(LS):] if iters_seen else None,
-                "batched": batched, "serving": serving}
+                "batched": batched, "serving": serving, "clusters_3d": clusters,
+                "normal_8d_1rhs": one_rhs}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -106,7 +106,7 @@ typedef struct {
                                   tiles; 1 = tcgen05 tensor cores, three-pass tf32 on the FP32
                                   W with FP32 accumulation; 2 = tcgen05 tensor cores on a BF16
                                   copy of W (half the bytes streamed), the vectors split into
-                                  three BF16 terms, FP32 accumulation; default 0 */
+                                  three BF16 terms, FP32 accumulation; default 2 */
     int32_t flexible;          /* mixed handles: 1 = flexible PCG, beta in the Polak-Ribiere
                                   form r_{k+1}^T (z_{k+1} - z_k) / r_k^T z_k (Notay 2000), which
                                   tolerates the FP32 apply being inexact; 0 = the textbook

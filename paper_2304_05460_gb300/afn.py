@@ -99,6 +99,12 @@ def _load():
         "afn_launch_count": (i64, []),
         "afn_release_cached_memory": (None, []),
         "afn_set_wait_limit_ns": (None, [i64]),
+        "afn_tune_set_cache": (i32, [C.c_char_p]),
+        "afn_tune_get": (i32, [C.c_char_p, C.POINTER(i32)]),
+        "afn_tune_put": (i32, [C.c_char_p, i32]),
+        "afn_tune_count": (i32, []),
+        "afn_tune_key": (i32, [i32, C.c_char_p, i32]),
+        "afn_tune_clear": (None, []),
         "afn_kernel_matvec_noalloc": (i32, [P, i64, i32, i32, dbl, dbl, P, i32, P, P]),
         "afn_build_batched": (i32, [C.POINTER(afn_system), i32, C.POINTER(afn_options),
                                     C.POINTER(P)]),
@@ -321,6 +327,37 @@ def afn_release_cached_memory():
 def afn_set_wait_limit_ns(ns: int):
     """Limit of the tensor-core kernels' bounded device waits (ns; <= 0 = 2 s)."""
     _lib.afn_set_wait_limit_ns(int(ns))
+
+
+# --------------------------------------------------------------- autotuner --
+def afn_tune_set_cache(path):
+    """Persist the autotuner's choices in `path` (loaded if present); None stops."""
+    _check(_lib.afn_tune_set_cache(None if path is None else str(path).encode()))
+
+
+def afn_tune_get(key):
+    v = C.c_int32(0)
+    _check(_lib.afn_tune_get(key.encode(), C.byref(v)))
+    return int(v.value)
+
+
+def afn_tune_put(key, choice):
+    _check(_lib.afn_tune_put(key.encode(), int(choice)))
+
+
+def afn_tune_entries():
+    """{key: choice} of every recorded decision."""
+    out = {}
+    buf = C.create_string_buffer(256)
+    for i in range(_lib.afn_tune_count()):
+        v = _lib.afn_tune_key(i, buf, 256)
+        if v >= 0:
+            out[buf.value.decode()] = int(v)
+    return out
+
+
+def afn_tune_clear():
+    _lib.afn_tune_clear()
 
 
 def afn_reset_kernel_stats(h: Handle):

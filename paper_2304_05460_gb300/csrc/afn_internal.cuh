@@ -263,9 +263,10 @@ afn_status nystrom_factor(Handle *h, cudaStream_t s);
 struct GDev;
 // share: fraction of each SM's CTA slots the persistent grids take (1 = all;
 // less leaves room for work on other streams, e.g. the server's builds)
-afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share);
+// cps: persistent CTAs per SM (0 = the default; the autotuner's choice)
+afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share, int cps = 0);
 afn_status group_matvec64(const GDev *gd, cudaStream_t s, double share);
-afn_status group_apply(const GDev *gd, cudaStream_t s, double share);
+afn_status group_apply(const GDev *gd, cudaStream_t s, double share, int cps = 0);
 int persistent_grid(int ctas_per_sm, double share);   // max(1, SMs x ctas_per_sm x share)
 // caps, for the calling thread's scope, the fraction of CTA slots a
 // double-float matvec may take (read at every launch; 1 = no cap); used by

@@ -989,9 +989,9 @@ __global__ void __launch_bounds__(256) gap_sparse_kernel(const GDev *__restrict_
 int group_sparse_rows() { return 256 / GC; }
 int group_block_rows() { return GM; }
 
-afn_status group_apply(const GDev *gd, cudaStream_t s, double share)
+afn_status group_apply(const GDev *gd, cudaStream_t s, double share, int cps)
 {
-    const int g = persistent_grid(4, share);
+    const int g = persistent_grid(cps > 0 ? cps : 4, share);
     gap_gemm_kernel<0><<<g, 256, 0, s>>>(gd);
     gap_gemm_kernel<1><<<g, 256, 0, s>>>(gd);
     gap_sparse_kernel<0><<<g, 256, 0, s>>>(gd);

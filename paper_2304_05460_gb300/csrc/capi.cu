@@ -691,7 +691,7 @@ void afn_default_options(afn_options *o)
     o->precond = AFN_PRECOND_AFN;
     o->precond_threshold = 0;
     o->factors = AFN_FACTORS_FP32;
-    o->apply_tc = 0;
+    o->apply_tc = 2;
     o->flexible = 0;
     o->pad_ = 0;
 }

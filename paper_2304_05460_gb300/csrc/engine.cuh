@@ -56,6 +56,7 @@ public:
 private:
     afn_status upload();
     afn_status capture();
+    void tune();                  // persistent-grid sizes of the grouped kernels (autotuner)
     afn_status iteration(int it);
     void mark(int it, int stage);
 
@@ -71,6 +72,8 @@ private:
     int *nact_host_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     long long kpg_ = 0;           // kernels per graph launch
+    bool tuned_ = false;
+    int cps_mv_ = 0, cps_ap_ = 0; // CTAs per SM of the grouped matvec and apply (0 = default)
     int launches_ = 0;
     GDev hgd_{};
     bool prof_ = false;

@@ -15,10 +15,11 @@
 
 namespace afn {
 
-static constexpr int FT = 256;   // threads per CTA
 static constexpr int KC = 32;    // landmarks per Gram chunk
 
-template <int WM, class TW>
+// FT threads per CTA (autotuned: 128 or 256 for w <= 64, 256 or 512 above;
+// every Gram entry and Cholesky step is the same sum whatever FT is)
+template <int WM, class TW, int FT>
 __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr, int d, int kernel,
                                                   double l, double mu,
                                                   const TW *__restrict__ Wt, int64_t k,
@@ -143,14 +144,14 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
     if (tid == 0 && bad) atomicExch(status, DEV_NOT_SPD);
 }
 
-template <int WM, class TW>
-static afn_status launch_fsai(const double *Xr, int64_t nr, int d, KParams kp, const TW *Wt,
-                              int64_t k, const int32_t *pat, int w, double *G, int *status,
-                              cudaStream_t s)
+template <int WM, class TW, int FT>
+static afn_status launch_fsai_ft(const double *Xr, int64_t nr, int d, KParams kp, const TW *Wt,
+                                 int64_t k, const int32_t *pat, int w, double *G, int *status,
+                                 cudaStream_t s)
 {
     size_t smem = sizeof(double) * WM * (WM + 1) +
                   std::max(sizeof(TW) * WM * (KC + 1), sizeof(double) * WM);
-    auto kfn = fsai_kernel<WM, TW>;
+    auto kfn = fsai_kernel<WM, TW, FT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "fsai smem attribute");
@@ -162,6 +163,26 @@ static afn_status launch_fsai(const double *Xr, int64_t nr, int d, KParams kp, c
     }
     AFN_CUDA(cudaGetLastError());
     return AFN_OK;
+}
+
+// the FSAI rows with the autotuned block size (each run writes the same G)
+template <int WM, class TW>
+static afn_status launch_fsai(const double *Xr, int64_t nr, int d, KParams kp, const TW *Wt,
+                              int64_t k, const int32_t *pat, int w, double *G, int *status,
+                              cudaStream_t s)
+{
+    constexpr int FA = WM <= 64 ? 128 : 256;
+    char key[96];
+    snprintf(key, sizeof(key), "fsai/wm%d/%s/k2^%d/nr2^%d/%s", WM, sizeof(TW) == 8 ? "f64" : "f32",
+             log2_bucket(k), log2_bucket(nr), tune_device_tag().c_str());
+    afn_status st = AFN_OK;
+    auto run = [&](int c) {
+        st = c == 0 ? launch_fsai_ft<WM, TW, FA>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s)
+                    : launch_fsai_ft<WM, TW, 2 * FA>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+    };
+    const int c = tune_pick(key, 2, run, s, 1);
+    run(c);
+    return st;
 }
 
 template <class TW>

@@ -1187,9 +1187,9 @@ int persistent_grid(int ctas_per_sm, double share)
     return g > 0 ? g : 1;
 }
 
-afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share)
+afn_status group_matvec32(const GDev *gd, cudaStream_t s, double share, int cps)
 {
-    gmv32_kernel<<<persistent_grid(GMV32_MINB, share), 256, 0, s>>>(gd);
+    gmv32_kernel<<<persistent_grid(cps > 0 ? cps : GMV32_MINB, share), 256, 0, s>>>(gd);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AFN_OK : cuda_fail(e, "grouped matvec32 launch");
 }

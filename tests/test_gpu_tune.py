@@ -1,0 +1,76 @@
+"""The autotuner on the GPU: the first call with a shape records a choice
+under its key, and every candidate gives bit-identical results (row warps of
+the tcgen05 matvec, threads per CTA of the FSAI build, CTAs per SM of the
+grouped kernels), so what the tuner picks never changes a result."""
+import numpy as np
+import pytest
+
+from paper_2304_05460_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def afn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_05460_gb300 import afn as a
+    return a
+
+
+def _keys(afn, prefix):
+    return [k for k in afn.afn_tune_entries() if k.startswith(prefix)]
+
+
+def test_matvec_row_warp_split_bit_identical(afn):
+    X = inputs.normal_points(3000, 8, 91)
+    P = inputs.rhs(3000, 32, 92)
+    q0 = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.PREC_MIXED)
+    keys = _keys(afn, "mv32u/ds8/nb4/ker0/")
+    assert keys, afn.afn_tune_entries()
+    out = []
+    for c in (0, 1):
+        for k in keys:
+            afn.afn_tune_put(k, c)
+        out.append(afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.PREC_MIXED))
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], q0)
+
+
+def test_fsai_block_size_bit_identical(afn):
+    X = inputs.uniform_points(2500, 3, 93)
+    h = afn.afn_build(X, afn.GAUSSIAN, 0.1, 1e-3, 250, 32, precision=afn.PREC_MIXED)
+    afn.afn_free(h)
+    keys = _keys(afn, "fsai/wm32/f32/")
+    assert keys
+    gs = []
+    for c in (0, 1):
+        for k in keys:
+            afn.afn_tune_put(k, c)
+        h = afn.afn_build(X, afn.GAUSSIAN, 0.1, 1e-3, 250, 32, precision=afn.PREC_MIXED)
+        gs.append(afn.afn_get_G(h)[1])
+        afn.afn_free(h)
+    assert np.array_equal(gs[0], gs[1])
+
+
+def test_grouped_grid_sizes_bit_identical(afn):
+    systems, rhs = [], []
+    for i, (n, d) in enumerate([(900, 3), (1400, 5), (600, 8)]):
+        X = inputs.normal_points(n, d, 95 + i)
+        systems.append(dict(points=X, kernel=afn.GAUSSIAN, l=1.0 * np.sqrt(d), mu=1e-2,
+                            k_max=n // 4, fsai_nnz=16))
+        rhs.append(inputs.rhs(n, 8, 98 + i))
+    b = afn.afn_build_batched(systems, precision=afn.PREC_MIXED)
+    xs0, _ = afn.afn_solve_batched(b, rhs, 1e-6)
+    afn.afn_batch_free(b)
+    keys = _keys(afn, "gmv32/") + _keys(afn, "gapply/")
+    assert keys
+    for c in (0, 2):
+        for k in keys:
+            afn.afn_tune_put(k, c)
+        b = afn.afn_build_batched(systems, precision=afn.PREC_MIXED)
+        xs, _ = afn.afn_solve_batched(b, rhs, 1e-6)
+        afn.afn_batch_free(b)
+        for a, c_ in zip(xs0, xs):
+            assert np.array_equal(a, c_)
