@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--only", default="",
-                    help="'batched', 'serving' or 'clusters': run that workload alone")
+                    help="'batched', 'serving', 'clusters' or 'paper3d': run that workload alone")
+    ap.add_argument("--paper-kernel", default="both", choices=["both", "gaussian", "matern"])
+    ap.add_argument("--paper-kmax", type=int, default=20000)
     ap.add_argument("--alg5-steps", type=int, default=1,
                     help="steps of the workload under the paper's Alg. 5 strategy (0 = skip)")
     ap.add_argument("--sequential", action="store_true",
@@ -537,6 +539,62 @@ def run_clusters(afn, stream):
                          "at n = 200k, 64 columns); measured once outside the default run"}
 
 
+# ------------------------------------------------- the paper's 3-D cube --
+# AFN iteration counts the paper prints for these columns (Table 1a, 1b); its runs
+# use an H^2 matvec, other random points and FP64 arithmetic: context, not a target
+PAPER_AFN_ITERS_GAUSSIAN = (3, 35, 37, 38, 40, 42, 46, 50, 57, 62, 1)
+PAPER_AFN_ITERS_MATERN = (3, 6, 6, 6, 7, 7, 7, 7, 7, 6, 9)
+
+
+def run_paper3d(afn, stream, which="both", k_max=20000, precision=None):
+    """The paper's synthetic 3-D setting (Sec. 5, Table 1): n = 160,000 points
+    U[0, n^(1/3)]^3, mu = 1e-4, one U[-0.5, 0.5] right-hand side, tol 1e-4,
+    Alg. 5 (Alg. 4 estimate; the Nystrom preconditioner below k = 2000, AFN
+    with min(k, k_max) landmarks above), FSAI with w = 100, every Gaussian l^2
+    and Matern-3/2 1/l column of Table 1.  Reports k, the branch, iterations,
+    build and solve times per column beside the paper's AFN iterations."""
+    import torch
+    from paper_2304_05460_gb300 import inputs
+    s = inputs.paper_cube_3d()
+    Xd = torch.tensor(s.X, device="cuda")
+    Bd = torch.tensor(np.ascontiguousarray(s.B), device="cuda")
+    prec = afn.PREC_MIXED if precision is None else precision
+    rows = []
+    cases = []
+    if which in ("both", "gaussian"):
+        cases += [(afn.GAUSSIAN, "l2", v, float(np.sqrt(v)), p) for v, p in
+                  zip(inputs.PAPER_GAUSSIAN_L2, PAPER_AFN_ITERS_GAUSSIAN)]
+    if which in ("both", "matern"):
+        cases += [(afn.MATERN32, "inv_l", v, 1.0 / v, p) for v, p in
+                  zip(inputs.PAPER_MATERN_INV_L, PAPER_AFN_ITERS_MATERN)]
+    o = afn.options(precision=prec, precond=afn.PRECOND_AUTO, rank_mode=afn.RANK_ESTIMATE,
+                    rank_subsample=1000, seed=1006, max_iter=500, stream=stream)
+    for ker, lab, v, l, paper_it in cases:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = afn.afn_build(Xd, ker, l, s.mu, k_max, s.w, o)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        x, info = afn.afn_solve(h, Bd, 1e-4)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        bi = h.info
+        rows.append({"kernel": "gaussian" if ker == afn.GAUSSIAN else "matern32", lab: v,
+                     "k": int(bi.k), "k_estimate_r": int(bi.rank_r),
+                     "precond": "nystrom" if bi.precond == afn.PRECOND_NYSTROM else "afn",
+                     "iters": int(info["iters"][0]), "converged": int(info["converged"]),
+                     "relres": float(info["relres"][0]), "build_s": t1 - t0, "solve_s": t2 - t1,
+                     "paper_afn_iters": paper_it})
+        afn.afn_free(h)
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return {"workload": "paper_cube_3d: n=160000 U[0, n^(1/3)]^3, mu=1e-4, 1 RHS U[-0.5,0.5], "
+                        "tol 1e-4, Alg. 5 with Alg. 4 k capped at %d, w=100" % k_max,
+            "precision": "mixed" if prec == afn.PREC_MIXED else "fp64-accurate (DF)",
+            "rows": rows,
+            "note": "paper_afn_iters: Table 1 of the paper (H^2 matvec, other points, FP64); "
+                    "context only"}
+
+
 # ------------------------------------------------------------ one column --
 def run_one_rhs(afn, s, Xd, Bd, stream, opts):
     """The n = 50k, d = 8 workload with one right-hand side per system: the four
@@ -651,6 +709,8 @@ def main():
             out = run_batched(afn, args.batched, args.fp64_sample, stream)
         elif args.only == "clusters":
             out = run_clusters(afn, stream)
+        elif args.only == "paper3d":
+            out = run_paper3d(afn, stream, args.paper_kernel, args.paper_kmax)
         else:
             out = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4))
         print(json.dumps({"only": args.only, args.only: out}), flush=True)

@@ -111,7 +111,11 @@ typedef struct {
                                   form r_{k+1}^T (z_{k+1} - z_k) / r_k^T z_k (Notay 2000), which
                                   tolerates the FP32 apply being inexact; 0 = the textbook
                                   Fletcher-Reeves beta; default 0 */
-    int32_t pad_;
+    int32_t schur_order;       /* order of the Schur rows X_r, which defines "numbered less
+                                  than i" of the FSAI pattern (Sec. 3.1): 0 = ascending original
+                                  index; 1 = maximin, farthest point sampling continued over
+                                  all n points after the k landmarks (the screening-effect
+                                  ordering, Sec. 3.1; needs FPS landmarks); default 0 */
 } afn_options;
 
 typedef enum {

@@ -43,7 +43,7 @@ class afn_options(C.Structure):
                 ("check_every", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
                 ("precond", C.c_int32), ("precond_threshold", C.c_int32),
                 ("factors", C.c_int32), ("apply_tc", C.c_int32), ("flexible", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("schur_order", C.c_int32)]
 
 
 class afn_build_info(C.Structure):

@@ -362,12 +362,19 @@ static afn_status build_impl(Handle *h, const double *points)
     }
     h->w = (int)std::max<int64_t>(1, std::min<int64_t>(h->w_req, std::max<int64_t>(nr, 1)));
 
-    // landmarks (Alg. 2: FPS when d <= 10, uniform otherwise, or forced)
+    // landmarks (Alg. 2: FPS when d <= 10, uniform otherwise, or forced); with the
+    // maximin Schur order FPS continues over all n points and its order is the permutation
+    int pol = h->opt.landmarks;
+    if (pol == AFN_LM_AUTO) pol = (d <= 10) ? AFN_LM_FPS : AFN_LM_UNIFORM;
+    const bool maximin = h->opt.schur_order == 1 && h->precond == AFN_PRECOND_AFN && k > 0;
+    if (maximin && pol != AFN_LM_FPS) {
+        set_error("schur_order = 1 (maximin) needs FPS landmarks");
+        return AFN_ERR_ARG;
+    }
+    const int64_t kf = maximin ? n : k;     // FPS steps
     DevBuf lm;
-    AFN_TRY(lm.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(k, 1)));
+    AFN_TRY(lm.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(kf, 1)));
     if (k > 0) {
-        int pol = h->opt.landmarks;
-        if (pol == AFN_LM_AUTO) pol = (d <= 10) ? AFN_LM_FPS : AFN_LM_UNIFORM;
         if (pol == AFN_LM_FPS) {
             Scope sc(&h->prof, K_FPS);
             int64_t start = h->opt.fps_start;
@@ -382,7 +389,7 @@ static afn_status build_impl(Handle *h, const double *points)
                 set_error("fps_start %lld out of range", (long long)start);
                 return AFN_ERR_ARG;
             }
-            AFN_TRY(fps_run(X0, n, d, k, start, lm.as<int64_t>(), st + 1, s));
+            AFN_TRY(fps_run(X0, n, d, kf, start, lm.as<int64_t>(), st + 1, s));
         } else {
             std::vector<int64_t> hl;
             uniform_sample_host(n, k, h->opt.seed, hl);
@@ -392,7 +399,7 @@ static afn_status build_impl(Handle *h, const double *points)
     }
     AFN_TRY(h->perm.alloc(sizeof(int64_t) * (size_t)n));
     log.mark("landmarks");
-    AFN_TRY(build_perm(lm.as<int64_t>(), k, n, h->perm.as<int64_t>(), s));
+    AFN_TRY(build_perm(lm.as<int64_t>(), kf, n, h->perm.as<int64_t>(), s));
     AFN_TRY(h->X64.alloc(sizeof(double) * (size_t)(n * d)));
     AFN_TRY(gather_points(X0, h->perm.as<int64_t>(), n, d, h->X64.as<double>(), s));
     const double *Xk = h->X64.as<double>();
@@ -557,6 +564,10 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         set_error("bad factors %d", o.factors);
         return AFN_ERR_ARG;
     }
+    if (o.schur_order != 0 && o.schur_order != 1) {
+        set_error("bad schur_order %d", o.schur_order);
+        return AFN_ERR_ARG;
+    }
     if (o.flexible != 0 && o.flexible != 1) {
         set_error("bad flexible %d", o.flexible);
         return AFN_ERR_ARG;
@@ -693,7 +704,7 @@ void afn_default_options(afn_options *o)
     o->factors = AFN_FACTORS_FP32;
     o->apply_tc = 2;
     o->flexible = 0;
-    o->pad_ = 0;
+    o->schur_order = 0;
 }
 
 const char *afn_last_error(void) { return g_err; }

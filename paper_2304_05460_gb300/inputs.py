@@ -20,6 +20,11 @@ Workloads (points drawn first, then right-hand sides; seed 1000 + c):
 * ``serving_stream``   Poisson arrivals, n = floor(exp U[ln 1e3, ln 1e5]),
   d in {3, 8, 16}, kernel 50/50 Gaussian / Matern-3/2, l and mu as above,
   1..16 RHS.
+* ``paper_cube_3d``    the setting of the paper's synthetic 3-D experiments
+  (Sec. 5, Tables 1-2): n = 160,000 points U[0, n^(1/3)]^3, mu = 1e-4, one
+  U[-0.5, 0.5] right-hand side, tol 1e-4; Gaussian l^2 and Matern-3/2 1/l
+  taken from the tables' columns, w = 100 (the tables' FSAI with 100
+  neighbours).  Seed 1006.
 
 The median pairwise distance is exact (all i<j pairs, lower median) for
 n <= 2048 and estimated from 10^5 seeded random pairs above that.
@@ -123,6 +128,20 @@ def clusters_3d(n=200_000, nrhs=64, seed=1003, k=2000, w=50):
     X = np.concatenate([Xc, Xu])[g.permutation(n)]
     B = np.asfortranarray(g.standard_normal((nrhs, n)).T)
     return System("clusters_3d", X, B, MATERN32, 0.05, 1e-3, k, w)
+
+
+# the length-scale columns of the paper's Table 1 (a: Gaussian l^2, b: Matern-3/2 1/l)
+PAPER_GAUSSIAN_L2 = (1000.0, 65.0, 60.0, 55.0, 50.0, 45.0, 40.0, 35.0, 30.0, 25.0, 0.1)
+PAPER_MATERN_INV_L = (1.0, 0.065, 0.060, 0.055, 0.050, 0.045, 0.040, 0.035, 0.030, 0.025, 0.001)
+
+
+def paper_cube_3d(n=160_000, seed=1006):
+    """Points U[0, n^(1/3)]^3 and one U[-0.5, 0.5] right-hand side (Sec. 5)."""
+    g = rng(seed)
+    X = g.uniform(0.0, n ** (1.0 / 3.0), size=(n, 3))
+    B = np.asfortranarray(g.uniform(-0.5, 0.5, size=(1, n)).T)
+    return System("paper_cube_3d", X, B, GAUSSIAN, 1.0, 1e-4, 20000, 100, rank_mode="estimate",
+                  seed=seed)
 
 
 def _random_system(g, idx, n, d, kernel, nrhs, seed_base, name, w=32):

@@ -75,7 +75,7 @@ def test_default_options():
     assert o.inner_tol == 0.01 and o.fps_start == 0
     # Alg. 5 fields sit after the stream pointer; AFN is the default preconditioner
     assert (o.precond, o.precond_threshold) == (afn.PRECOND_AFN, 0)
-    assert (o.factors, o.apply_tc, o.flexible) == (afn.FACTORS_FP32, 2, 0)
+    assert (o.factors, o.apply_tc, o.flexible, o.schur_order) == (afn.FACTORS_FP32, 2, 0, 0)
     assert ctypes.sizeof(afn.afn_options) == 88
     assert ctypes.sizeof(afn.afn_build_info) == 96
 
@@ -93,7 +93,7 @@ def test_bad_factor_and_apply_options_rejected_without_gpu():
     from paper_2304_05460_gb300 import afn
     X = np.zeros((4, 3))
     for kw in (dict(factors=2), dict(factors=-1), dict(apply_tc=3), dict(apply_tc=-1),
-               dict(flexible=3)):
+               dict(flexible=3), dict(schur_order=2)):
         with pytest.raises(afn.AfnError) as e:
             afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, 2, **kw)
         assert e.value.status == afn.AFN_ERR_ARG

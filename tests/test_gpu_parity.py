@@ -250,6 +250,35 @@ def test_build_mixed_fp64_factors(afn, n, d, ker, l, mu, k, w):
     afn.afn_free(h)
 
 
+@pytest.mark.parametrize("ker,d,l,w", [(G, 3, 0.15, 32), (M32, 8, 2.5, 50)])
+def test_build_maximin_schur_order(afn, ker, d, l, w):
+    # schur_order = 1: the Schur rows in the order FPS continued over all points picks
+    # them (the maximin ordering of the screening-effect argument, Sec. 3.1).  The oracle
+    # runs the same definition: its full FPS order, then Alg. 2 on the points taken in that
+    # order with the first k as landmarks.  FP64: permutation and pattern bit-exact, L and
+    # G within 1e-10, iteration counts within +-2
+    n, k, mu = 3000, 300, 1e-3
+    X = inputs.uniform_points(n, d, 860 + d)
+    order = oracle.fps(X, n, 0)
+    ref = oracle.afn_build(X[order], ker, l, mu, k, w, landmarks=np.arange(k))
+    h = afn.afn_build(X, ker, l, mu, k, w, precision=afn.PREC_FP64, schur_order=1)
+    assert np.array_equal(afn.afn_get_perm(h), order)
+    pat, Gv = afn.afn_get_G(h)
+    assert np.array_equal(pat, ref["pattern"])
+    assert _cmp(afn.afn_get_L(h), ref["L"], 0) <= 1e-10
+    assert _cmp(Gv, ref["G"], 0) <= 1e-10
+    b = inputs.rhs(n, 1, 870 + d)
+    xr, itr, relr, st_ = oracle.pcg(ref, b[order, 0], 1e-6)
+    x, info = afn.afn_solve(h, b, 1e-6)
+    assert abs(int(info["iters"][0]) - itr) <= 2, (info["iters"], itr)
+    assert oracle.true_relres(X, ker, l, mu, x, b).max() <= 1e-6
+    afn.afn_free(h)
+    with pytest.raises(afn.AfnError) as e:
+        afn.afn_build(X, ker, l, mu, k, w, precision=afn.PREC_FP64, schur_order=1,
+                      landmarks=afn.LM_UNIFORM)
+    assert e.value.status == afn.AFN_ERR_ARG
+
+
 def test_build_mixed_close_to_oracle(afn):
     X = inputs.uniform_points(1200, 3, 700)
     ref = oracle.afn_build(X, G, 0.1, 1e-3, 120, 24)
