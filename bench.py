@@ -71,7 +71,7 @@ def parse():
                     help="systems of the batched workload (0 = skip)")
     ap.add_argument("--fp64-sample", type=int, default=24,
                     help="batched systems solved one at a time in plain FP64 for comparison")
-    ap.add_argument("--serving", type=int, default=40,
+    ap.add_argument("--serving", type=int, default=24,
                     help="requests of the serving stream (0 = skip)")
     ap.add_argument("--serving-rate", type=float, default=-0.8,
                     help="Poisson arrival rate, requests/s (0 = all requests at t = 0; "

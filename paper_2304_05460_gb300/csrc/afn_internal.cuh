@@ -140,6 +140,7 @@ struct Handle {
     DevBuf gt_ptr;    // int32 [nr+1]  CSR of G^T (column c's entries, ascending row)
     DevBuf gt_row;    // int32 [nnz]
     DevBuf gt_slot;   // int32 [nnz]   index into the ELL arrays (row*w + p)
+    DevBuf gtv, gtv32;  // double / float [nnz]  G's values in the order of the G^T lists
     DevBuf status;    // int [4] device status words
 
     // solve workspace (grown on demand)
@@ -254,6 +255,8 @@ size_t apply_tmp_elems(const Handle *h, int nrhs);
 // tiled images of W for the tcgen05 apply of a mixed handle (no-op when they
 // exist, the handle has no W, or its option apply_tc is 0)
 afn_status apply_tc_prepare(Handle *h, cudaStream_t s);
+// the values of G (and of its FP32 copy) in the order of the G^T column lists
+afn_status make_gt_values(Handle *h, cudaStream_t s);
 // the Nystrom factors of a handle whose L (chol(K11 + nu I)) and Bn are set:
 // Lc = chol(mu I + B^T B) and its triangular inverses (FP32 copies for mixed
 // handles)

@@ -176,49 +176,107 @@ __global__ void spmv_gt_kernel(const T *__restrict__ G, const int32_t *__restric
 }
 
 // Row-major forms of the two sparse products for many right-hand sides: one
-// warp per row, lanes over columns; the pattern index and value of each
-// nonzero are one broadcast load, the gathered row is one coalesced read.
+// warp per row, lanes over columns.  The row's (index, value) entries are
+// loaded 32 at a time by the warp in one coalesced read and handed out by
+// shuffles; each entry is then one coalesced gather of the row of t (or y)
+// it names, four gathers in flight per lane.  Each output is the sum over the
+// row's entries in slot order, the same as a sequential loop.
+template <class T, int CB>
+__device__ __forceinline__ void sparse_row_rm(const int32_t *__restrict__ idx, const T *__restrict__ val,
+                                              int m, int nrhs, const T *__restrict__ src,
+                                              T *__restrict__ dst)
+{
+    const int lane = threadIdx.x & 31;
+    for (int cb = 0; cb < nrhs; cb += CB) {
+        const int c = cb + lane;
+        const bool on = c < nrhs;
+        T s = 0;
+        for (int p0 = 0; p0 < m; p0 += 32) {
+            const int cnt = min(32, m - p0);
+            const int32_t jl = lane < cnt ? idx[p0 + lane] : 0;
+            const T gl = lane < cnt ? val[p0 + lane] : (T)0;
+            int p = 0;
+            for (; p + 4 <= cnt; p += 4) {
+                const int32_t j0 = __shfl_sync(0xffffffffu, jl, p), j1 = __shfl_sync(0xffffffffu, jl, p + 1);
+                const int32_t j2 = __shfl_sync(0xffffffffu, jl, p + 2), j3 = __shfl_sync(0xffffffffu, jl, p + 3);
+                const T g0 = __shfl_sync(0xffffffffu, gl, p), g1 = __shfl_sync(0xffffffffu, gl, p + 1);
+                const T g2 = __shfl_sync(0xffffffffu, gl, p + 2), g3 = __shfl_sync(0xffffffffu, gl, p + 3);
+                T v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+                if (on) {
+                    v0 = src[(int64_t)j0 * nrhs + c];
+                    v1 = src[(int64_t)j1 * nrhs + c];
+                    v2 = src[(int64_t)j2 * nrhs + c];
+                    v3 = src[(int64_t)j3 * nrhs + c];
+                }
+                s += g0 * v0;
+                s += g1 * v1;
+                s += g2 * v2;
+                s += g3 * v3;
+            }
+            for (; p < cnt; ++p) {
+                const int32_t j = __shfl_sync(0xffffffffu, jl, p);
+                const T g = __shfl_sync(0xffffffffu, gl, p);
+                if (on) s += g * src[(int64_t)j * nrhs + c];
+            }
+        }
+        if (on) dst[c] = s;
+    }
+}
+
 template <class T>
 __global__ void spmv_ell_rm_kernel(const T *__restrict__ G, const int32_t *__restrict__ pat,
                                    int64_t nr, int w, int nrhs, const T *__restrict__ trm,
                                    T *__restrict__ yrm)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (i >= nr) return;
-    for (int cb = 0; cb < nrhs; cb += 32) {
-        const int c = cb + lane;
-        T s = 0;
-        for (int p = 0; p < w; ++p) {
-            const int32_t j = pat[i * w + p];
-            if (j < 0) break;
-            const T g = G[i * w + p];
-            if (c < nrhs) s += g * trm[(int64_t)j * nrhs + c];
-        }
-        if (c < nrhs) yrm[i * nrhs + c] = s;
-    }
+    // used slots: i + 1 for the short first rows, w after them (diagonal last)
+    const int m = (int)min((int64_t)w, i + 1);
+    sparse_row_rm<T, 32>(pat + i * w, G + i * w, m, nrhs, trm, yrm + i * nrhs);
 }
 
+// s = G^T y through the column lists of G (ascending row), with the values
+// copied into list order (gtv) so that each entry is read where it is listed
 template <class T>
-__global__ void spmv_gt_rm_kernel(const T *__restrict__ G, const int32_t *__restrict__ ptr,
-                                  const int32_t *__restrict__ row,
-                                  const int32_t *__restrict__ slot, int64_t nr, int nrhs,
+__global__ void spmv_gt_rm_kernel(const T *__restrict__ gtv, const int32_t *__restrict__ ptr,
+                                  const int32_t *__restrict__ row, int64_t nr, int nrhs,
                                   const T *__restrict__ yrm, T *__restrict__ orm)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (j >= nr) return;
     const int32_t q0 = ptr[j], q1 = ptr[j + 1];
-    for (int cb = 0; cb < nrhs; cb += 32) {
-        const int c = cb + lane;
-        T s = 0;
-        for (int32_t q = q0; q < q1; ++q) {
-            const int32_t r = row[q];
-            const T g = G[slot[q]];
-            if (c < nrhs) s += g * yrm[(int64_t)r * nrhs + c];
-        }
-        if (c < nrhs) orm[j * nrhs + c] = s;
+    sparse_row_rm<T, 32>(row + q0, gtv + q0, q1 - q0, nrhs, yrm, orm + j * nrhs);
+}
+
+// gtv[q] = G[slot[q]]: the values of G in the order of the column lists
+template <class T>
+__global__ void gt_values_kernel(const T *__restrict__ G, const int32_t *__restrict__ slot,
+                                 int64_t nnz, T *__restrict__ gtv)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nnz) gtv[q] = G[slot[q]];
+}
+
+afn_status make_gt_values(Handle *h, cudaStream_t s)
+{
+    const int64_t nr = h->nr;
+    if (nr <= 0 || !h->gt_ptr.p) return AFN_OK;
+    int32_t nnz = 0;
+    AFN_CUDA(cudaMemcpyAsync(&nnz, h->gt_ptr.as<int32_t>() + nr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AFN_CUDA(cudaStreamSynchronize(s));
+    const unsigned g = (unsigned)((nnz + 255) / 256);
+    if (h->G.p && h->precision != AFN_PREC_MIXED) {     // the FP64 apply
+        AFN_TRY(h->gtv.alloc(sizeof(double) * (size_t)std::max(nnz, 1)));
+        if (nnz) gt_values_kernel<double><<<g, 256, 0, s>>>(h->G.as<double>(), h->gt_slot.as<int32_t>(), nnz,
+                                                            h->gtv.as<double>());
     }
+    if (h->G32.p) {
+        AFN_TRY(h->gtv32.alloc(sizeof(float) * (size_t)std::max(nnz, 1)));
+        if (nnz) gt_values_kernel<float><<<g, 256, 0, s>>>(h->G32.as<float>(), h->gt_slot.as<int32_t>(), nnz,
+                                                           h->gtv32.as<float>());
+    }
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
 }
 
 // out[i*cols + c] = in[c*ldin + i]  (column-major -> row-major), 32x32 tiles
@@ -828,8 +886,9 @@ afn_status afn_apply(const Handle *h, const T *Linv, const T *LinvT, const T *Wt
             unsigned gw = (unsigned)((nr + 7) / 8);
             cm_to_rm_kernel<T><<<tg, tb, 0, st>>>(t, nr, nr, nrhs, trm);
             spmv_ell_rm_kernel<T><<<gw, 256, 0, st>>>(G, h->pat.as<int32_t>(), nr, w, nrhs, trm, y);
-            spmv_gt_rm_kernel<T><<<gw, 256, 0, st>>>(G, h->gt_ptr.as<int32_t>(), h->gt_row.as<int32_t>(),
-                                                     h->gt_slot.as<int32_t>(), nr, nrhs, y, trm);
+            const T *gtv = reinterpret_cast<const T *>(std::is_same<T, float>::value ? h->gtv32.p : h->gtv.p);
+            spmv_gt_rm_kernel<T><<<gw, 256, 0, st>>>(gtv, h->gt_ptr.as<int32_t>(), h->gt_row.as<int32_t>(),
+                                                     nr, nrhs, y, trm);
             rm_to_cm_kernel<T><<<tg, tb, 0, st>>>(trm, nr, nrhs, s2, n);
         } else {
             unsigned g = (unsigned)((tot + 255) / 256);

@@ -166,7 +166,7 @@ int64_t Handle::device_bytes() const
 {
     const DevBuf *b[] = {&perm, &X64, &X32, &Xdf, &L, &Linv, &LinvT, &Linv32, &LinvT32, &Wt, &Wt32, &Wu1, &Wu2, &Wb1, &Wb2,
                          &Bn, &Bn32, &LcInv, &LcInvT, &LcInv32, &LcInvT32,
-                         &pat, &G, &G32, &gt_ptr, &gt_row, &gt_slot, &status, &ws};
+                         &pat, &G, &G32, &gt_ptr, &gt_row, &gt_slot, &gtv, &gtv32, &status, &ws};
     int64_t s = 0;
     for (auto x : b) s += (int64_t)x->bytes;
     return s;
@@ -541,6 +541,7 @@ static afn_status build_impl(Handle *h, const double *points)
         AFN_TRY(h->gt_slot.alloc(sizeof(int32_t) * (size_t)(nr * w)));
         AFN_TRY(transpose_pattern(h->pat.as<int32_t>(), nr, w, h->gt_ptr.as<int32_t>(),
                                   h->gt_row.as<int32_t>(), h->gt_slot.as<int32_t>(), s));
+        AFN_TRY(make_gt_values(h, s));
     }
     AFN_CUDA(cudaStreamSynchronize(s));
     log.mark("Gt lists");

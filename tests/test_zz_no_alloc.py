@@ -1,6 +1,7 @@
 """afn_kernel_matvec_noalloc: the FP64 kernel matvec for callers that cannot
-allocate device memory (for example code running during stream capture, or a
-service whose device memory is handed out by its own pool).  Its scratch is a
+allocate device memory (for example a service whose device memory is planned
+up front and handed out by its own pool, or a plug-in that must not grow its
+host process's device footprint).  Its scratch is a
 fixed array inside the library, so the test checks that two calls in a row --
 which share and reuse that array -- each give the same result as the
 allocating entry point afn_kernel_matvec, within the FP64 matvec tolerance
