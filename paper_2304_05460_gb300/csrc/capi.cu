@@ -498,10 +498,14 @@ static afn_status build_impl(Handle *h, const double *points)
             AFN_TRY(h->LinvT32.alloc(sizeof(float) * (size_t)(k * k)));
             AFN_TRY(tri_inverse32(L32.as<float>(), k, h->Linv32.as<float>(), h->LinvT32.as<float>(), s));
             if (nr > 0) {
+                // W^T = K21 L^{-T}: the kernel block, then one tiled product with the
+                // triangular inverse (the same operator as the triangular solve)
                 AFN_TRY(h->Wt32.alloc(sizeof(float) * (size_t)(nr * k)));
+                DevBuf K21;
+                AFN_TRY(K21.alloc(sizeof(float) * (size_t)(nr * k)));
                 const float *X32 = h->X32.as<float>();
-                AFN_TRY(kernel_block32(X32 + k * ds, nr, X32, k, h->dp, h->kernel, h->Wt32.as<float>(), k, s));
-                AFN_TRY(trsm_right_lt32(L32.as<float>(), k, h->Wt32.as<float>(), nr, s));
+                AFN_TRY(kernel_block32(X32 + k * ds, nr, X32, k, h->dp, h->kernel, K21.as<float>(), k, s));
+                AFN_TRY(gemm_upper32(K21.as<float>(), nr, k, h->LinvT32.as<float>(), h->Wt32.as<float>(), s));
             }
             AFN_CUDA(cudaStreamSynchronize(s));
         }

@@ -347,6 +347,100 @@ afn_status tri_inverse32(const float *L, int64_t k, float *Linv, float *LinvT, c
     return tri_inverse<float>(L, k, Linv, LinvT, s);
 }
 
+// ------------------------------------------------------------------ SGEMM --
+// C = A B in FP32 on the CUDA cores: A (M x K) and B (K x N) row-major, C
+// (M x N) row-major.  UPPER: B is upper triangular (B[q][p] = 0 for q > p),
+// so column block [n0, n0 + 128) needs only q < n0 + 128.  128 x 128 tiles,
+// 8-deep K slices double-buffered in shared memory, 8 x 8 outputs per thread;
+// each output is the sum over q in ascending order.
+static constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
+
+template <bool UPPER>
+__global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A, int64_t lda,
+                                                    const float *__restrict__ B, int64_t ldb,
+                                                    float *__restrict__ C, int64_t ldc, int64_t M,
+                                                    int64_t N, int64_t K)
+{
+    __shared__ __align__(16) float As[2][SG_BK][SG_BM];
+    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * SG_BM, n0 = (int64_t)blockIdx.x * SG_BN;
+    const int64_t kend = UPPER ? min(K, n0 + SG_BN) : K;
+    // this thread's loads: A rows m0 + tid / 2, K-elements (tid % 2) * 4 + u;
+    // B row tid / 32 of the slice, columns (tid % 32) * 4 + u
+    const int am = tid / 2, ak = (tid % 2) * 4;
+    const int bk = tid / 32, bn = (tid % 32) * 4;
+    float ra[4], rb[4];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t gm = m0 + am, gk = k0 + ak + u;
+            ra[u] = (gm < M && gk < kend) ? A[gm * lda + gk] : 0.f;
+            const int64_t gq = k0 + bk, gp = n0 + bn + u;
+            rb[u] = (gq < kend && gp < N) ? B[gq * ldb + gp] : 0.f;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            As[buf][ak + u][am] = ra[u];
+            Bs[buf][bk][bn + u] = rb[u];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const int nt = (int)((kend + SG_BK - 1) / SG_BK);
+    if (nt > 0) {
+        fetch(0);
+        stash(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nt) fetch((int64_t)(t + 1) * SG_BK);
+#pragma unroll
+        for (int kk = 0; kk < SG_BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        if (t + 1 < nt) {
+            stash(buf ^ 1);     // the other buffer was last read before the previous barrier
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t gp = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (gp < N) C[gm * ldc + gp] = acc[i][j];
+        }
+    }
+}
+
+// C (m x k) = A (m x k) U with U (k x k) upper triangular, FP32, row-major
+afn_status gemm_upper32(const float *A, int64_t m, int64_t k, const float *U, float *C, cudaStream_t s)
+{
+    if (m <= 0 || k <= 0) return AFN_OK;
+    dim3 g((unsigned)((k + SG_BN - 1) / SG_BN), (unsigned)((m + SG_BM - 1) / SG_BM));
+    sgemm_kernel<true><<<g, 256, 0, s>>>(A, k, U, k, C, k, m, k, k);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
 // ------------------------------------------------------------- conversion --
 __global__ void cvt64to32_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n)
 {

@@ -288,6 +288,10 @@ def test_build_mixed_close_to_oracle(afn):
     assert np.array_equal(pat, ref["pattern"])
     assert _cmp(afn.afn_get_L(h), ref["L"], 0) <= 1e-10      # Cholesky stays FP64
     assert _cmp(Gv, ref["G"], 0) <= 1e-2                      # FP32 Schur blocks
+    # W^T = K21 L^{-T} from the FP32 kernel block and the FP32 triangular inverse
+    W = np.linalg.solve(ref["L"], ref["K12"]).T
+    errw = _cmp(afn.afn_get_W(h), W, 0)
+    assert errw <= 1e-3, errw
 
 
 @pytest.mark.parametrize("n,k,nrhs", [(3001, 300, 32), (2600, 130, 16), (3001, 300, 48)])
