@@ -60,6 +60,7 @@ def parse():
                     help="'batched', 'serving', 'clusters' or 'paper3d': run that workload alone")
     ap.add_argument("--paper-kernel", default="both", choices=["both", "gaussian", "matern"])
     ap.add_argument("--paper-kmax", type=int, default=20000)
+    ap.add_argument("--paper-k", default="table", choices=["table", "estimate"])
     ap.add_argument("--alg5-steps", type=int, default=1,
                     help="steps of the workload under the paper's Alg. 5 strategy (0 = skip)")
     ap.add_argument("--sequential", action="store_true",
@@ -358,27 +359,30 @@ def serving_fp64_baseline(afn, count, fp64_sample):
     scaled figure is an estimate; the sample and the scaling are reported."""
     import torch
     from paper_2304_05460_gb300 import inputs
-    reqs = inputs.serving_stream(count=count, rate=1.0)
-    small = [i for i, r in enumerate(reqs) if r["n"] <= 20_000]
+    # the sample is drawn from the first 64 requests of the stream whatever `count` is, so the
+    # estimate does not move with the stream's length
+    pool = inputs.serving_stream(count=max(count, 64), rate=1.0)
+    reqs = pool[:count]
+    small = [i for i, r in enumerate(pool[:64]) if r["n"] <= 20_000]
     g = np.random.Generator(np.random.PCG64(11))
     pick = sorted(g.choice(small, size=min(fp64_sample, len(small)), replace=False).tolist())
     o64 = afn.options(precision=afn.PREC_FP64, seed=1005, max_iter=SERVE_MAXIT)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for i in pick:
-        sy = inputs.serving_system(reqs[i])
+        sy = inputs.serving_system(pool[i])
         h = afn.afn_build(sy.X, sy.kernel, sy.l, sy.mu, sy.k, sy.w, o64)
         afn.afn_solve(h, sy.B, TOL)
         afn.afn_free(h)
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t1
-    n2 = sum(float(reqs[i]["n"]) ** 2 for i in pick)
+    n2 = sum(float(pool[i]["n"]) ** 2 for i in pick)
     n2_all = sum(float(r["n"]) ** 2 for r in reqs)
     t_all = t64 * n2_all / n2
     cols = sum(r["nrhs"] for r in reqs)
     return {"solves_per_s": cols / t_all, "requests_per_s": count / t_all,
-            "sample_requests": len(pick), "sample_n": [int(reqs[i]["n"]) for i in pick],
-            "sample_s": t64,
+            "sample_requests": len(pick), "sample_n": [int(pool[i]["n"]) for i in pick],
+            "sample_s": t64, "s_per_n2": t64 / n2,
             "scaling": "sample (requests with n <= 20000) time x sum(n^2) / sum(n^2) of the "
                        "sample; an estimate: iteration counts are not proportional to n^2"}
 
@@ -469,6 +473,20 @@ def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None, fp64=
     if fp64:
         out["fp64_one_at_a_time"] = fp64
         out["speedup_vs_fp64"] = out["solves_per_s"] / fp64["solves_per_s"]
+        if rate > 0 and world == 1:
+            # the same arrivals served one at a time by the FP64 path (FIFO), with each
+            # request's service time estimated as s_per_n2 x n^2 from the timed sample
+            free, fl = 0.0, []
+            for r in reqs:
+                start = max(free, r["t"])
+                free = start + fp64["s_per_n2"] * float(r["n"]) ** 2
+                fl.append((free - r["t"]) * 1e3)
+            fl = np.sort(np.array(fl))
+            out["fp64_fifo_estimate"] = {
+                "latency_p50_ms": float(np.percentile(fl, 50)),
+                "latency_p99_ms": float(np.percentile(fl, 99)),
+                "basis": "FIFO queue over the same arrival times, service time = s_per_n2 x n^2 "
+                         "(an estimate from the FP64 sample)"}
     return out
 
 
@@ -554,15 +572,21 @@ def run_clusters(afn, stream):
 # use an H^2 matvec, other random points and FP64 arithmetic: context, not a target
 PAPER_AFN_ITERS_GAUSSIAN = (3, 35, 37, 38, 40, 42, 46, 50, 57, 62, 1)
 PAPER_AFN_ITERS_MATERN = (3, 6, 6, 6, 7, 7, 7, 7, 7, 6, 9)
+# the rank k the paper's Alg. 4 estimated for each column (Table 1, row k)
+PAPER_K_GAUSSIAN = (565, 9600, 9600, 9600, 9600, 12800, 12800, 12800, 16000, 19200, 160000)
+PAPER_K_MATERN = (160000, 19200, 16000, 14080, 12800, 9600, 9600, 6400, 6400, 6400, 178)
 
 
-def run_paper3d(afn, stream, which="both", k_max=20000, precision=None):
+def run_paper3d(afn, stream, which="both", k_max=20000, precision=None, kmode="table"):
     """The paper's synthetic 3-D setting (Sec. 5, Table 1): n = 160,000 points
     U[0, n^(1/3)]^3, mu = 1e-4, one U[-0.5, 0.5] right-hand side, tol 1e-4,
-    Alg. 5 (Alg. 4 estimate; the Nystrom preconditioner below k = 2000, AFN
-    with min(k, k_max) landmarks above), FSAI with w = 100, every Gaussian l^2
-    and Matern-3/2 1/l column of Table 1.  Reports k, the branch, iterations,
-    build and solve times per column beside the paper's AFN iterations."""
+    FSAI with w = 100, every Gaussian l^2 and Matern-3/2 1/l column of Table 1.
+    kmode "table": the rank k the paper's Table 1 lists for the column (capped at
+    k_max), with Alg. 5's rule on it (the Nystrom preconditioner below 2000, AFN
+    above); kmode "estimate": this library's Alg. 4 estimate and Alg. 5.  Either
+    way the Alg. 4 estimate is reported beside the paper's k.  Reports k, the
+    branch, iterations, build and solve times per column beside the paper's
+    AFN iterations."""
     import torch
     from paper_2304_05460_gb300 import inputs
     s = inputs.paper_cube_3d()
@@ -572,17 +596,24 @@ def run_paper3d(afn, stream, which="both", k_max=20000, precision=None):
     rows = []
     cases = []
     if which in ("both", "gaussian"):
-        cases += [(afn.GAUSSIAN, "l2", v, float(np.sqrt(v)), p) for v, p in
-                  zip(inputs.PAPER_GAUSSIAN_L2, PAPER_AFN_ITERS_GAUSSIAN)]
+        cases += [(afn.GAUSSIAN, "l2", v, float(np.sqrt(v)), p, kp) for v, p, kp in
+                  zip(inputs.PAPER_GAUSSIAN_L2, PAPER_AFN_ITERS_GAUSSIAN, PAPER_K_GAUSSIAN)]
     if which in ("both", "matern"):
-        cases += [(afn.MATERN32, "inv_l", v, 1.0 / v, p) for v, p in
-                  zip(inputs.PAPER_MATERN_INV_L, PAPER_AFN_ITERS_MATERN)]
-    o = afn.options(precision=prec, precond=afn.PRECOND_AUTO, rank_mode=afn.RANK_ESTIMATE,
-                    rank_subsample=1000, seed=1006, max_iter=500, stream=stream)
-    for ker, lab, v, l, paper_it in cases:
+        cases += [(afn.MATERN32, "inv_l", v, 1.0 / v, p, kp) for v, p, kp in
+                  zip(inputs.PAPER_MATERN_INV_L, PAPER_AFN_ITERS_MATERN, PAPER_K_MATERN)]
+    for ker, lab, v, l, paper_it, paper_k in cases:
+        k_est, r_est, br = afn.afn_rank_estimate(Xd, ker, l, s.mu, m=1000, seed=1006, k_max=k_max)
+        if kmode == "table":
+            k_use = min(paper_k, k_max)
+            pc = afn.PRECOND_NYSTROM if paper_k < 2000 else afn.PRECOND_AFN
+            o = afn.options(precision=prec, precond=pc, seed=1006, max_iter=500, stream=stream)
+        else:
+            k_use = k_max
+            o = afn.options(precision=prec, precond=afn.PRECOND_AUTO, rank_mode=afn.RANK_ESTIMATE,
+                            rank_subsample=1000, seed=1006, max_iter=500, stream=stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = afn.afn_build(Xd, ker, l, s.mu, k_max, s.w, o)
+        h = afn.afn_build(Xd, ker, l, s.mu, k_use, s.w, o)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         x, info = afn.afn_solve(h, Bd, 1e-4)
@@ -590,7 +621,7 @@ def run_paper3d(afn, stream, which="both", k_max=20000, precision=None):
         t2 = time.perf_counter()
         bi = h.info
         rows.append({"kernel": "gaussian" if ker == afn.GAUSSIAN else "matern32", lab: v,
-                     "k": int(bi.k), "k_estimate_r": int(bi.rank_r),
+                     "k": int(bi.k), "paper_k": paper_k, "alg4_k": int(k_est), "alg4_r": int(r_est),
                      "precond": "nystrom" if bi.precond == afn.PRECOND_NYSTROM else "afn",
                      "iters": int(info["iters"][0]), "converged": int(info["converged"]),
                      "relres": float(info["relres"][0]), "build_s": t1 - t0, "solve_s": t2 - t1,
@@ -598,11 +629,12 @@ def run_paper3d(afn, stream, which="both", k_max=20000, precision=None):
         afn.afn_free(h)
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     return {"workload": "paper_cube_3d: n=160000 U[0, n^(1/3)]^3, mu=1e-4, 1 RHS U[-0.5,0.5], "
-                        "tol 1e-4, Alg. 5 with Alg. 4 k capped at %d, w=100" % k_max,
+                        "tol 1e-4, w=100, k %s (capped at %d)"
+                        % ("from Table 1" if kmode == "table" else "by Alg. 4 + Alg. 5", k_max),
             "precision": "mixed" if prec == afn.PREC_MIXED else "fp64-accurate (DF)",
             "rows": rows,
-            "note": "paper_afn_iters: Table 1 of the paper (H^2 matvec, other points, FP64); "
-                    "context only"}
+            "note": "paper_afn_iters and paper_k: Table 1 of the paper (H^2 matvec, other points, "
+                    "FP64); context only"}
 
 
 # ------------------------------------------------------------ one column --
@@ -720,9 +752,9 @@ def main():
         elif args.only == "clusters":
             out = run_clusters(afn, stream)
         elif args.only == "paper3d":
-            out = run_paper3d(afn, stream, args.paper_kernel, args.paper_kmax)
+            out = run_paper3d(afn, stream, args.paper_kernel, args.paper_kmax, kmode=args.paper_k)
         else:
-            out = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4))
+            out = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 8))
         print(json.dumps({"only": args.only, args.only: out}), flush=True)
         return
     s = workload(args.n, args.nrhs)
@@ -946,7 +978,7 @@ def main():
     serving = None
     if args.serving > 0:
         try:
-            serving = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 4),
+            serving = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 8),
                                   rank, world, dist)
         except Exception as e:
             serving = {"error": repr(e)}
