@@ -473,21 +473,33 @@ static void launch_u_any(const float *Xs, int64_t n, float *Xpr, const uint32_t 
     char key[96];
     snprintf(key, sizeof(key), "mv32u/ds%d/nb%d/ker%d/n2^%d/%s", DS, NB, KER, log2_bucket(n),
              tune_device_tag().c_str());
-    auto run = [&](int c) {
-        if (c == 1) launch_u<DS, NB, KER, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
-        else launch_u<DS, NB, KER, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
-    };
-    const int uh = tune_pick(key, 2, run, s, 0);
-    run(uh);
+    if constexpr (NB == 8) {
+        // 64 columns: two row warps per lane quarter, each folding 32 columns
+        launch_u<DS, NB, KER, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+        return;
+    } else {
+        auto run = [&](int c) {
+            if (c == 1) launch_u<DS, NB, KER, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+            else launch_u<DS, NB, KER, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
+        };
+        const int uh = tune_pick(key, 2, run, s, 0);
+        run(uh);
+    }
 }
+
+// columns per launch of the FP32 matvec: 64 on the tcgen05 path (one kernel
+// value feeds all 64), else at most 32
+static int piece_cap(int nrhs) { return (nrhs >= 64 && nrhs % 16 == 0) ? 64 : 32; }
 
 size_t matvec32_scratch(int64_t n, int nrhs)
 {
+    const int cap = piece_cap(nrhs);
     const size_t part = sizeof(float) * (size_t)std::max(pick_js(n), UJS_MAX) *
-                        (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
+                        (size_t)std::min(std::max(nrhs, 1), cap) * (size_t)n;
     const size_t np = (size_t)tc_npad(n);
     const size_t dup = sizeof(f2_t) * np * 18;                     // DS + 2 <= 18
-    const size_t psp = sizeof(uint32_t) * np * TcRow<4>::ROW;
+    // the mma.sync tile's split p rows, or the tcgen05 path's hi/lo halves of cap columns
+    const size_t psp = sizeof(uint32_t) * np * (size_t)std::max(TcRow<4>::ROW, 2 * cap);
     return (part + 255) / 256 * 256 + (dup + 255) / 256 * 256 + psp + 256;
 }
 
@@ -524,7 +536,15 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
 #else
     constexpr bool use_tc = true;
 #endif
-    if constexpr (NR >= 16 && use_tc) {
+    if constexpr (NR == 64) {
+        // only the tcgen05 path takes 64-column pieces
+        constexpr int DS = (D == 3 ? 4 : D);
+        const int64_t tot = tp.npad * NR;
+        ksplit_kernel<NR><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, n, n, tp.npad, tp.Psp);
+        launch_u_any<DS, 8, KER>(Xs, n, reinterpret_cast<float *>(tp.Xdup), tp.Psp, part, tp.jsu,
+                                 tp.chunk_st, tp.npad, tp.err, s);
+        return;
+    } else if constexpr (NR >= 16 && use_tc) {
         if (tp.umma) {
             constexpr int DS = (D == 3 ? 4 : D);
             const int64_t tot = tp.npad * NR;
@@ -556,7 +576,8 @@ static void launch32_nr(int nr, const float *Xs, int64_t n, const float *P, floa
     case 4: launch32<D, 4, KER>(Xs, n, P, part, js, chunk, tp, s); break;
     case 8: launch32<D, 8, KER>(Xs, n, P, part, js, chunk, tp, s); break;
     case 16: launch32<D, 16, KER>(Xs, n, P, part, js, chunk, tp, s); break;
-    default: launch32<D, 32, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    case 32: launch32<D, 32, KER>(Xs, n, P, part, js, chunk, tp, s); break;
+    default: launch32<D, 64, KER>(Xs, n, P, part, js, chunk, tp, s); break;
     }
 }
 
@@ -596,7 +617,7 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
     {
         char *b = static_cast<char *>(scratch);
         const size_t pb = sizeof(float) * (size_t)std::max(js, UJS_MAX) *
-                          (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n;
+                          (size_t)std::min(std::max(nrhs, 1), piece_cap(nrhs)) * (size_t)n;
         f2_t *xd = reinterpret_cast<f2_t *>(b + (pb + 255) / 256 * 256);
         const size_t db = sizeof(f2_t) * (size_t)tp.npad * 18;
         tp.Psp = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(xd) + (db + 255) / 256 * 256);
@@ -614,7 +635,7 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
 #ifdef AFN_NO_TC
         int b = piece(nrhs - c0, 16);
 #else
-        int b = piece(nrhs - c0, 32);
+        int b = piece(nrhs - c0, tp.umma ? piece_cap(nrhs - c0) : 32);
 #endif
         const float *pp = p + (int64_t)c0 * n;
         if (kernel == 0) launch32_d<0>(dp, b, Xs, n, pp, part, js, chunk, tp, s);

@@ -221,8 +221,11 @@ __device__ __forceinline__ void umma_fold(const uint32_t (&v)[C], f2_t *acc, f2_
 //        (c%8)4 + jj%4 for point jj of the stage and column c).
 // Row sums of rows [row0, row0 + 128) leave through part (column-major per
 // chunk, leading dimension n).
+// two CTAs per SM (their TMEM allocations fit together) when the registers allow
+__host__ __device__ constexpr int umma_min_blocks(int uh) { return umma_threads(uh) * 2 * 168 <= 65536 ? 2 : 1; }
+
 template <int DS, int NB, int KER, int UH>
-__global__ void __launch_bounds__(umma_threads(UH), 2)
+__global__ void __launch_bounds__(umma_threads(UH), umma_min_blocks(UH))
     matvec32u_kernel(const float *__restrict__ Xs, int64_t n, const float *__restrict__ Xpr,
                      const uint32_t *__restrict__ Pk, float *__restrict__ part, int64_t chunk_st,
                      int64_t nstage, int *__restrict__ err, uint64_t wait_ns)

@@ -150,8 +150,10 @@ def test_matvec_fp64(afn, n, d, ker, nrhs):
 
 
 @pytest.mark.parametrize("n,d,ker,nrhs", [(257, 3, G, 1), (1000, 8, M32, 3), (2049, 16, G, 32),
-                                          (1500, 2, M32, 7)])
+                                          (1500, 2, M32, 7), (1500, 3, M32, 64), (2049, 8, G, 80),
+                                          (777, 16, G, 64)])
 def test_matvec_fp32(afn, n, d, ker, nrhs):
+    # 64-column pieces (and 64 + 16) run the tcgen05 kernel with N = 64
     X = inputs.normal_points(n, d, 400 + n)
     P = inputs.rhs(n, nrhs, 401 + n)
     l = 0.7 * np.sqrt(d)
