@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <type_traits>
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
@@ -910,7 +911,8 @@ __global__ void __launch_bounds__(NT) matvecdf_kernel(const float2 *__restrict__
                                                       double *__restrict__ part, int64_t chunk,
                                                       int js)
 {
-    __shared__ __align__(16) float sm[MvDfSmem<DS, NR>::v];
+    extern __shared__ __align__(16) float dfsm[];   // MvDfSmem<DS, NR>::v floats
+    float *sm = dfsm;
     __shared__ DfExpTable T;
     df_table_init(T);
     // tiles (row tile, j-chunk), one per CTA or -- with a capped grid -- a
@@ -951,35 +953,37 @@ static void launchdf_nr(int nr, const float2 *Xd, int64_t n, const double *P, do
     const double share = tl_df_share ? tl_df_share->load(std::memory_order_relaxed) : 1.0;
     if (share < 1.0) g = std::min<int64_t>(g, persistent_grid(2, share));
     const unsigned grid = (unsigned)g;
+    auto go = [&](auto nrc) {
+        constexpr int NR = decltype(nrc)::value;
+        const int smem = (int)(sizeof(float) * MvDfSmem<DS, NR>::v);
+        cudaFuncSetAttribute(matvecdf_kernel<DS, NR, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        matvecdf_kernel<DS, NR, KER><<<grid, NT, smem, s>>>(Xd, n, P, n, part, chunk, js);
+    };
     switch (nr) {
-    case 1: matvecdf_kernel<DS, 1, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
-    case 2: matvecdf_kernel<DS, 2, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
-    case 4: matvecdf_kernel<DS, 4, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
-    case 8: matvecdf_kernel<DS, 8, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
-    default: matvecdf_kernel<DS, 16, KER><<<grid, NT, 0, s>>>(Xd, n, P, n, part, chunk, js); break;
+    case 1: go(std::integral_constant<int, 1>{}); break;
+    case 2: go(std::integral_constant<int, 2>{}); break;
+    case 4: go(std::integral_constant<int, 4>{}); break;
+    case 8: go(std::integral_constant<int, 8>{}); break;
+    case 16: go(std::integral_constant<int, 16>{}); break;
+    default: go(std::integral_constant<int, 32>{}); break;
     }
 }
 
 size_t matvecdf_scratch(int64_t n, int nrhs)
 {
-    return sizeof(double) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 16) *
+    return sizeof(double) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 32) *
                (size_t)n + 256;
 }
 
-afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
-                     int nrhs, double *q, void *scratch, size_t scratch_bytes, cudaStream_t s)
+// the double-float matvec in column pieces of at most cap (16 or 32): every
+// column's sum is formed the same way whatever the piece, so the results do
+// not depend on cap
+static void matvec_df_pieces(int cap, const float2 *Xd, int64_t n, int ds, int kernel, double mu,
+                             const double *p, int nrhs, double *q, double *part, int js,
+                             int64_t chunk, cudaStream_t s)
 {
-    if (n <= 0 || nrhs <= 0) return AFN_OK;
-    if (scratch_bytes < matvecdf_scratch(n, nrhs)) {
-        set_error("matvec_df: scratch too small");
-        return AFN_ERR_ARG;
-    }
-    int js;
-    int64_t chunk;
-    chunking(n, js, chunk);
-    double *part = static_cast<double *>(scratch);
     for (int c0 = 0; c0 < nrhs;) {
-        const int b = piece(nrhs - c0, 16);
+        const int b = piece(nrhs - c0, cap);
         const double *pp = p + (int64_t)c0 * n;
         const int key = ds * 2 + kernel;
         switch (key) {
@@ -994,6 +998,32 @@ afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu,
         matvec_finish<double><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
             part, js, b, n, pp, n, q + (int64_t)c0 * n, n, mu);
         c0 += b;
+    }
+}
+
+afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
+                     int nrhs, double *q, void *scratch, size_t scratch_bytes, cudaStream_t s)
+{
+    if (n <= 0 || nrhs <= 0) return AFN_OK;
+    if (scratch_bytes < matvecdf_scratch(n, nrhs)) {
+        set_error("matvec_df: scratch too small");
+        return AFN_ERR_ARG;
+    }
+    int js;
+    int64_t chunk;
+    chunking(n, js, chunk);
+    double *part = static_cast<double *>(scratch);
+    if (nrhs >= 32) {
+        // 16- or 32-column pieces by the autotuner: 32 evaluates each kernel value half as
+        // often, 16 keeps twice the CTAs resident
+        char key[96];
+        snprintf(key, sizeof(key), "mvdf/ds%d/ker%d/n2^%d/%s", ds, kernel, log2_bucket(n),
+                 tune_device_tag().c_str());
+        auto run = [&](int c) { matvec_df_pieces(c == 1 ? 32 : 16, Xd, n, ds, kernel, mu, p, nrhs, q, part,
+                                                 js, chunk, s); };
+        run(tune_pick(key, 2, run, s, 0));
+    } else {
+        matvec_df_pieces(16, Xd, n, ds, kernel, mu, p, nrhs, q, part, js, chunk, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matvec_df launch");

@@ -74,3 +74,18 @@ def test_grouped_grid_sizes_bit_identical(afn):
         afn.afn_batch_free(b)
         for a, c_ in zip(xs0, xs):
             assert np.array_equal(a, c_)
+
+
+def test_double_float_matvec_piece_width_bit_identical(afn):
+    X = inputs.normal_points(2500, 8, 99)
+    P = inputs.rhs(2500, 48, 100)
+    q0 = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
+    keys = _keys(afn, "mvdf/ds8/ker0/")
+    assert keys
+    out = []
+    for c in (0, 1):
+        for k in keys:
+            afn.afn_tune_put(k, c)
+        out.append(afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF))
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], q0)
