@@ -1005,7 +1005,8 @@ def main():
                 "fp64_gpu": fp64,
                 "pcg_iters_max": iters_seen[-len(LS):] if iters_seen else None,
                 "batched": batched, "serving": serving, "clusters_3d": clusters,
-                "normal_8d_1rhs": one_rhs}
+                "normal_8d_1rhs": one_rhs,
+                "autotuner": afn.afn_tune_entries()}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
