@@ -135,21 +135,58 @@ __global__ void sturm_kernel(const double *dg, const double *of, int m, const do
     *out = sturm_count_dev(dg, of, m, sigma);
 }
 
-// largest eigenvalue by bisection on the Sturm count (Gershgorin start)
-__global__ void lmax_kernel(const double *dg, const double *of, int m, double *out)
+// largest eigenvalue by bisection on the Sturm count (Gershgorin start).
+// The bisection takes the same midpoints as a sequential loop, eight levels
+// at a time: thread t of the 255 evaluates the Sturm count at node t of the
+// next eight levels' subtree (its interval reached from [lo, hi] by the same
+// midpoint arithmetic), and thread 0 then walks the subtree.
+__global__ void __launch_bounds__(256) lmax_kernel(const double *dg, const double *of, int m, double *out)
 {
-    double lo = DBL_MAX, hi = -DBL_MAX;
-    for (int i = 0; i < m; ++i) {
-        double rad = (i > 0 ? fabs(of[i - 1]) : 0.0) + (i + 1 < m ? fabs(of[i]) : 0.0);
-        lo = fmin(lo, dg[i] - rad);
-        hi = fmax(hi, dg[i] + rad);
+    __shared__ double slo, shi;
+    __shared__ int done;
+    __shared__ unsigned char top[256];   // count == m at node t (mid is above every eigenvalue)
+    if (threadIdx.x == 0) {
+        double lo = DBL_MAX, hi = -DBL_MAX;
+        for (int i = 0; i < m; ++i) {
+            double rad = (i > 0 ? fabs(of[i - 1]) : 0.0) + (i + 1 < m ? fabs(of[i]) : 0.0);
+            lo = fmin(lo, dg[i] - rad);
+            hi = fmax(hi, dg[i] + rad);
+        }
+        slo = lo;
+        shi = hi;
+        done = 0;
     }
-    for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi)) break;
-        if (sturm_count_dev(dg, of, m, mid) == m) hi = mid; else lo = mid;
+    __syncthreads();
+    for (int round = 0; round < 25 && !done; ++round) {
+        const int t = threadIdx.x;      // node t in 1..255 (BFS order, root 1)
+        if (t >= 1) {
+            // the path from the root: bits of t below its leading one, high to low
+            int depth = 31 - __clz(t);
+            double lo = slo, hi = shi;
+            bool ok = true;
+            for (int b = depth - 1; b >= 0; --b) {
+                const double mid = 0.5 * (lo + hi);
+                if (!(mid > lo && mid < hi)) { ok = false; break; }
+                if ((t >> b) & 1) lo = mid; else hi = mid;
+            }
+            const double mid = 0.5 * (lo + hi);
+            top[t] = (ok && mid > lo && mid < hi && sturm_count_dev(dg, of, m, mid) == m) ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double lo = slo, hi = shi;
+            int node = 1;
+            for (int lev = 0; lev < 8; ++lev) {
+                const double mid = 0.5 * (lo + hi);
+                if (!(mid > lo && mid < hi)) { done = 1; break; }
+                if (top[node]) { hi = mid; node = 2 * node; } else { lo = mid; node = 2 * node + 1; }
+            }
+            slo = lo;
+            shi = hi;
+        }
+        __syncthreads();
     }
-    *out = 0.5 * (lo + hi);
+    if (threadIdx.x == 0) *out = 0.5 * (slo + shi);
 }
 
 // A <- factor * (*base) I - A  (sz x sz)
@@ -284,7 +321,7 @@ afn_status rank_estimate(const double *X, int64_t n, int d, KParams kp, int m, u
     AFN_CUDA(cudaMemcpyAsync(T.p, Ko.p, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
     AFN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     AFN_TRY(tridiagonalize(T.as<double>(), m, dg.as<double>(), of.as<double>(), status, s));
-    lmax_kernel<<<1, 1, 0, s>>>(dg.as<double>(), of.as<double>(), m, lm.as<double>());
+    lmax_kernel<<<1, 256, 0, s>>>(dg.as<double>(), of.as<double>(), m, lm.as<double>());
     // Cholesky of K_o in FPS order with negligible pivots dropped
     AFN_CUDA(cudaMemcpyAsync(Lo.p, Ko.p, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
     const double tiny = (double)m * 2.220446049250313e-16;   // max diag of K_o is 1
