@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--paper-kernel", default="both", choices=["both", "gaussian", "matern"])
     ap.add_argument("--paper-kmax", type=int, default=20000)
     ap.add_argument("--paper-k", default="table", choices=["table", "estimate"])
+    ap.add_argument("--paper-n", type=int, default=160_000)
+    ap.add_argument("--paper-precision", default="auto", choices=["auto", "mixed", "df", "fp64"])
     ap.add_argument("--alg5-steps", type=int, default=1,
                     help="steps of the workload under the paper's Alg. 5 strategy (0 = skip)")
     ap.add_argument("--sequential", action="store_true",
@@ -577,7 +579,7 @@ PAPER_K_GAUSSIAN = (565, 9600, 9600, 9600, 9600, 12800, 12800, 12800, 16000, 192
 PAPER_K_MATERN = (160000, 19200, 16000, 14080, 12800, 9600, 9600, 6400, 6400, 6400, 178)
 
 
-def run_paper3d(afn, stream, which="both", k_max=20000, precision=None, kmode="table"):
+def run_paper3d(afn, stream, which="both", k_max=20000, precision=None, kmode="table", n=160_000):
     """The paper's synthetic 3-D setting (Sec. 5, Table 1): n = 160,000 points
     U[0, n^(1/3)]^3, mu = 1e-4, one U[-0.5, 0.5] right-hand side, tol 1e-4,
     FSAI with w = 100, every Gaussian l^2 and Matern-3/2 1/l column of Table 1.
@@ -589,10 +591,11 @@ def run_paper3d(afn, stream, which="both", k_max=20000, precision=None, kmode="t
     AFN iterations."""
     import torch
     from paper_2304_05460_gb300 import inputs
-    s = inputs.paper_cube_3d()
+    s = inputs.paper_cube_3d(n=n)
     Xd = torch.tensor(s.X, device="cuda")
     Bd = torch.tensor(np.ascontiguousarray(s.B), device="cuda")
-    prec = afn.PREC_MIXED if precision is None else precision
+    prec = afn.PREC_AUTO if precision is None else precision
+    kscale = n / 160_000.0        # Table 1's k scaled to the same k / n on a smaller cube
     rows = []
     cases = []
     if which in ("both", "gaussian"):
@@ -604,7 +607,7 @@ def run_paper3d(afn, stream, which="both", k_max=20000, precision=None, kmode="t
     for ker, lab, v, l, paper_it, paper_k in cases:
         k_est, r_est, br = afn.afn_rank_estimate(Xd, ker, l, s.mu, m=1000, seed=1006, k_max=k_max)
         if kmode == "table":
-            k_use = min(paper_k, k_max)
+            k_use = min(max(1, int(round(paper_k * kscale))), k_max, n)
             pc = afn.PRECOND_NYSTROM if paper_k < 2000 else afn.PRECOND_AFN
             o = afn.options(precision=prec, precond=pc, seed=1006, max_iter=500, stream=stream)
         else:
@@ -622,16 +625,20 @@ def run_paper3d(afn, stream, which="both", k_max=20000, precision=None, kmode="t
         bi = h.info
         rows.append({"kernel": "gaussian" if ker == afn.GAUSSIAN else "matern32", lab: v,
                      "k": int(bi.k), "paper_k": paper_k, "alg4_k": int(k_est), "alg4_r": int(r_est),
+                     "precision": {0: "fp64", 1: "mixed", 2: "df"}.get(int(bi.precision), "?"),
+                     "rho32": float(bi.rho32),
                      "precond": "nystrom" if bi.precond == afn.PRECOND_NYSTROM else "afn",
                      "iters": int(info["iters"][0]), "converged": int(info["converged"]),
                      "relres": float(info["relres"][0]), "build_s": t1 - t0, "solve_s": t2 - t1,
                      "paper_afn_iters": paper_it})
         afn.afn_free(h)
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
-    return {"workload": "paper_cube_3d: n=160000 U[0, n^(1/3)]^3, mu=1e-4, 1 RHS U[-0.5,0.5], "
+    return {"workload": "paper_cube_3d: n=%d U[0, n^(1/3)]^3, mu=1e-4, 1 RHS U[-0.5,0.5], "
                         "tol 1e-4, w=100, k %s (capped at %d)"
-                        % ("from Table 1" if kmode == "table" else "by Alg. 4 + Alg. 5", k_max),
-            "precision": "mixed" if prec == afn.PREC_MIXED else "fp64-accurate (DF)",
+                        % (n, "from Table 1 scaled by n / 160000" if kmode == "table"
+                           else "by Alg. 4 + Alg. 5", k_max),
+            "precision": {afn.PREC_MIXED: "mixed", afn.PREC_AUTO: "auto (mixed or DF per system)",
+                          afn.PREC_DF: "fp64-accurate (DF)", afn.PREC_FP64: "fp64"}[prec],
             "rows": rows,
             "note": "paper_afn_iters and paper_k: Table 1 of the paper (H^2 matvec, other points, "
                     "FP64); context only"}
@@ -752,7 +759,10 @@ def main():
         elif args.only == "clusters":
             out = run_clusters(afn, stream)
         elif args.only == "paper3d":
-            out = run_paper3d(afn, stream, args.paper_kernel, args.paper_kmax, kmode=args.paper_k)
+            prec = {"auto": afn.PREC_AUTO, "mixed": afn.PREC_MIXED, "df": afn.PREC_DF,
+                    "fp64": afn.PREC_FP64}[args.paper_precision]
+            out = run_paper3d(afn, stream, args.paper_kernel, args.paper_kmax, precision=prec,
+                              kmode=args.paper_k, n=args.paper_n)
         else:
             out = run_serving(afn, args.serving, args.serving_rate, min(args.fp64_sample, 8))
         print(json.dumps({"only": args.only, args.only: out}), flush=True)
