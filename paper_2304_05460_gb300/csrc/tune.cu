@@ -23,6 +23,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <vector>
 
 #include "afn_internal.cuh"
 
@@ -131,22 +132,28 @@ int tune_pick(const std::string &key, int ncand, const std::function<void(int)> 
         cudaEventDestroy(a);
         return fallback;
     }
-    float best = 0.f;
-    int bi = fallback;
+    // each candidate: one warm-up run, then the best of three timed runs; the
+    // default is kept unless another candidate is faster by more than 2 %
+    std::vector<float> best((size_t)ncand, -1.f);
     for (int c = 0; c < ncand; ++c) {
         run(c);                       // warm-up (first-launch costs)
-        cudaEventRecord(a, s);
-        run(c);
-        cudaEventRecord(b, s);
-        float ms = 0.f;
-        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(a, s);
+            run(c);
+            cudaEventRecord(b, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (best[c] < 0.f || ms < best[c]) best[c] = ms;
         }
-        if (c == 0 || ms < best) {
-            best = ms;
-            bi = c;
-        }
+    }
+    int bi = fallback;
+    for (int c = 0; c < ncand; ++c) {
+        if (best[c] < 0.f) continue;
+        const float ref = (bi >= 0 && bi < ncand && best[bi] >= 0.f) ? best[bi] : -1.f;
+        if (ref < 0.f || best[c] < 0.98f * ref) bi = c;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
