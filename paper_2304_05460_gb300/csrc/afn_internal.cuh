@@ -45,6 +45,11 @@ void tune_store(const std::string &key, int choice);
 // timing is not possible
 int tune_pick(const std::string &key, int ncand, const std::function<void(int)> &run,
               cudaStream_t s, int fallback);
+// run the work once with the key's candidate: the recorded choice; else, outside
+// a stream capture, the default on the key's first call and then each candidate
+// on one call, timed, until the fastest is recorded (no work is repeated)
+void tune_run(const std::string &key, int ncand, const std::function<void(int)> &run,
+              cudaStream_t s, int fallback);
 
 // device status word values (written by kernels, read by the host)
 enum : int { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_TIMEOUT = 2 };

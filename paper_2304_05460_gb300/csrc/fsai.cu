@@ -180,8 +180,7 @@ static afn_status launch_fsai(const double *Xr, int64_t nr, int d, KParams kp, c
         st = c == 0 ? launch_fsai_ft<WM, TW, FA>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s)
                     : launch_fsai_ft<WM, TW, 2 * FA>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
     };
-    const int c = tune_pick(key, 2, run, s, 1);
-    run(c);
+    tune_run(key, 2, run, s, 1);
     return st;
 }
 

@@ -483,8 +483,7 @@ static void launch_u_any(const float *Xs, int64_t n, float *Xpr, const uint32_t 
             if (c == 1) launch_u<DS, NB, KER, 2>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
             else launch_u<DS, NB, KER, 1>(Xs, n, Xpr, Pk, part, js, chunk_st, nst, err, s);
         };
-        const int uh = tune_pick(key, 2, run, s, 0);
-        run(uh);
+        tune_run(key, 2, run, s, 0);
     }
 }
 
@@ -1021,7 +1020,7 @@ afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu,
                  tune_device_tag().c_str());
         auto run = [&](int c) { matvec_df_pieces(c == 1 ? 32 : 16, Xd, n, ds, kernel, mu, p, nrhs, q, part,
                                                  js, chunk, s); };
-        run(tune_pick(key, 2, run, s, 0));
+        tune_run(key, 2, run, s, 0);
     } else {
         matvec_df_pieces(16, Xd, n, ds, kernel, mu, p, nrhs, q, part, js, chunk, s);
     }

@@ -11,8 +11,12 @@
 // candidate by timing: the first call with a given shape runs every
 // candidate on its own operands (each run overwrites the same outputs with
 // the same values), keeps the fastest, and records the choice under a key of
-// (kernel, shape bucket, device: compute capability and SM count).  Later
-// calls with that key launch the recorded choice directly.  The cache is
+// (kernel, shape bucket, device: compute capability and SM count).  Kernels
+// whose launches are captured into a graph (the grouped solves) are timed
+// candidate by candidate before the capture; the others are tuned on their
+// real calls (tune_run): the first call with a key runs the default, the next
+// ones each candidate once, timed, and then the fastest is recorded, so no
+// work is repeated for tuning.  Later calls launch the recorded choice.  The cache is
 // process-wide and can be persisted to a text file (afn_tune_set_cache):
 // one "key choice" line per entry.  Because every candidate gives the same
 // bits, a result never depends on what the tuner picked.
@@ -34,6 +38,12 @@ struct TuneCache {
     std::mutex mu;
     std::map<std::string, int> m;
     std::string path;        // "" = not persisted
+    // keys being tuned online (tune_run): calls seen, best time per candidate
+    struct Trial {
+        int calls = 0;
+        std::vector<float> ms;
+    };
+    std::map<std::string, Trial> trials;
 };
 
 TuneCache &cache()
@@ -159,6 +169,76 @@ int tune_pick(const std::string &key, int ncand, const std::function<void(int)> 
     cudaEventDestroy(b);
     tune_store(key, bi);
     return bi;
+}
+
+void tune_run(const std::string &key, int ncand, const std::function<void(int)> &run,
+              cudaStream_t s, int fallback)
+{
+    int choice = fallback;
+    if (tune_lookup(key, &choice)) {
+        run(choice);
+        return;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        run(fallback);
+        return;
+    }
+    // the call's candidate: the default on the first call (its first-launch costs stay
+    // out of the comparison), then each candidate once, timed
+    TuneCache &c = cache();
+    int cand;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        TuneCache::Trial &t = c.trials[key];
+        if (t.ms.empty()) t.ms.assign((size_t)ncand, -1.f);
+        const int call = t.calls++;
+        cand = call == 0 ? -1 : (call - 1) % ncand;
+    }
+    if (cand < 0) {
+        run(fallback);
+        return;
+    }
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) {
+        run(cand);
+        return;
+    }
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        run(cand);
+        return;
+    }
+    cudaEventRecord(a, s);
+    run(cand);
+    cudaEventRecord(b, s);
+    float ms = -1.f;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        ms = -1.f;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    bool decide = false;
+    int bi = fallback;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        TuneCache::Trial &t = c.trials[key];
+        if (ms >= 0.f && (t.ms[cand] < 0.f || ms < t.ms[cand])) t.ms[cand] = ms;
+        bool all = true;
+        for (float v : t.ms) all = all && v >= 0.f;
+        if (all || t.calls > 4 * ncand + 1) {
+            for (int q = 0; q < ncand; ++q) {
+                if (t.ms[q] < 0.f) continue;
+                const float ref = (bi >= 0 && bi < ncand && t.ms[bi] >= 0.f) ? t.ms[bi] : -1.f;
+                if (ref < 0.f || t.ms[q] < 0.98f * ref) bi = q;
+            }
+            c.trials.erase(key);
+            decide = true;
+        }
+    }
+    if (decide) tune_store(key, bi);
 }
 
 int log2_bucket(int64_t v)
