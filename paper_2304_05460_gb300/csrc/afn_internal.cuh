@@ -239,6 +239,7 @@ afn_status trsm_right_lt64(const double *L, int64_t k, double *B, int64_t m,
 afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaStream_t s);
 // C (m x k) = A (m x k) U, U (k x k) upper triangular, FP32 row-major (tiled SGEMM)
 afn_status gemm_upper32(const float *A, int64_t m, int64_t k, const float *U, float *C, cudaStream_t s);
+afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s);
 afn_status kernel_block32(const float *Xa, int64_t na, const float *Xb, int64_t nb, int dp,
                           int kernel, float *out, int64_t ld, cudaStream_t s);
 afn_status convert64to32(const double *a, float *b, int64_t count, cudaStream_t s);

@@ -472,9 +472,13 @@ static afn_status build_impl(Handle *h, const double *points)
             AFN_TRY(h->LinvT.alloc(sizeof(double) * (size_t)(k * k)));
             AFN_TRY(tri_inverse64(h->L.as<double>(), k, h->Linv.as<double>(), h->LinvT.as<double>(), s));
             if (nr > 0) {
+                // W^T = K21 L^{-T}: the kernel block, then one tiled product with the
+                // triangular inverse (the same operator as the triangular solve)
                 AFN_TRY(h->Wt.alloc(sizeof(double) * (size_t)(nr * k)));
-                AFN_TRY(kernel_block(Xr, nr, Xk, k, d, kp, 0.0, h->Wt.as<double>(), k, s));
-                AFN_TRY(trsm_right_lt64(h->L.as<double>(), k, h->Wt.as<double>(), nr, s));
+                DevBuf K21;
+                AFN_TRY(K21.alloc(sizeof(double) * (size_t)(nr * k)));
+                AFN_TRY(kernel_block(Xr, nr, Xk, k, d, kp, 0.0, K21.as<double>(), k, s));
+                AFN_TRY(gemm_upper64(K21.as<double>(), nr, k, h->LinvT.as<double>(), h->Wt.as<double>(), s));
             }
             if (mixed) {
                 // FP64 factors rounded to FP32 for the apply of the mixed solves

@@ -431,6 +431,93 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
     }
 }
 
+// The FP64 form: 64 x 64 tiles, 4 x 4 outputs per thread (GB300 retires few
+// FP64 FMAs per cycle, so the tile only needs enough reuse to keep that pipe
+// busy); same loads, same ascending-q sums.
+static constexpr int DG_B = 64, DG_BK = 8;
+
+template <bool UPPER>
+__global__ void __launch_bounds__(256) dgemm_kernel(const double *__restrict__ A, int64_t lda,
+                                                    const double *__restrict__ B, int64_t ldb,
+                                                    double *__restrict__ C, int64_t ldc, int64_t M,
+                                                    int64_t N, int64_t K)
+{
+    __shared__ __align__(16) double As[2][DG_BK][DG_B];
+    __shared__ __align__(16) double Bs[2][DG_BK][DG_B];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * DG_B, n0 = (int64_t)blockIdx.x * DG_B;
+    const int64_t kend = UPPER ? min(K, n0 + DG_B) : K;
+    // loads: A rows m0 + tid / 4, K-elements (tid % 4) * 2 + u; B row tid / 32, columns (tid % 32) * 2 + u
+    const int am = tid / 4, ak = (tid % 4) * 2;
+    const int bk = tid / 32, bn = (tid % 32) * 2;
+    double ra[2], rb[2];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t gm = m0 + am, gk = k0 + ak + u;
+            ra[u] = (gm < M && gk < kend) ? A[gm * lda + gk] : 0.0;
+            const int64_t gq = k0 + bk, gp = n0 + bn + u;
+            rb[u] = (gq < kend && gp < N) ? B[gq * ldb + gp] : 0.0;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            As[buf][ak + u][am] = ra[u];
+            Bs[buf][bk][bn + u] = rb[u];
+        }
+    };
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    const int nt = (int)((kend + DG_BK - 1) / DG_BK);
+    if (nt > 0) {
+        fetch(0);
+        stash(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nt) fetch((int64_t)(t + 1) * DG_BK);
+#pragma unroll
+        for (int kk = 0; kk < DG_BK; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[buf][kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[buf][kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        if (t + 1 < nt) stash(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gp = n0 + tx * 4 + j;
+            if (gp < N) C[gm * ldc + gp] = acc[i][j];
+        }
+    }
+}
+
+// C (m x k) = A (m x k) U with U (k x k) upper triangular, FP64, row-major
+afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s)
+{
+    if (m <= 0 || k <= 0) return AFN_OK;
+    dim3 g((unsigned)((k + DG_B - 1) / DG_B), (unsigned)((m + DG_B - 1) / DG_B));
+    dgemm_kernel<true><<<g, 256, 0, s>>>(A, k, U, k, C, k, m, k, k);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
 // C (m x k) = A (m x k) U with U (k x k) upper triangular, FP32, row-major
 afn_status gemm_upper32(const float *A, int64_t m, int64_t k, const float *U, float *C, cudaStream_t s)
 {
