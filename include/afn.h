@@ -56,8 +56,8 @@ typedef enum {
                                   double-float on the FP32 pipes (matvec_df) */
     AFN_PREC_AUTO = 3          /* per system at build time: MIXED when
                                   rho = 2^-24 max_i sum_j K_ij / mu <= 0.3 (the FP32 matvec
-                                  error stays small next to mu; AFN_AUTO_RHO in the
-                                  environment overrides 0.3), else DF; the handle reports
+                                  error stays small next to mu; the option auto_rho
+                                  overrides 0.3), else DF; the handle reports
                                   the precision chosen and rho (afn_build_info) */
 } afn_precision;
 
@@ -89,8 +89,9 @@ typedef struct {
     int64_t fps_start;         /* FPS start index; -1 = the point nearest the centroid (Alg. 6) */
     uint64_t seed;             /* SplitMix64 seed for uniform landmarks and Alg. 4's subsample */
     int32_t max_iter;          /* PCG iteration cap per column (FP64) / per inner solve; default 500 */
-    int32_t max_outer;         /* mixed precision, restarted refinement only (AFN_REFINE=restart):
-                                  FP64 refinement steps cap; default 10 */
+    int32_t max_outer;         /* mixed precision, restarted refinement only
+                                  (krylov = AFN_KRYLOV_RESTART): FP64 refinement steps cap;
+                                  default 10 */
     double inner_tol;          /* mixed precision: drop of the FP32 recursive residual between
                                   two FP64 residual replacements (delta); default 0.01 */
     int32_t check_every;       /* iterations between host convergence polls; default 4 */
@@ -116,7 +117,23 @@ typedef struct {
                                   index; 1 = maximin, farthest point sampling continued over
                                   all n points after the k landmarks (the screening-effect
                                   ordering, Sec. 3.1; needs FPS landmarks); default 0 */
+    int32_t krylov;            /* mixed handles: the Krylov scheme around the FP32 matvec and
+                                  apply (afn_krylov), default AFN_KRYLOV_FP32 */
+    int32_t pad_;              /* reserved, 0 */
+    double auto_rho;           /* AFN_PREC_AUTO: the largest rho32 that still takes MIXED;
+                                  0 = 0.3 */
 } afn_options;
+
+typedef enum {
+    AFN_KRYLOV_FP32 = 0,       /* one PCG sequence with FP32 vectors (FP64 dots and scalars) and
+                                  reliable updates: the residual replaced by the FP64-accurate
+                                  b - (K + mu I) x once the recursive one fell by inner_tol */
+    AFN_KRYLOV_FP64 = 1,       /* the same reliable updates with FP64 vectors: x, r, z, p, q
+                                  and their updates in FP64, only the matvec and the apply in
+                                  FP32 (their inputs rounded to FP32, outputs widened) */
+    AFN_KRYLOV_RESTART = 2     /* restarted refinement: FP32 PCG on the scaled FP64 residual to
+                                  inner_tol, x updated in FP64, at most max_outer restarts */
+} afn_krylov;
 
 typedef enum {
     AFN_FACTORS_FP32 = 0,      /* K12 from the FP32 points, W = L^{-1} K12 by an FP32 triangular

@@ -28,6 +28,7 @@ MATVEC_DF = PREC_DF        # afn_kernel_matvec: FP64-accurate double-float
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
 FACTORS_FP32, FACTORS_FP64 = 0, 1
+KRYLOV_FP32, KRYLOV_FP64, KRYLOV_RESTART = 0, 1, 2
 
 
 class AfnError(RuntimeError):
@@ -43,7 +44,8 @@ class afn_options(C.Structure):
                 ("check_every", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
                 ("precond", C.c_int32), ("precond_threshold", C.c_int32),
                 ("factors", C.c_int32), ("apply_tc", C.c_int32), ("flexible", C.c_int32),
-                ("schur_order", C.c_int32)]
+                ("schur_order", C.c_int32), ("krylov", C.c_int32), ("pad_", C.c_int32),
+                ("auto_rho", C.c_double)]
 
 
 class afn_build_info(C.Structure):

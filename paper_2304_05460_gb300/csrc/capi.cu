@@ -172,12 +172,7 @@ int64_t Handle::device_bytes() const
     return s;
 }
 
-double auto_rho_limit()
-{
-    const char *e = getenv("AFN_AUTO_RHO");
-    const double v = e ? atof(e) : 0.0;
-    return v > 0.0 ? v : 0.3;
-}
+double auto_rho_limit(const afn_options &o) { return o.auto_rho > 0.0 ? o.auto_rho : 0.3; }
 
 bool is_device_ptr(const void *p)
 {
@@ -417,7 +412,7 @@ static afn_status build_impl(Handle *h, const double *points)
         double rmax = 0.0;
         AFN_TRY(kernel_row_sum_max(h->X32.as<float>(), n, h->dp, h->kernel, &rmax, s));
         h->rho32 = rmax * 0x1p-24 / h->mu;
-        h->precision = h->rho32 <= auto_rho_limit() ? AFN_PREC_MIXED : AFN_PREC_DF;
+        h->precision = h->rho32 <= auto_rho_limit(h->opt) ? AFN_PREC_MIXED : AFN_PREC_DF;
         if (h->precision != AFN_PREC_MIXED) h->X32.release();
     }
     log.mark("points");
@@ -581,6 +576,14 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         set_error("bad flexible %d", o.flexible);
         return AFN_ERR_ARG;
     }
+    if (o.krylov < AFN_KRYLOV_FP32 || o.krylov > AFN_KRYLOV_RESTART) {
+        set_error("bad krylov %d", o.krylov);
+        return AFN_ERR_ARG;
+    }
+    if (!(o.auto_rho >= 0.0)) {
+        set_error("bad auto_rho %g", o.auto_rho);
+        return AFN_ERR_ARG;
+    }
     if (o.apply_tc < 0 || o.apply_tc > 2) {
         set_error("bad apply_tc %d", o.apply_tc);
         return AFN_ERR_ARG;
@@ -714,6 +717,9 @@ void afn_default_options(afn_options *o)
     o->apply_tc = 2;
     o->flexible = 0;
     o->schur_order = 0;
+    o->krylov = AFN_KRYLOV_FP32;
+    o->pad_ = 0;
+    o->auto_rho = 0.0;
 }
 
 const char *afn_last_error(void) { return g_err; }

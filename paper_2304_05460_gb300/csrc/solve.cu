@@ -332,24 +332,12 @@ static afn_status apply32(Handle *h, const float *r, int nrhs, float *z, void *t
                             h->G32.as<float>(), r, nrhs, z, static_cast<float *>(tmp), h->stream);
 }
 
-// AFN_RESID=fp64 computes the residual replacements of mixed handles with
-// the FP64 kernel instead of the double-float one (comparison)
-static bool resid_fp64()
-{
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("AFN_RESID");
-        v = (e && e[0] == 'f') ? 1 : 0;
-    }
-    return v == 1;
-}
-
 // FP64-accurate q = (K + mu I) p: FP64 kernel on FP64 handles, double-float
 // kernel on the FP32 pipes for mixed handles
 static afn_status mv64(Handle *h, const double *p, int nrhs, double *q, const Work &wk)
 {
     Scope sc(&h->prof, K_MATVEC64);
-    if (h->Xdf.p && !resid_fp64())
+    if (h->Xdf.p)
         return matvec_df(h->Xdf.as<float2>(), h->n, stored_dim32(h->dp), h->kernel, h->mu, p, nrhs,
                          q, wk.mv, wk.mv_bytes, h->stream);
     KParams kp{h->kernel, h->l, h->mu};
@@ -500,13 +488,6 @@ __global__ void scale_up_kernel(double *x, const float *x32, const double *rn, c
 
 static unsigned g1(int64_t tot) { return (unsigned)((tot + 255) / 256); }
 
-// AFN_REFINE=restart selects the earlier restarted refinement (comparison)
-static bool legacy_refinement()
-{
-    const char *e = getenv("AFN_REFINE");
-    return e && e[0] == 'r';
-}
-
 __global__ void init_rel_kernel(const double *bnorm, double *rel, int nrhs)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,6 +525,12 @@ __global__ void to32_kernel(const double *a, float *b, int64_t count)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < count) b[e] = (float)a[e];
+}
+
+__global__ void to64_kernel(const float *a, double *b, int64_t count)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < count) b[e] = (double)a[e];
 }
 
 // after a replacement: cs.val = ||b - A x||^2 (FP64); test the true residual
@@ -667,6 +654,78 @@ static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int 
     return AFN_OK;
 }
 
+// The same reliable updates with the Krylov vectors in FP64: x, r, z, p, q,
+// their updates and dots in FP64; only the two operators run in FP32, on
+// their inputs rounded to FP32 (p for the matvec, r for the apply), their
+// outputs widened back to FP64.  Rounding then enters the recurrences only
+// through the operators, not through the vector updates.
+static afn_status mixed_reliable64(Handle *h, Work &wk, int nrhs, double tol, int maxit,
+                                   double *drel, int *steps_out)
+{
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n, tot = n * nrhs;
+    const double delta = h->opt.inner_tol > 0 ? h->opt.inner_tol : 0.05;
+    const bool flexible = h->opt.flexible == 1;
+    const Cols &cs = wk.cs;
+    ru_init_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(cs, nrhs, delta);
+    AFN_CUDA(cudaMemsetAsync(wk.x, 0, sizeof(double) * tot, s));
+    AFN_CUDA(cudaMemcpyAsync(wk.r, wk.b, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+    auto precondition = [&]() -> afn_status {
+        to32_kernel<<<g1(tot), 256, 0, s>>>(wk.r, wk.r32, tot);
+        AFN_TRY(apply32(h, wk.r32, nrhs, wk.z32, wk.tmp));
+        to64_kernel<<<g1(tot), 256, 0, s>>>(wk.z32, wk.z, tot);
+        return AFN_OK;
+    };
+    AFN_TRY(precondition());
+    {
+        Scope sc(&h->prof, K_BLAS1);
+        launch_dot<double>(0, wk.r, wk.z, nullptr, nullptr, n, nrhs, M_RHO0, cs, maxit, s);
+        launch_pupdate<double>(wk.p, wk.z, n, nrhs, cs, 1, s);
+    }
+    const int every = std::max(1, h->opt.check_every);
+    int steps = 0;
+    for (int it = 0; it < maxit + every; ++it) {
+        to32_kernel<<<g1(tot), 256, 0, s>>>(wk.p, wk.p32, tot);
+        AFN_TRY(mv32(h, wk.p32, nrhs, wk.q32, wk));
+        to64_kernel<<<g1(tot), 256, 0, s>>>(wk.q32, wk.q, tot);
+        {
+            Scope sc(&h->prof, K_BLAS1);
+            launch_dot<double>(0, wk.p, wk.q, nullptr, nullptr, n, nrhs, M_ALPHA, cs, maxit, s);
+            launch_dot<double>(1, wk.r, wk.q, wk.x, wk.p, n, nrhs, M_RRU, cs, maxit, s);
+        }
+        if ((it + 1) % every == 0) {
+            int na = 0, nf = 0;
+            AFN_TRY(poll_both(cs, nrhs, h->status.as<int>() + 3, s, &na, &nf));
+            if (na == 0) break;
+            if (nf > 0) {
+                // replacement for every active column: r = b - (K + mu I) x
+                AFN_TRY(mv64(h, wk.x, nrhs, wk.q, wk));
+                residual_kernel<<<g1(tot), 256, 0, s>>>(wk.b, wk.q, wk.r, n, nrhs);
+                launch_dot<double>(0, wk.r, wk.r, nullptr, nullptr, n, nrhs, M_STORE, cs, maxit, s);
+                ru_post_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(cs, nrhs, tol, maxit, drel);
+                ++steps;
+                AFN_TRY(poll_both(cs, nrhs, h->status.as<int>() + 3, s, &na, &nf));
+                if (na == 0) break;
+            }
+        }
+        if (flexible) {
+            Scope sc(&h->prof, K_BLAS1);
+            launch_dot<double>(0, wk.r, wk.z, nullptr, nullptr, n, nrhs, M_SIGMA, cs, maxit, s);
+        }
+        AFN_TRY(precondition());
+        {
+            Scope sc(&h->prof, K_BLAS1);
+            launch_dot<double>(0, wk.r, wk.z, nullptr, nullptr, n, nrhs,
+                               flexible ? M_BETA_PR : M_BETA, cs, maxit, s);
+            launch_pupdate<double>(wk.p, wk.z, n, nrhs, cs, 0, s);
+        }
+    }
+    *steps_out = steps;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
+    return AFN_OK;
+}
+
 afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, double *x_perm,
                      int32_t *iters, double *relres, int *outer, int *converged)
 {
@@ -708,9 +767,12 @@ afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, doub
         AFN_CUDA(cudaMemcpyAsync(x_perm, wk.x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
         AFN_CUDA(cudaMemcpyAsync(hrel.data(), drel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         if (iters) AFN_CUDA(cudaMemcpyAsync(iters, wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
-    } else if (!legacy_refinement()) {
+    } else if (h->opt.krylov != AFN_KRYLOV_RESTART) {
         init_rel_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(wk.cs.bnorm, drel, nrhs);
-        AFN_TRY(mixed_reliable(h, wk, nrhs, tol, maxit, drel, &steps));
+        if (h->opt.krylov == AFN_KRYLOV_FP64)
+            AFN_TRY(mixed_reliable64(h, wk, nrhs, tol, maxit, drel, &steps));
+        else
+            AFN_TRY(mixed_reliable(h, wk, nrhs, tol, maxit, drel, &steps));
         AFN_CUDA(cudaMemcpyAsync(x_perm, wk.x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
         AFN_CUDA(cudaMemcpyAsync(hrel.data(), drel, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         if (iters) AFN_CUDA(cudaMemcpyAsync(iters, wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));

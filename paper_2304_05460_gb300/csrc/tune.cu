@@ -191,10 +191,20 @@ void tune_run(const std::string &key, int ncand, const std::function<void(int)> 
     int cand;
     {
         std::lock_guard<std::mutex> lk(c.mu);
-        TuneCache::Trial &t = c.trials[key];
-        if (t.ms.empty()) t.ms.assign((size_t)ncand, -1.f);
-        const int call = t.calls++;
-        cand = call == 0 ? -1 : (call - 1) % ncand;
+        auto f = c.m.find(key);          // decided by another thread meanwhile
+        if (f != c.m.end()) {
+            cand = -2;
+            choice = f->second;
+        } else {
+            TuneCache::Trial &t = c.trials[key];
+            if (t.ms.empty()) t.ms.assign((size_t)ncand, -1.f);
+            const int call = t.calls++;
+            cand = call == 0 ? -1 : (call - 1) % ncand;
+        }
+    }
+    if (cand == -2) {
+        run(choice);
+        return;
     }
     if (cand < 0) {
         run(fallback);
@@ -224,7 +234,11 @@ void tune_run(const std::string &key, int ncand, const std::function<void(int)> 
     int bi = fallback;
     {
         std::lock_guard<std::mutex> lk(c.mu);
-        TuneCache::Trial &t = c.trials[key];
+        // another thread with the same key may have decided (and dropped the
+        // trial) while this call ran: then there is nothing left to record
+        auto it = c.trials.find(key);
+        if (it == c.trials.end() || it->second.ms.size() != (size_t)ncand) return;
+        TuneCache::Trial &t = it->second;
         if (ms >= 0.f && (t.ms[cand] < 0.f || ms < t.ms[cand])) t.ms[cand] = ms;
         bool all = true;
         for (float v : t.ms) all = all && v >= 0.f;

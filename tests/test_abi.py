@@ -76,8 +76,18 @@ def test_default_options():
     # Alg. 5 fields sit after the stream pointer; AFN is the default preconditioner
     assert (o.precond, o.precond_threshold) == (afn.PRECOND_AFN, 0)
     assert (o.factors, o.apply_tc, o.flexible, o.schur_order) == (afn.FACTORS_FP32, 2, 0, 0)
-    assert ctypes.sizeof(afn.afn_options) == 88
+    assert (o.krylov, o.auto_rho) == (afn.KRYLOV_FP32, 0.0)
+    assert ctypes.sizeof(afn.afn_options) == 104
     assert ctypes.sizeof(afn.afn_build_info) == 96
+
+
+def test_bad_krylov_and_auto_rho_rejected_without_gpu():
+    from paper_2304_05460_gb300 import afn
+    X = np.zeros((4, 3))
+    for kw in (dict(krylov=3), dict(krylov=-1), dict(auto_rho=-0.5), dict(auto_rho=float("nan"))):
+        with pytest.raises(afn.AfnError) as e:
+            afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, 2, **kw)
+        assert e.value.status == afn.AFN_ERR_ARG
 
 
 def test_bad_precond_rejected_without_gpu():

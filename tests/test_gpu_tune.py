@@ -97,3 +97,36 @@ def test_double_float_matvec_piece_width_bit_identical(afn):
         out.append(afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF))
     assert np.array_equal(out[0], out[1])
     assert np.array_equal(out[0], q0)
+
+
+def test_online_tuning_from_concurrent_threads(afn):
+    # several host threads, each on its own stream, make the first calls of one
+    # tuning key at the same time: one of them records the choice while the
+    # others are still timing candidates; every result stays bit-identical
+    import threading
+    import torch
+    afn.afn_tune_clear()
+    X = inputs.normal_points(2000, 8, 103)
+    P = inputs.rhs(2000, 32, 104)
+    ref = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
+    afn.afn_tune_clear()
+    out, errs = [], []
+
+    def work():
+        try:
+            st = torch.cuda.Stream()
+            for _ in range(5):
+                out.append(afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P,
+                                                 precision=afn.MATVEC_DF, stream=st))
+        except BaseException as e:      # reported below
+            errs.append(e)
+    ts = [threading.Thread(target=work) for _ in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs, errs
+    assert len(out) == 40
+    for q in out:
+        assert np.array_equal(q, ref)
+    assert _keys(afn, "mvdf/ds8/ker0/")
