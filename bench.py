@@ -39,6 +39,7 @@ SERVE_MAXIT = 1000   # per request in the serving stream (a request past it repo
 METRIC = "AFN-PCG solves/s at rel. residual 1e-6 (mixed precision, 8-D normal, n=50k, 32 RHS)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES, MUFU_PER_SM, SM_MAX_MHZ = 152, 128, 16, 2070.0
+AUTO_RHO = [0.0]   # AFN_PREC_AUTO's MIXED/DF threshold for the batched and served systems (0 = 0.3)
 LANE_PEAK_TOPS = N_SM * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12    # FP32 lane operations / s
 # DRAM bytes read + written per launch of matvec32u_kernel<8, 4, Gaussian> at n = 50,000,
 # 32 columns, from one ncu capture of that launch; to be re-taken when the kernel changes
@@ -79,6 +80,9 @@ def parse():
     ap.add_argument("--serving-rate", type=float, default=-0.8,
                     help="Poisson arrival rate, requests/s (0 = all requests at t = 0; "
                          "negative: that multiple of the measured FP64 one-at-a-time rate)")
+    ap.add_argument("--auto-rho", type=float, default=0.0,
+                    help="MIXED/DF threshold of AFN_PREC_AUTO for the batched and served "
+                         "systems (0 = the library's 0.3)")
     ap.add_argument("--clusters", type=int, default=1,
                     help="1 = run the n = 200k clustered 64-RHS workload (0 = skip)")
     ap.add_argument("--one-rhs", type=int, default=1,
@@ -285,7 +289,8 @@ def run_batched(afn, count, fp64_sample, stream, rank=0, world=1, dist=None):
                   k_max=s.k, fsai_nnz=s.w) for s in systems]
     rhs = [torch.tensor(np.ascontiguousarray(s.B), device="cuda") for s in systems]
     cols = sum(s.nrhs for s in systems)
-    opt = dict(seed=1004, max_iter=MAXIT, check_every=4, precision=afn.PREC_AUTO)
+    opt = dict(seed=1004, max_iter=MAXIT, check_every=4, precision=afn.PREC_AUTO,
+               auto_rho=AUTO_RHO[0])
 
     def once():
         torch.cuda.synchronize()
@@ -418,7 +423,7 @@ def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None, fp64=
     args_ = [dict(points=s.X, kernel=s.kernel, l=s.l, mu=s.mu, k_max=s.k, fsai_nnz=s.w)
              for s in systems]
     cols = sum(s.nrhs for s in systems)
-    srv = afn.Server(seed=1005, max_iter=SERVE_MAXIT, build_threads=8)
+    srv = afn.Server(seed=1005, max_iter=SERVE_MAXIT, build_threads=8, auto_rho=AUTO_RHO[0])
     # warm-up request (graph capture, pool growth), not counted
     wid = srv.submit(args_[0], systems[0].B, TOL)
     while not srv.poll(wait_ms=100):
@@ -543,9 +548,9 @@ def run_clusters(afn, stream):
     ap_bytes = 2 * 2.0 * k * nr + 2 * 8.0 * nr * w + 2 * 4.0 * k * (k + 1) / 2 + 2 * 4.0 * n * 64
     ap_avg = ap_ms / max(ap_cnt, 1)
     mv_cnt, mv_ms = st["matvec32"]
-    mv_avg = mv_ms / max(mv_cnt, 1)          # one 64-column matvec = two 32-column launches
-    ops_pair = 2 * 4 + 4 + 32                # d-hat = 4: 2 d-hat + Matern's sqrt/scale + 32 columns
-    mv_ops = 2.0 * float(n) * n * ops_pair
+    mv_avg = mv_ms / max(mv_cnt, 1)          # one 64-column launch per matvec (tcgen05, N = 64)
+    ops_pair = 2 * 4 + 4 + 64                # d-hat = 4: 2 d-hat + Matern's sqrt/scale + 64 columns
+    mv_ops = float(n) * n * ops_pair
     return {"workload": "clusters_3d: n=200000 d=3 (3 clusters sigma=0.1 + 20%% uniform), "
                         "Matern-3/2 l=0.05, mu=1e-3, k=2000 FPS, w=50, 64 RHS N(0,1), tol 1e-6, "
                         "mixed precision, BF16 tensor-core W products",
@@ -738,6 +743,7 @@ def main():
     args = parse()
     global LS
     LS = tuple(float(v) for v in args.ls.split(","))
+    AUTO_RHO[0] = args.auto_rho
     if args.impl == "reference":
         return run_reference(args)
     import torch

@@ -199,10 +199,16 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
 size_t matvec32_scratch(int64_t n, int nrhs);
 int pad_dim(int d);
 int stored_dim32(int dp);
-// FP64-accurate q = (K + mu I) p on the FP32 pipes (double-float), from
-// prescaled double-float points (make_points_df, n x ds)
+// FP64-accurate q = (K + mu I) p from prescaled double-float points
+// (make_points_df, n x ds): kernel values in double-float on the FP32 pipes;
+// the sum over j in double-float on the same pipes below DFU_MIN_COLS columns,
+// else exact on the tensor cores (BF16 digit splitting, matvec_dfu.cuh).
+// err: device word set to DEV_TIMEOUT if a bounded wait of the tensor-core
+// kernel runs out
+static constexpr int DFU_MIN_COLS = 8;
 afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
-                     int nrhs, double *q, void *scratch, size_t scratch_bytes, cudaStream_t s);
+                     int nrhs, double *q, void *scratch, size_t scratch_bytes, int *err,
+                     cudaStream_t s);
 size_t matvecdf_scratch(int64_t n, int nrhs);
 afn_status make_points_df(const double *X, int64_t n, int d, int ds, int kernel, double l,
                           float2 *Xd, cudaStream_t s);

@@ -979,8 +979,18 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
         AFN_TRY(make_points_df(X, n, d, ds, kernel, l, xd.as<float2>(), s));
         size_t sb = matvecdf_scratch(n, nrhs);
         AFN_TRY(scratch.alloc(sb));
-        AFN_TRY(matvec_df(xd.as<float2>(), n, ds, kernel, mu, P, nrhs, Q, scratch.p, sb, s));
+        DevBuf flag;
+        AFN_TRY(flag.alloc(sizeof(int)));
+        AFN_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+        AFN_TRY(matvec_df(xd.as<float2>(), n, ds, kernel, mu, P, nrhs, Q, scratch.p, sb,
+                          flag.as<int>(), s));
+        int hf = 0;
+        AFN_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         AFN_CUDA(cudaStreamSynchronize(s));
+        if (hf) {
+            set_error("afn_kernel_matvec: a bounded wait of the double-float matvec ran out");
+            return AFN_ERR_TIMEOUT;
+        }
     } else {
         int dp = pad_dim(d);
         int ds = stored_dim32(dp);

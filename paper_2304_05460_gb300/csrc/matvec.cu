@@ -747,8 +747,10 @@ __global__ void __launch_bounds__(NT) matvec64_kernel(const double *__restrict__
 
 size_t matvec64_scratch(int64_t n, int nrhs)
 {
-    return sizeof(double) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 32) *
-               (size_t)n + 256;
+    // the same scratch serves the double-float matvec of mixed handles
+    return std::max(sizeof(double) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 32) *
+                        (size_t)n + 256,
+                    matvecdf_scratch(n, nrhs));
 }
 
 template <int D>
@@ -820,6 +822,10 @@ __device__ __forceinline__ void df_table_init(DfExpTable &T)
         T.log2e_l = (float)(log2e - (double)T.log2e_h);
     }
 }
+
+}  // namespace afn
+#include "matvec_dfu.cuh"
+namespace afn {
 
 template <int DS, int NR>
 struct MvDfSmem {
@@ -968,10 +974,25 @@ static void launchdf_nr(int nr, const float2 *Xd, int64_t n, const double *P, do
     }
 }
 
+static constexpr int DUJS_MAX = 8;   // j-chunks of the tcgen05 double-float path
+
+// scratch of the tcgen05 double-float matvec: partials (up to DUJS_MAX chunks
+// x 32 columns, FP64), the digit tiles of p, the staged points, column maxima
+// and exponents
+static size_t dfu_scratch(int64_t n)
+{
+    const size_t np = (size_t)((n + DU_J - 1) / DU_J * DU_J);
+    const size_t part = sizeof(double) * (size_t)DUJS_MAX * DU_NR * (size_t)n;
+    const size_t dig = 2 * np * (size_t)(DU_DIG * DU_NR);
+    const size_t pts = sizeof(float2) * np * 16;
+    return (part + 255) / 256 * 256 + (dig + 255) / 256 * 256 + (pts + 255) / 256 * 256 + 1024;
+}
+
 size_t matvecdf_scratch(int64_t n, int nrhs)
 {
-    return sizeof(double) * (size_t)pick_js(n) * (size_t)std::min(std::max(nrhs, 1), 32) *
-               (size_t)n + 256;
+    const size_t cuda_core = sizeof(double) * (size_t)pick_js(n) *
+                                 (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n + 256;
+    return std::max(cuda_core, nrhs >= DFU_MIN_COLS ? dfu_scratch(n) : (size_t)0);
 }
 
 // the double-float matvec in column pieces of at most cap (16 or 32): every
@@ -1000,29 +1021,156 @@ static void matvec_df_pieces(int cap, const float2 *Xd, int64_t n, int ds, int k
     }
 }
 
+// ------------------------------------ double-float on the tensor cores --
+// zero-padded copy of the double-float points for the staged tiles
+__global__ void dupoints_kernel(const float2 *__restrict__ Xd, int64_t n, int ds, int64_t npad,
+                                float2 *__restrict__ Xpr)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < npad * ds) Xpr[e] = e < n * ds ? Xd[e] : make_float2(0.f, 0.f);
+}
+
+// max_j |p_jc| of the nc columns, as the bits of a non-negative double
+__global__ void du_colmax_kernel(const double *__restrict__ p, int64_t n, int nc,
+                                 unsigned long long *__restrict__ mx)
+{
+    const int c = blockIdx.y;
+    double m = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(p[(int64_t)c * n + j]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(mx + c, (unsigned long long)__double_as_longlong(m));
+}
+
+// the digit tiles of p: with 2^E > max_j |p_jc| (frexp), p_jc 2^(7-E) = sum_t
+// b_t 2^(-8t), each digit the nearest integer of the remainder so far (every
+// step exact in FP64); one thread per (stage, column, point)
+__global__ void du_pdigits_kernel(const double *__restrict__ p, int64_t n, int nc, int64_t npad,
+                                  const unsigned long long *__restrict__ mx, int *__restrict__ pexp,
+                                  __nv_bfloat16 *__restrict__ Pd)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npad * DU_NR) return;
+    const int kk = (int)(e % DU_J);
+    const int c = (int)((e / DU_J) % DU_NR);
+    const int64_t st = e / (DU_J * DU_NR);
+    const int64_t j = st * DU_J + kk;
+    int E = 0;
+    double w = 0.0;
+    if (c < nc) {
+        const double m = __longlong_as_double((long long)mx[c]);
+        if (m > 0.0) frexp(m, &E);
+        if (j == 0) pexp[c] = E;
+        if (j < n) w = ldexp(p[(int64_t)c * n + j], 7 - E);
+    }
+    __nv_bfloat16 *tile = Pd + st * (int64_t)(DU_J * DU_DIG * DU_NR);
+#pragma unroll
+    for (int t = 0; t < DU_DIG; ++t) {
+        const double d = rint(w);
+        w = (w - d) * 256.0;
+        tile[du_tile_elem(t * DU_NR + c, kk)] = __double2bfloat16(d);
+    }
+}
+
+// j-chunks (in staged tiles) of the tcgen05 double-float path: the count whose
+// CTAs (one per SM) fill the last wave best, chunks of at least 8 tiles
+static void chunking_du(int64_t n, int64_t nstage, int &js, int64_t &chunk_st)
+{
+    const int64_t rt = (n + UR - 1) / UR;
+    const int64_t slots = num_sms();
+    double best = -1.0;
+    js = 1;
+    chunk_st = nstage;
+    for (int q = 1; q <= DUJS_MAX; ++q) {
+        const int64_t cs = (nstage + q - 1) / q;
+        if (q > 1 && cs < 8) break;
+        const int64_t jq = (nstage + cs - 1) / cs;
+        const int64_t tot = rt * jq;
+        const int64_t waves = (tot + slots - 1) / slots;
+        const double eff = (double)tot / (double)(waves * slots);
+        if (eff > best + 1e-9) {
+            best = eff;
+            js = (int)jq;
+            chunk_st = cs;
+        }
+    }
+}
+
+template <int DS, int KER>
+static void launch_du(const float2 *Xd, int64_t n, const float2 *Xpr, const __nv_bfloat16 *Pd,
+                      const int *pexp, double *part, int nc, int js, int64_t chunk_st,
+                      int64_t nstage, int *err, cudaStream_t s)
+{
+    constexpr int smem = DuStage<DS>::SMEM;
+    cudaFuncSetAttribute(matvecdfu_kernel<DS, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 g((unsigned)((n + UR - 1) / UR), (unsigned)js);
+    matvecdfu_kernel<DS, KER><<<g, DU_THREADS, smem, s>>>(Xd, n, Xpr, Pd, pexp, part, nc, chunk_st,
+                                                          nstage, err, wait_limit_ns());
+}
+
+// the double-float matvec with the contraction on the tensor cores, in pieces
+// of 32 columns (the last one zero-padded)
+static afn_status matvec_dfu(const float2 *Xd, int64_t n, int ds, int kernel, double mu,
+                             const double *p, int nrhs, double *q, void *scratch, int *err,
+                             cudaStream_t s)
+{
+    const int64_t npad = (n + DU_J - 1) / DU_J * DU_J, nstage = npad / DU_J;
+    char *c = static_cast<char *>(scratch);
+    double *part = reinterpret_cast<double *>(c);
+    c += (sizeof(double) * (size_t)DUJS_MAX * DU_NR * (size_t)n + 255) / 256 * 256;
+    __nv_bfloat16 *Pd = reinterpret_cast<__nv_bfloat16 *>(c);
+    c += (2 * (size_t)npad * (DU_DIG * DU_NR) + 255) / 256 * 256;
+    float2 *Xpr = reinterpret_cast<float2 *>(c);
+    c += (sizeof(float2) * (size_t)npad * 16 + 255) / 256 * 256;
+    unsigned long long *mx = reinterpret_cast<unsigned long long *>(c);
+    int *pexp = reinterpret_cast<int *>(c + 512);
+    int js;
+    int64_t chunk_st;
+    chunking_du(n, nstage, js, chunk_st);
+    dupoints_kernel<<<(unsigned)((npad * ds + 255) / 256), 256, 0, s>>>(Xd, n, ds, npad, Xpr);
+    for (int c0 = 0; c0 < nrhs; c0 += DU_NR) {
+        const int nc = std::min(DU_NR, nrhs - c0);
+        const double *pp = p + (int64_t)c0 * n;
+        AFN_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * DU_NR, s));
+        du_colmax_kernel<<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 256), (unsigned)nc), 256, 0, s>>>(
+            pp, n, nc, mx);
+        du_pdigits_kernel<<<(unsigned)((npad * DU_NR + 255) / 256), 256, 0, s>>>(pp, n, nc, npad, mx,
+                                                                                 pexp, Pd);
+        switch (ds * 2 + kernel) {
+        case 8: launch_du<4, 0>(Xd, n, Xpr, Pd, pexp, part, nc, js, chunk_st, nstage, err, s); break;
+        case 9: launch_du<4, 1>(Xd, n, Xpr, Pd, pexp, part, nc, js, chunk_st, nstage, err, s); break;
+        case 16: launch_du<8, 0>(Xd, n, Xpr, Pd, pexp, part, nc, js, chunk_st, nstage, err, s); break;
+        case 17: launch_du<8, 1>(Xd, n, Xpr, Pd, pexp, part, nc, js, chunk_st, nstage, err, s); break;
+        case 32: launch_du<16, 0>(Xd, n, Xpr, Pd, pexp, part, nc, js, chunk_st, nstage, err, s); break;
+        default: launch_du<16, 1>(Xd, n, Xpr, Pd, pexp, part, nc, js, chunk_st, nstage, err, s); break;
+        }
+        const int64_t tot = n * nc;
+        matvec_finish<double><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            part, js, nc, n, pp, n, q + (int64_t)c0 * n, n, mu);
+    }
+    return AFN_OK;
+}
+
 afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
-                     int nrhs, double *q, void *scratch, size_t scratch_bytes, cudaStream_t s)
+                     int nrhs, double *q, void *scratch, size_t scratch_bytes, int *err,
+                     cudaStream_t s)
 {
     if (n <= 0 || nrhs <= 0) return AFN_OK;
     if (scratch_bytes < matvecdf_scratch(n, nrhs)) {
         set_error("matvec_df: scratch too small");
         return AFN_ERR_ARG;
     }
-    int js;
-    int64_t chunk;
-    chunking(n, js, chunk);
-    double *part = static_cast<double *>(scratch);
-    if (nrhs >= 32) {
-        // 16- or 32-column pieces by the autotuner: 32 evaluates each kernel value half as
-        // often, 16 keeps twice the CTAs resident
-        char key[96];
-        snprintf(key, sizeof(key), "mvdf/ds%d/ker%d/n2^%d/%s", ds, kernel, log2_bucket(n),
-                 tune_device_tag().c_str());
-        auto run = [&](int c) { matvec_df_pieces(c == 1 ? 32 : 16, Xd, n, ds, kernel, mu, p, nrhs, q, part,
-                                                 js, chunk, s); };
-        tune_run(key, 2, run, s, 0);
+    if (nrhs >= DFU_MIN_COLS) {
+        // eight or more columns: the contraction on the tensor cores
+        AFN_TRY(matvec_dfu(Xd, n, ds, kernel, mu, p, nrhs, q, scratch, err, s));
     } else {
-        matvec_df_pieces(16, Xd, n, ds, kernel, mu, p, nrhs, q, part, js, chunk, s);
+        int js;
+        int64_t chunk;
+        chunking(n, js, chunk);
+        matvec_df_pieces(16, Xd, n, ds, kernel, mu, p, nrhs, q, static_cast<double *>(scratch), js,
+                         chunk, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matvec_df launch");

@@ -339,7 +339,7 @@ static afn_status mv64(Handle *h, const double *p, int nrhs, double *q, const Wo
     Scope sc(&h->prof, K_MATVEC64);
     if (h->Xdf.p)
         return matvec_df(h->Xdf.as<float2>(), h->n, stored_dim32(h->dp), h->kernel, h->mu, p, nrhs,
-                         q, wk.mv, wk.mv_bytes, h->stream);
+                         q, wk.mv, wk.mv_bytes, h->status.as<int>() + 3, h->stream);
     KParams kp{h->kernel, h->l, h->mu};
     return matvec64(h->X64.as<double>(), h->n, h->d, kp, p, nrhs, q, wk.mv, wk.mv_bytes, h->stream);
 }
@@ -814,6 +814,15 @@ afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, doub
         if (iters) AFN_CUDA(cudaMemcpyAsync(iters, wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
     }
     AFN_CUDA(cudaStreamSynchronize(s));
+    {
+        // a bounded wait of a tensor-core kernel that ran out invalidates the solve
+        int hs = 0;
+        AFN_CUDA(cudaMemcpy(&hs, h->status.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost));
+        if (hs) {
+            set_error("solve: a bounded device wait of a tensor-core kernel ran out");
+            return AFN_ERR_TIMEOUT;
+        }
+    }
     int conv = 0;
     for (int c = 0; c < nrhs; ++c) {
         if (relres) relres[c] = hrel[c];

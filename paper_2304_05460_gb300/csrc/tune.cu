@@ -3,8 +3,7 @@
 // Some launch parameters change only how the work is spread over the GPU,
 // never a result: the number of row warps per TMEM lane quarter of the
 // tcgen05 matvec (each kernel value and each column sum is formed the same
-// way), the column-piece width of the double-float matvec, the CTAs per SM
-// of the persistent grouped kernels (each tile is
+// way), the CTAs per SM of the persistent grouped kernels (each tile is
 // computed the same way by whichever CTA takes it) and the threads per CTA
 // of the FSAI build (each Gram entry and each step of the local Cholesky is
 // the same sum in the same order).  For these the library picks the fastest

@@ -149,6 +149,36 @@ def test_matvec_fp64(afn, n, d, ker, nrhs):
         assert err.max() <= 1e-12, (prec, err.max())
 
 
+@pytest.mark.parametrize("n,d,ker,nrhs", [(1, 3, G, 8), (31, 3, M32, 9), (2049, 16, G, 8),
+                                          (777, 8, M32, 40), (1000, 3, G, 32), (1500, 2, M32, 64),
+                                          (4097, 8, G, 33)])
+def test_matvec_double_float_tensor_core(afn, n, d, ker, nrhs):
+    # eight or more columns: double-float kernel values, the sum over j exact on the
+    # tensor cores (BF16 digits); ragged n, zero-padded last piece, one-point system
+    X = inputs.normal_points(n, d, 350 + n)
+    P = inputs.rhs(n, nrhs, 351 + n)
+    l = 0.7 * np.sqrt(d)
+    ref = oracle.matvec(X, ker, l, 1e-2, P)
+    q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=afn.MATVEC_DF)
+    bound = scale_bound(X, ker, l, 1e-2, P).reshape(q.shape)
+    err = np.abs(q - ref.reshape(q.shape)) / (bound + 1e-300)
+    assert err.max() <= 1e-12, err.max()
+
+
+def test_matvec_double_float_tensor_core_scaled_columns(afn):
+    # columns of very different magnitude (each has its own digit exponent) and a zero column
+    n = 3000
+    X = inputs.normal_points(n, 8, 361)
+    P = inputs.rhs(n, 12, 362) * np.array([1e-200, 1e-8, 1.0, 1e6, 1e150, 0.0, 3.0, 1e-3,
+                                             7.0, 1e-280, 1e280, 0.5])
+    ref = oracle.matvec(X, G, 2.0, 1e-2, P)
+    q = afn.afn_kernel_matvec(X, G, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
+    bound = scale_bound(X, G, 2.0, 1e-2, P).reshape(q.shape)
+    err = np.abs(q - ref.reshape(q.shape)) / (bound + 1e-300)
+    assert np.all(q[:, 5] == 0.0)
+    assert err.max() <= 1e-12, err.max()
+
+
 @pytest.mark.parametrize("n,d,ker,nrhs", [(257, 3, G, 1), (1000, 8, M32, 3), (2049, 16, G, 32),
                                           (1500, 2, M32, 7), (1500, 3, M32, 64), (2049, 8, G, 80),
                                           (777, 16, G, 64)])
@@ -189,6 +219,17 @@ def test_matvec_sampled_rows_full_size(afn):
         ref = oracle.matvec_rows(s.X, G, 2.0, 1e-2, s.B, rows)
         absb = oracle.matvec_rows(s.X, G, 2.0, 1e-2, np.abs(s.B), rows)
         assert np.all(np.abs(q[rows] - ref) <= tolr * absb)
+
+
+def test_matvec_double_float_tensor_core_full_size(afn):
+    # the residual replacement of the headline solve: n = 50k, d = 8, 32 columns, the
+    # tensor-core double-float matvec, on sampled rows (first and last rows included)
+    s = inputs.normal_8d(l=2.0, nrhs=32)
+    rows = _sample_rows(s.n, 40, 12, 12)
+    q = afn.afn_kernel_matvec(s.X, G, 2.0, 1e-2, s.B, precision=afn.MATVEC_DF)
+    ref = oracle.matvec_rows(s.X, G, 2.0, 1e-2, s.B, rows)
+    absb = oracle.matvec_rows(s.X, G, 2.0, 1e-2, np.abs(s.B), rows)
+    assert np.all(np.abs(q[rows] - ref) <= 1e-11 * absb)
 
 
 # ---------------------------------------------------------------- build ---

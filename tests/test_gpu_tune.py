@@ -81,24 +81,6 @@ def test_grouped_grid_sizes_bit_identical(afn):
             assert np.array_equal(a, c_)
 
 
-def test_double_float_matvec_piece_width_bit_identical(afn):
-    X = inputs.normal_points(2500, 8, 99)
-    P = inputs.rhs(2500, 48, 100)
-    q0 = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
-    for _ in range(3):
-        q = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
-        assert np.array_equal(q, q0)
-    keys = _keys(afn, "mvdf/ds8/ker0/")
-    assert keys
-    out = []
-    for c in (0, 1):
-        for k in keys:
-            afn.afn_tune_put(k, c)
-        out.append(afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF))
-    assert np.array_equal(out[0], out[1])
-    assert np.array_equal(out[0], q0)
-
-
 def test_online_tuning_from_concurrent_threads(afn):
     # several host threads, each on its own stream, make the first calls of one
     # tuning key at the same time: one of them records the choice while the
@@ -108,7 +90,7 @@ def test_online_tuning_from_concurrent_threads(afn):
     afn.afn_tune_clear()
     X = inputs.normal_points(2000, 8, 103)
     P = inputs.rhs(2000, 32, 104)
-    ref = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
+    ref = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.PREC_MIXED)
     afn.afn_tune_clear()
     out, errs = [], []
 
@@ -117,7 +99,7 @@ def test_online_tuning_from_concurrent_threads(afn):
             st = torch.cuda.Stream()
             for _ in range(5):
                 out.append(afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P,
-                                                 precision=afn.MATVEC_DF, stream=st))
+                                                 precision=afn.PREC_MIXED, stream=st))
         except BaseException as e:      # reported below
             errs.append(e)
     ts = [threading.Thread(target=work) for _ in range(8)]
@@ -129,4 +111,4 @@ def test_online_tuning_from_concurrent_threads(afn):
     assert len(out) == 40
     for q in out:
         assert np.array_equal(q, ref)
-    assert _keys(afn, "mvdf/ds8/ker0/")
+    assert _keys(afn, "mv32u/ds8/nb4/ker0/")
