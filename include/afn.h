@@ -289,10 +289,18 @@ void afn_tune_clear(void);
  * AFN_PREC_FP64 computes in FP64; AFN_PREC_MIXED evaluates pairs in FP32
  * (points and p rounded to FP32, FP32 accumulation) and returns FP64;
  * AFN_PREC_DF computes FP64-accurate values (kernel values to about 1e-14
- * relative, double-float sums) on the FP32 pipes -- the kernel of the DF
- * solves and of the mixed solves' FP64 residual b - (K + mu I) x.
+ * relative on the FP32 pipes) -- the kernel of the DF solves and of the
+ * mixed solves' FP64 residual b - (K + mu I) x: with at least 8 columns and
+ * 16384 points the sum over j runs exactly on the tensor cores (both
+ * operands split into BF16 base-256 digits, integer products accumulated
+ * exactly in FP32; Ozaki et al. 2012), otherwise in double-float on the FP32
+ * pipes.  AFN_MATVEC_DF_TC takes the tensor-core sum at every size (each
+ * column of p scaled by its own power of two, so columns of any magnitude);
+ * AFN_MATVEC_DF_CC the double-float sum at every size.
  */
 #define AFN_MATVEC_DF AFN_PREC_DF
+#define AFN_MATVEC_DF_TC 4
+#define AFN_MATVEC_DF_CC 5
 afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
                              double mu, const double *p, int32_t nrhs, double *q,
                              int32_t precision, void *stream);

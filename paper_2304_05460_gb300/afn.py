@@ -25,6 +25,7 @@ GAUSSIAN, MATERN32 = 0, 1
 PREC_FP64, PREC_MIXED, PREC_DF, PREC_AUTO = 0, 1, 2, 3
 PRECOND_AFN, PRECOND_NYSTROM, PRECOND_AUTO = 0, 1, 2
 MATVEC_DF = PREC_DF        # afn_kernel_matvec: FP64-accurate double-float
+MATVEC_DF_TC, MATVEC_DF_CC = 4, 5   # ... with the sum over j on the tensor cores / FP32 pipes
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
 FACTORS_FP32, FACTORS_FP64 = 0, 1

@@ -201,14 +201,21 @@ int pad_dim(int d);
 int stored_dim32(int dp);
 // FP64-accurate q = (K + mu I) p from prescaled double-float points
 // (make_points_df, n x ds): kernel values in double-float on the FP32 pipes;
-// the sum over j in double-float on the same pipes below DFU_MIN_COLS columns,
-// else exact on the tensor cores (BF16 digit splitting, matvec_dfu.cuh).
+// the sum over j exact on the tensor cores (BF16 digit splitting,
+// matvec_dfu.cuh) for at least DFU_MIN_COLS columns and DFU_MIN_N points,
+// else in double-float on the FP32 pipes (small systems keep the lighter
+// kernel, which shares the SMs with concurrent solves).
 // err: device word set to DEV_TIMEOUT if a bounded wait of the tensor-core
 // kernel runs out
 static constexpr int DFU_MIN_COLS = 8;
+static constexpr int64_t DFU_MIN_N = 16384;
+inline bool use_dfu(int64_t n, int nrhs) { return nrhs >= DFU_MIN_COLS && n >= DFU_MIN_N; }
+// sum: DF_SUM_AUTO (the rule above), DF_SUM_TC (tensor cores), DF_SUM_CC (FP32 pipes)
+enum : int { DF_SUM_AUTO = 0, DF_SUM_TC = 1, DF_SUM_CC = 2 };
 afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
                      int nrhs, double *q, void *scratch, size_t scratch_bytes, int *err,
-                     cudaStream_t s);
+                     cudaStream_t s, int sum = DF_SUM_AUTO);
+size_t matvecdf_scratch(int64_t n, int nrhs, int sum);
 size_t matvecdf_scratch(int64_t n, int nrhs);
 afn_status make_points_df(const double *X, int64_t n, int d, int ds, int kernel, double l,
                           float2 *Xd, cudaStream_t s);

@@ -954,6 +954,11 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
         set_error("afn_kernel_matvec: invalid argument");
         return AFN_ERR_ARG;
     }
+    if (precision != AFN_PREC_FP64 && precision != AFN_PREC_MIXED && precision != AFN_MATVEC_DF &&
+        precision != AFN_MATVEC_DF_TC && precision != AFN_MATVEC_DF_CC) {
+        set_error("afn_kernel_matvec: bad precision %d", precision);
+        return AFN_ERR_ARG;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     StreamGuard sg(s);
     int64_t tot = n * nrhs;
@@ -972,18 +977,21 @@ afn_status afn_kernel_matvec(const double *points, int64_t n, int32_t d, int32_t
         AFN_TRY(scratch.alloc(sb));
         KParams kp{kernel, l, mu};
         AFN_TRY(matvec64(X, n, d, kp, P, nrhs, Q, scratch.p, sb, s));
-    } else if (precision == AFN_MATVEC_DF) {
+    } else if (precision == AFN_MATVEC_DF || precision == AFN_MATVEC_DF_TC ||
+               precision == AFN_MATVEC_DF_CC) {
+        const int sum = precision == AFN_MATVEC_DF_TC ? DF_SUM_TC
+                        : precision == AFN_MATVEC_DF_CC ? DF_SUM_CC : DF_SUM_AUTO;
         const int ds = stored_dim32(pad_dim(d));
         DevBuf xd;
         AFN_TRY(xd.alloc(sizeof(float2) * n * ds));
         AFN_TRY(make_points_df(X, n, d, ds, kernel, l, xd.as<float2>(), s));
-        size_t sb = matvecdf_scratch(n, nrhs);
+        size_t sb = matvecdf_scratch(n, nrhs, sum);
         AFN_TRY(scratch.alloc(sb));
         DevBuf flag;
         AFN_TRY(flag.alloc(sizeof(int)));
         AFN_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
         AFN_TRY(matvec_df(xd.as<float2>(), n, ds, kernel, mu, P, nrhs, Q, scratch.p, sb,
-                          flag.as<int>(), s));
+                          flag.as<int>(), s, sum));
         int hf = 0;
         AFN_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         AFN_CUDA(cudaStreamSynchronize(s));

@@ -988,12 +988,19 @@ static size_t dfu_scratch(int64_t n)
     return (part + 255) / 256 * 256 + (dig + 255) / 256 * 256 + (pts + 255) / 256 * 256 + 1024;
 }
 
-size_t matvecdf_scratch(int64_t n, int nrhs)
+static bool df_on_tc(int64_t n, int nrhs, int sum)
+{
+    return sum == DF_SUM_TC || (sum == DF_SUM_AUTO && use_dfu(n, nrhs));
+}
+
+size_t matvecdf_scratch(int64_t n, int nrhs, int sum)
 {
     const size_t cuda_core = sizeof(double) * (size_t)pick_js(n) *
                                  (size_t)std::min(std::max(nrhs, 1), 32) * (size_t)n + 256;
-    return std::max(cuda_core, nrhs >= DFU_MIN_COLS ? dfu_scratch(n) : (size_t)0);
+    return std::max(cuda_core, df_on_tc(n, nrhs, sum) ? dfu_scratch(n) : (size_t)0);
 }
+
+size_t matvecdf_scratch(int64_t n, int nrhs) { return matvecdf_scratch(n, nrhs, DF_SUM_AUTO); }
 
 // the double-float matvec in column pieces of at most cap (16 or 32): every
 // column's sum is formed the same way whatever the piece, so the results do
@@ -1155,15 +1162,15 @@ static afn_status matvec_dfu(const float2 *Xd, int64_t n, int ds, int kernel, do
 
 afn_status matvec_df(const float2 *Xd, int64_t n, int ds, int kernel, double mu, const double *p,
                      int nrhs, double *q, void *scratch, size_t scratch_bytes, int *err,
-                     cudaStream_t s)
+                     cudaStream_t s, int sum)
 {
     if (n <= 0 || nrhs <= 0) return AFN_OK;
-    if (scratch_bytes < matvecdf_scratch(n, nrhs)) {
+    if (scratch_bytes < matvecdf_scratch(n, nrhs, sum)) {
         set_error("matvec_df: scratch too small");
         return AFN_ERR_ARG;
     }
-    if (nrhs >= DFU_MIN_COLS) {
-        // eight or more columns: the contraction on the tensor cores
+    if (df_on_tc(n, nrhs, sum)) {
+        // the contraction on the tensor cores
         AFN_TRY(matvec_dfu(Xd, n, ds, kernel, mu, p, nrhs, q, scratch, err, s));
     } else {
         int js;

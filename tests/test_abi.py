@@ -81,6 +81,16 @@ def test_default_options():
     assert ctypes.sizeof(afn.afn_build_info) == 96
 
 
+def test_bad_matvec_precision_rejected_without_gpu():
+    from paper_2304_05460_gb300 import afn
+    X = np.zeros((4, 3))
+    p = np.ones(4)
+    for prec in (3, 6, -1):
+        with pytest.raises(afn.AfnError) as e:
+            afn.afn_kernel_matvec(X, afn.GAUSSIAN, 1.0, 1e-3, p, precision=prec)
+        assert e.value.status == afn.AFN_ERR_ARG
+
+
 def test_bad_krylov_and_auto_rho_rejected_without_gpu():
     from paper_2304_05460_gb300 import afn
     X = np.zeros((4, 3))

@@ -159,10 +159,11 @@ def test_matvec_double_float_tensor_core(afn, n, d, ker, nrhs):
     P = inputs.rhs(n, nrhs, 351 + n)
     l = 0.7 * np.sqrt(d)
     ref = oracle.matvec(X, ker, l, 1e-2, P)
-    q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=afn.MATVEC_DF)
-    bound = scale_bound(X, ker, l, 1e-2, P).reshape(q.shape)
-    err = np.abs(q - ref.reshape(q.shape)) / (bound + 1e-300)
-    assert err.max() <= 1e-12, err.max()
+    bound = scale_bound(X, ker, l, 1e-2, P)
+    for prec in (afn.MATVEC_DF_TC, afn.MATVEC_DF_CC):
+        q = afn.afn_kernel_matvec(X, ker, l, 1e-2, P, precision=prec)
+        err = np.abs(q - ref.reshape(q.shape)) / (bound.reshape(q.shape) + 1e-300)
+        assert err.max() <= 1e-12, (prec, err.max())
 
 
 def test_matvec_double_float_tensor_core_scaled_columns(afn):
@@ -172,7 +173,7 @@ def test_matvec_double_float_tensor_core_scaled_columns(afn):
     P = inputs.rhs(n, 12, 362) * np.array([1e-200, 1e-8, 1.0, 1e6, 1e150, 0.0, 3.0, 1e-3,
                                              7.0, 1e-280, 1e280, 0.5])
     ref = oracle.matvec(X, G, 2.0, 1e-2, P)
-    q = afn.afn_kernel_matvec(X, G, 2.0, 1e-2, P, precision=afn.MATVEC_DF)
+    q = afn.afn_kernel_matvec(X, G, 2.0, 1e-2, P, precision=afn.MATVEC_DF_TC)
     bound = scale_bound(X, G, 2.0, 1e-2, P).reshape(q.shape)
     err = np.abs(q - ref.reshape(q.shape)) / (bound + 1e-300)
     assert np.all(q[:, 5] == 0.0)
@@ -226,7 +227,7 @@ def test_matvec_double_float_tensor_core_full_size(afn):
     # tensor-core double-float matvec, on sampled rows (first and last rows included)
     s = inputs.normal_8d(l=2.0, nrhs=32)
     rows = _sample_rows(s.n, 40, 12, 12)
-    q = afn.afn_kernel_matvec(s.X, G, 2.0, 1e-2, s.B, precision=afn.MATVEC_DF)
+    q = afn.afn_kernel_matvec(s.X, G, 2.0, 1e-2, s.B, precision=afn.MATVEC_DF_TC)
     ref = oracle.matvec_rows(s.X, G, 2.0, 1e-2, s.B, rows)
     absb = oracle.matvec_rows(s.X, G, 2.0, 1e-2, np.abs(s.B), rows)
     assert np.all(np.abs(q[rows] - ref) <= 1e-11 * absb)

@@ -67,3 +67,19 @@ def test_apply_wait_limit_runs_out_and_recovers(afn, mode):
     s1 = afn.afn_apply_precond(h, r)
     assert np.array_equal(s0, s1)
     afn.afn_free(h)
+
+
+def test_double_float_tensor_core_wait_limit_runs_out_and_recovers(afn):
+    # the double-float matvec with the sum on the tensor cores (32 columns)
+    X = inputs.normal_points(3000, 8, 75)
+    P = inputs.rhs(3000, 32, 76)
+    q0 = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF_TC)
+    try:
+        afn.afn_set_wait_limit_ns(1)
+        with pytest.raises(afn.AfnError) as e:
+            afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF_TC)
+        assert e.value.status == afn.AFN_ERR_TIMEOUT
+    finally:
+        afn.afn_set_wait_limit_ns(0)
+    q1 = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.MATVEC_DF_TC)
+    assert np.array_equal(q0, q1)
