@@ -92,20 +92,30 @@ __global__ void __launch_bounds__(FPS_T) fps_step_kernel(const double *__restric
         }
     }
     __syncthreads();
-    if (!last || wid != 0) return;
+    if (!last) return;
+    // the last block: every thread reads partials (one or two loads in flight
+    // per thread rather than a serial chain in one warp), then the block argmax
     __threadfence();
     double v = -3.0;
     int64_t ii = LLONG_MAX;
-    for (unsigned b = lane; b < gridDim.x; b += 32) {
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += FPS_T) {
         double v2 = __ldcg(partv + b);
         int64_t i2 = __ldcg(parti + b);
         if (better_max(v2, i2, v, ii)) { v = v2; ii = i2; }
     }
     warp_argmax(v, ii);
-    if (lane == 0) {
-        idx[it] = ii;
-        dm[ii] = -1.0;
-        *cnt = 0;
+    __syncthreads();                       // wv / wi of the first reduction are read
+    if (lane == 0) { wv[wid] = v; wi[wid] = ii; }
+    __syncthreads();
+    if (wid == 0) {
+        v = (lane < FPS_T / 32) ? wv[lane] : -3.0;
+        ii = (lane < FPS_T / 32) ? wi[lane] : LLONG_MAX;
+        warp_argmax(v, ii);
+        if (lane == 0) {
+            idx[it] = ii;
+            dm[ii] = -1.0;
+            *cnt = 0;
+        }
     }
 }
 
@@ -122,9 +132,11 @@ afn_status fps_run(const double *X, int64_t n, int d, int64_t k, int64_t start, 
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // about 8 points per thread, at most 4 blocks per SM
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 8 * FPS_T - 1) / (8 * FPS_T),
-                                                               (int64_t)sms * 4));
+    // one point per thread up to two blocks per SM: a step is a short chain of
+    // FP64 operations per point (GB300 retires few FP64 operations per cycle), so
+    // spreading the points over every SM shortens each of the k - 1 steps
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + FPS_T - 1) / FPS_T,
+                                                               (int64_t)sms * 2));
     DevBuf xt, dm, pv, pi, cnt;
     AFN_TRY(xt.alloc(sizeof(double) * (size_t)(n * d)));
     AFN_TRY(dm.alloc(sizeof(double) * (size_t)n));
