@@ -851,6 +851,11 @@ afn_status afn_solve_batched(afn_batch *bb, const double *rhs, const int32_t *nr
     std::vector<int> single;
     for (int q = 0; q < ns; ++q)
         if (b->h[q]->precision != AFN_PREC_MIXED) single.push_back(q);
+    // longest first (cost ~ n^2 x columns), so the last system to start is a short one
+    std::stable_sort(single.begin(), single.end(), [&](int a, int c) {
+        return (double)b->h[a]->n * (double)b->h[a]->n * nrhs[a] >
+               (double)b->h[c]->n * (double)b->h[c]->n * nrhs[c];
+    });
     std::vector<afn_status> sst(ns, AFN_OK);
     std::vector<int> sconv(ns, 0);
     std::atomic<int> snext{0};

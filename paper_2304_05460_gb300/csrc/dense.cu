@@ -298,13 +298,6 @@ afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaS
     return trsm_right_lt<float>(L, k, B, m, s);
 }
 
-template <class T>
-__global__ void identity_kernel(T *A, int64_t k)
-{
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= k * k) return;
-    A[e] = (e / k == e % k) ? (T)1 : (T)0;
-}
 
 template <class T>
 __global__ void transpose_kernel(const T *__restrict__ A, int64_t k, T *__restrict__ B)
@@ -322,17 +315,188 @@ __global__ void transpose_kernel(const T *__restrict__ A, int64_t k, T *__restri
     }
 }
 
-// LinvT = I L^{-T} = L^{-T} (upper, row-major) by the blocked solve;
-// Linv = its transpose (lower, row-major).
+
+// ------------------------------------------------------------------ GEMM --
+// C = alpha A B on the CUDA cores, A (M x K), B (K x N), C (M x N), all
+// row-major with leading dimensions; batch z adds z * (sa, sb, sc) to the
+// three pointers.  MODE says which operand is triangular, so a tile reads only
+// the K-range where both operands can be nonzero:
+//   GM_B_UPPER  B[q][p] = 0 for q > p  (column tile [n0, n0 + BN): q < n0 + BN)
+//   GM_B_LOWER  B[q][p] = 0 for q < p  (q >= n0)
+//   GM_A_LOWER  A[m][q] = 0 for q > m  (row tile [m0, m0 + BM): q < m0 + BM)
+// The zeros inside the range are read as stored.  Each output is the sum over
+// q in ascending order.  FP32: 128 x 128 tiles, 8 x 8 outputs per thread;
+// FP64: 64 x 64 tiles, 4 x 4 per thread (GB300 retires few FP64 FMAs per
+// cycle, so the tile only needs enough reuse to keep that pipe busy).  8-deep
+// K slices double-buffered in shared memory.
+enum : int { GM_B_UPPER = 1, GM_B_LOWER = 2, GM_A_LOWER = 4 };
+
+template <class T> struct GemmTile;
+template <> struct GemmTile<float> { static constexpr int B = 128, R = 8; };
+template <> struct GemmTile<double> { static constexpr int B = 64, R = 4; };
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) gemm_tri_kernel(const T *__restrict__ A, int64_t lda, int64_t sa,
+                                                       const T *__restrict__ B, int64_t ldb, int64_t sb,
+                                                       T *__restrict__ C, int64_t ldc, int64_t sc,
+                                                       int64_t M, int64_t N, int64_t K, T alpha)
+{
+    constexpr int BT = GemmTile<T>::B, R = GemmTile<T>::R, BK = 8;
+    constexpr int H = BT / 2;                       // outputs of a thread: rows {ty R/2 + i, H + ...}
+    constexpr int LA = BT * BK / 256;               // A elements loaded per thread per slice
+    __shared__ __align__(16) T As[2][BK][BT];
+    __shared__ __align__(16) T Bs[2][BK][BT];
+    A += (int64_t)blockIdx.z * sa;
+    B += (int64_t)blockIdx.z * sb;
+    C += (int64_t)blockIdx.z * sc;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * BT, n0 = (int64_t)blockIdx.x * BT;
+    int64_t klo = (MODE & GM_B_LOWER) ? n0 : 0, khi = K;
+    if (MODE & GM_B_UPPER) khi = min(khi, n0 + BT);
+    if (MODE & GM_A_LOWER) khi = min(khi, m0 + BT);
+    // this thread's loads: A row m0 + tid / (BK / LA), K-elements (tid % (BK / LA)) LA + u;
+    // B row tid / 32 of the slice, columns (tid % 32) LA + u
+    const int am = tid / (BK / LA), ak = (tid % (BK / LA)) * LA;
+    const int bk = tid / 32, bn = (tid % 32) * LA;
+    T ra[LA], rb[LA];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            const int64_t gm = m0 + am, gk = k0 + ak + u;
+            ra[u] = (gm < M && gk < khi) ? A[gm * lda + gk] : (T)0;
+            const int64_t gq = k0 + bk, gp = n0 + bn + u;
+            rb[u] = (gq < khi && gp < N) ? B[gq * ldb + gp] : (T)0;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            As[buf][ak + u][am] = ra[u];
+            Bs[buf][bk][bn + u] = rb[u];
+        }
+    };
+    T acc[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = (T)0;
+    const int nt = khi > klo ? (int)((khi - klo + BK - 1) / BK) : 0;
+    if (nt > 0) {
+        fetch(klo);
+        stash(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nt) fetch(klo + (int64_t)(t + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[R], bv[R];
+#pragma unroll
+            for (int i = 0; i < R / 2; ++i) {
+                av[i] = As[buf][kk][ty * (R / 2) + i];
+                av[R / 2 + i] = As[buf][kk][H + ty * (R / 2) + i];
+                bv[i] = Bs[buf][kk][tx * (R / 2) + i];
+                bv[R / 2 + i] = Bs[buf][kk][H + tx * (R / 2) + i];
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < R; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        if (t + 1 < nt) stash(buf ^ 1);     // the other buffer was last read before the previous barrier
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int64_t gm = m0 + (i < R / 2 ? ty * (R / 2) + i : H + ty * (R / 2) + (i - R / 2));
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int64_t gp = n0 + (j < R / 2 ? tx * (R / 2) + j : H + tx * (R / 2) + (j - R / 2));
+            if (gp < N) C[gm * ldc + gp] = alpha * acc[i][j];
+        }
+    }
+}
+
+template <class T, int MODE>
+static void gemm_tri(const T *A, int64_t lda, int64_t sa, const T *B, int64_t ldb, int64_t sb, T *C,
+                     int64_t ldc, int64_t sc, int64_t M, int64_t N, int64_t K, T alpha, int batch,
+                     cudaStream_t s)
+{
+    constexpr int BT = GemmTile<T>::B;
+    if (M <= 0 || N <= 0 || batch <= 0) return;
+    dim3 g((unsigned)((N + BT - 1) / BT), (unsigned)((M + BT - 1) / BT), (unsigned)batch);
+    gemm_tri_kernel<T, MODE><<<g, 256, 0, s>>>(A, lda, sa, B, ldb, sb, C, ldc, sc, M, N, K, alpha);
+}
+
+// Inverses of the 64 x 64 diagonal blocks of L (one CTA per block, one thread
+// per column: forward substitution of the unit vector, p ascending).
+static constexpr int TI_B = 64;
+
+template <class T>
+__global__ void __launch_bounds__(TI_B) diag_inverse_kernel(const T *__restrict__ L, int64_t k,
+                                                            T *__restrict__ Linv)
+{
+    // dynamic shared memory: lb[TI_B][TI_B + 1] (the block of L), then
+    // xs[TI_B][TI_B + 1] (xs[i][c]: row i of column c of the block inverse)
+    extern __shared__ __align__(16) unsigned char tism[];
+    T(*lb)[TI_B + 1] = reinterpret_cast<T(*)[TI_B + 1]>(tism);
+    T(*xs)[TI_B + 1] = reinterpret_cast<T(*)[TI_B + 1]>(tism + sizeof(T) * TI_B * (TI_B + 1));
+    const int64_t r0 = (int64_t)blockIdx.x * TI_B;
+    const int nb = (int)(k - r0 < TI_B ? k - r0 : TI_B);
+    for (int e = threadIdx.x; e < nb * nb; e += TI_B) {
+        const int r = e / nb, c = e % nb;
+        lb[r][c] = L[(r0 + r) * k + r0 + c];
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c >= nb) return;
+    for (int i = c; i < nb; ++i) {
+        T v = (i == c) ? (T)1 : (T)0;
+        for (int p = c; p < i; ++p) v -= lb[i][p] * xs[p][c];
+        xs[i][c] = v / lb[i][i];
+        Linv[(r0 + i) * k + r0 + c] = xs[i][c];
+    }
+}
+
+// Linv = L^{-1} (lower, row-major) by recursive doubling over block sizes
+// b = 64, 128, ...: with [A 0; B C] the 2b-block at i0 (A, C already
+// inverted), its lower-left block is -C^{-1} (B A^{-1}); the products run as
+// batched tiled GEMMs over all 2b-blocks of a level (the one at the end of
+// the matrix, which may be shorter, in its own launch).  LinvT holds
+// T = B A^{-1} during the levels and L^{-T} at the end.
 template <class T>
 static afn_status tri_inverse(const T *L, int64_t k, T *Linv, T *LinvT, cudaStream_t s)
 {
     if (k <= 0) return AFN_OK;
-    unsigned g = (unsigned)((k * k + 255) / 256);
-    identity_kernel<T><<<g, 256, 0, s>>>(LinvT, k);
-    AFN_TRY(trsm_right_lt<T>(L, k, LinvT, k, s));
+    AFN_CUDA(cudaMemsetAsync(Linv, 0, sizeof(T) * (size_t)(k * k), s));
+    const int dsm = (int)(2 * sizeof(T) * TI_B * (TI_B + 1));
+    cudaFuncSetAttribute(diag_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm);
+    diag_inverse_kernel<T><<<(unsigned)((k + TI_B - 1) / TI_B), TI_B, dsm, s>>>(L, k, Linv);
+    for (int64_t b = TI_B; b < k; b *= 2) {
+        const int64_t st = 2 * b * k + 2 * b;                // one 2b-block further down the diagonal
+        const int64_t full = (k - b) / (2 * b);              // pairs whose C block has b rows
+        const int64_t i0l = full * 2 * b;                    // the pair at the end, if any
+        const int64_t cl = i0l + b < k ? std::min<int64_t>(b, k - i0l - b) : 0;
+        auto level = [&](int64_t i0, int64_t c, int batch) {
+            const int64_t a = i0 * k + i0, bl = (i0 + b) * k + i0, cc = (i0 + b) * k + i0 + b;
+            // T = B A^{-1}   (A^{-1} lower triangular)
+            gemm_tri<T, GM_B_LOWER>(L + bl, k, st, Linv + a, k, st, LinvT + bl, k, st, c, b, b,
+                                    (T)1, batch, s);
+            // lower-left block = -C^{-1} T   (C^{-1} lower triangular)
+            gemm_tri<T, GM_A_LOWER>(Linv + cc, k, st, LinvT + bl, k, st, Linv + bl, k, st, c, b, c,
+                                    (T)-1, batch, s);
+        };
+        if (full > 0 && i0l + b < k && cl == b) {
+            level(0, b, (int)(full + 1));
+        } else {
+            if (full > 0) level(0, b, (int)full);
+            if (cl > 0) level(i0l, cl, 1);
+        }
+    }
     dim3 gt((unsigned)((k + 31) / 32), (unsigned)((k + 31) / 32));
-    transpose_kernel<T><<<gt, dim3(32, 8), 0, s>>>(LinvT, k, Linv);
+    transpose_kernel<T><<<gt, dim3(32, 8), 0, s>>>(Linv, k, LinvT);
     AFN_CUDA(cudaGetLastError());
     return AFN_OK;
 }
@@ -347,173 +511,11 @@ afn_status tri_inverse32(const float *L, int64_t k, float *Linv, float *LinvT, c
     return tri_inverse<float>(L, k, Linv, LinvT, s);
 }
 
-// ------------------------------------------------------------------ SGEMM --
-// C = A B in FP32 on the CUDA cores: A (M x K) and B (K x N) row-major, C
-// (M x N) row-major.  UPPER: B is upper triangular (B[q][p] = 0 for q > p),
-// so column block [n0, n0 + 128) needs only q < n0 + 128.  128 x 128 tiles,
-// 8-deep K slices double-buffered in shared memory, 8 x 8 outputs per thread;
-// each output is the sum over q in ascending order.
-static constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
-
-template <bool UPPER>
-__global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A, int64_t lda,
-                                                    const float *__restrict__ B, int64_t ldb,
-                                                    float *__restrict__ C, int64_t ldc, int64_t M,
-                                                    int64_t N, int64_t K)
-{
-    __shared__ __align__(16) float As[2][SG_BK][SG_BM];
-    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int64_t m0 = (int64_t)blockIdx.y * SG_BM, n0 = (int64_t)blockIdx.x * SG_BN;
-    const int64_t kend = UPPER ? min(K, n0 + SG_BN) : K;
-    // this thread's loads: A rows m0 + tid / 2, K-elements (tid % 2) * 4 + u;
-    // B row tid / 32 of the slice, columns (tid % 32) * 4 + u
-    const int am = tid / 2, ak = (tid % 2) * 4;
-    const int bk = tid / 32, bn = (tid % 32) * 4;
-    float ra[4], rb[4];
-    auto fetch = [&](int64_t k0) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t gm = m0 + am, gk = k0 + ak + u;
-            ra[u] = (gm < M && gk < kend) ? A[gm * lda + gk] : 0.f;
-            const int64_t gq = k0 + bk, gp = n0 + bn + u;
-            rb[u] = (gq < kend && gp < N) ? B[gq * ldb + gp] : 0.f;
-        }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            As[buf][ak + u][am] = ra[u];
-            Bs[buf][bk][bn + u] = rb[u];
-        }
-    };
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    const int nt = (int)((kend + SG_BK - 1) / SG_BK);
-    if (nt > 0) {
-        fetch(0);
-        stash(0);
-    }
-    __syncthreads();
-    for (int t = 0; t < nt; ++t) {
-        const int buf = t & 1;
-        if (t + 1 < nt) fetch((int64_t)(t + 1) * SG_BK);
-#pragma unroll
-        for (int kk = 0; kk < SG_BK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-        }
-        if (t + 1 < nt) {
-            stash(buf ^ 1);     // the other buffer was last read before the previous barrier
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t gp = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
-            if (gp < N) C[gm * ldc + gp] = acc[i][j];
-        }
-    }
-}
-
-// The FP64 form: 64 x 64 tiles, 4 x 4 outputs per thread (GB300 retires few
-// FP64 FMAs per cycle, so the tile only needs enough reuse to keep that pipe
-// busy); same loads, same ascending-q sums.
-static constexpr int DG_B = 64, DG_BK = 8;
-
-template <bool UPPER>
-__global__ void __launch_bounds__(256) dgemm_kernel(const double *__restrict__ A, int64_t lda,
-                                                    const double *__restrict__ B, int64_t ldb,
-                                                    double *__restrict__ C, int64_t ldc, int64_t M,
-                                                    int64_t N, int64_t K)
-{
-    __shared__ __align__(16) double As[2][DG_BK][DG_B];
-    __shared__ __align__(16) double Bs[2][DG_BK][DG_B];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int64_t m0 = (int64_t)blockIdx.y * DG_B, n0 = (int64_t)blockIdx.x * DG_B;
-    const int64_t kend = UPPER ? min(K, n0 + DG_B) : K;
-    // loads: A rows m0 + tid / 4, K-elements (tid % 4) * 2 + u; B row tid / 32, columns (tid % 32) * 2 + u
-    const int am = tid / 4, ak = (tid % 4) * 2;
-    const int bk = tid / 32, bn = (tid % 32) * 2;
-    double ra[2], rb[2];
-    auto fetch = [&](int64_t k0) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int64_t gm = m0 + am, gk = k0 + ak + u;
-            ra[u] = (gm < M && gk < kend) ? A[gm * lda + gk] : 0.0;
-            const int64_t gq = k0 + bk, gp = n0 + bn + u;
-            rb[u] = (gq < kend && gp < N) ? B[gq * ldb + gp] : 0.0;
-        }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            As[buf][ak + u][am] = ra[u];
-            Bs[buf][bk][bn + u] = rb[u];
-        }
-    };
-    double acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    const int nt = (int)((kend + DG_BK - 1) / DG_BK);
-    if (nt > 0) {
-        fetch(0);
-        stash(0);
-    }
-    __syncthreads();
-    for (int t = 0; t < nt; ++t) {
-        const int buf = t & 1;
-        if (t + 1 < nt) fetch((int64_t)(t + 1) * DG_BK);
-#pragma unroll
-        for (int kk = 0; kk < DG_BK; ++kk) {
-            double av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[buf][kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[buf][kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-        }
-        if (t + 1 < nt) stash(buf ^ 1);
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t gm = m0 + ty * 4 + i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t gp = n0 + tx * 4 + j;
-            if (gp < N) C[gm * ldc + gp] = acc[i][j];
-        }
-    }
-}
-
 // C (m x k) = A (m x k) U with U (k x k) upper triangular, FP64, row-major
 afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s)
 {
     if (m <= 0 || k <= 0) return AFN_OK;
-    dim3 g((unsigned)((k + DG_B - 1) / DG_B), (unsigned)((m + DG_B - 1) / DG_B));
-    dgemm_kernel<true><<<g, 256, 0, s>>>(A, k, U, k, C, k, m, k, k);
+    gemm_tri<double, GM_B_UPPER>(A, k, 0, U, k, 0, C, k, 0, m, k, k, 1.0, 1, s);
     AFN_CUDA(cudaGetLastError());
     return AFN_OK;
 }
@@ -522,8 +524,7 @@ afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, 
 afn_status gemm_upper32(const float *A, int64_t m, int64_t k, const float *U, float *C, cudaStream_t s)
 {
     if (m <= 0 || k <= 0) return AFN_OK;
-    dim3 g((unsigned)((k + SG_BN - 1) / SG_BN), (unsigned)((m + SG_BM - 1) / SG_BM));
-    sgemm_kernel<true><<<g, 256, 0, s>>>(A, k, U, k, C, k, m, k, k);
+    gemm_tri<float, GM_B_UPPER>(A, k, 0, U, k, 0, C, k, 0, m, k, k, 1.f, 1, s);
     AFN_CUDA(cudaGetLastError());
     return AFN_OK;
 }
