@@ -856,11 +856,19 @@ __device__ __forceinline__ void mvdf_rows(const float2 *__restrict__ Xd, int64_t
     float S[NR], Cc[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) S[c] = Cc[c] = 0.f;
+    // the point tile holds packed pairs: points 2m, 2m + 1 and dimension q at
+    // float4 m DS + q = {h, h', l, l'} (two kernel values per f32x2 operation)
+    float *xsf = reinterpret_cast<float *>(xs);
+    const float4 *xs4 = reinterpret_cast<const float4 *>(xs);
     for (int64_t jt = j0; jt < j1; jt += TJ) {
         __syncthreads();
         for (int e = threadIdx.x; e < TJ * DS; e += NT) {
-            const int64_t j = jt + e / DS;
-            xs[e] = j < j1 ? Xd[jt * DS + e] : make_float2(0.f, 0.f);
+            const int jj = e / DS, q = e % DS;
+            const int64_t j = jt + jj;
+            const float2 v = j < j1 ? Xd[jt * DS + e] : make_float2(0.f, 0.f);
+            float *b = xsf + ((jj >> 1) * DS + q) * 4;
+            b[jj & 1] = v.x;
+            b[2 + (jj & 1)] = v.y;
         }
         for (int e = threadIdx.x; e < NR * TJ; e += NT) {
             const int c = e / TJ, jj = e % TJ;
@@ -870,19 +878,26 @@ __device__ __forceinline__ void mvdf_rows(const float2 *__restrict__ Xd, int64_t
             ps[e] = make_float2(h, (float)(v - (double)h));
         }
         __syncthreads();
-        for (int jj = g * (TJ / JG); jj < (g + 1) * (TJ / JG); ++jj) {
-            const dfl z = df_dist2<DS>(xi, xs + jj * DS);
-            const dfl kv = df_kernel<KER>(z, T);
+        for (int jj = g * (TJ / JG); jj < (g + 1) * (TJ / JG); jj += 2) {
+            // kernel values of points jj and jj + 1 together, then their terms in order
+            const dfl2 kv2 = df_kernel2<KER>(df_dist2_2<DS>(xi, xs4 + (jj >> 1) * DS), T);
+            dfl kvs[2];
+            f2_unpack(kv2.h, kvs[0].h, kvs[1].h);
+            f2_unpack(kv2.l, kvs[0].l, kvs[1].l);
 #pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                const float2 x = ps[c * TJ + jj];
-                const float p = __fmul_rn(kv.h, x.x);
-                float e = __fmaf_rn(kv.h, x.x, -p);
-                e = __fmaf_rn(kv.h, x.y, e);
-                e = __fmaf_rn(kv.l, x.x, e);
-                float t;
-                two_sum(S[c], p, S[c], t);
-                Cc[c] = __fadd_rn(Cc[c], __fadd_rn(t, e));
+            for (int u = 0; u < 2; ++u) {
+                const dfl kv = kvs[u];
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    const float2 x = ps[c * TJ + jj + u];
+                    const float p = __fmul_rn(kv.h, x.x);
+                    float e = __fmaf_rn(kv.h, x.x, -p);
+                    e = __fmaf_rn(kv.h, x.y, e);
+                    e = __fmaf_rn(kv.l, x.x, e);
+                    float t;
+                    two_sum(S[c], p, S[c], t);
+                    Cc[c] = __fadd_rn(Cc[c], __fadd_rn(t, e));
+                }
             }
         }
         // renormalise so the correction term stays small next to the sum
@@ -1029,12 +1044,19 @@ static void matvec_df_pieces(int cap, const float2 *Xd, int64_t n, int ds, int k
 }
 
 // ------------------------------------ double-float on the tensor cores --
-// zero-padded copy of the double-float points for the staged tiles
+// the double-float points for the staged tiles, zero-padded, as packed pairs:
+// points 2m, 2m + 1 and dimension q at float4 m ds + q = {h, h', l, l'}
 __global__ void dupoints_kernel(const float2 *__restrict__ Xd, int64_t n, int ds, int64_t npad,
-                                float2 *__restrict__ Xpr)
+                                float4 *__restrict__ Xpr)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < npad * ds) Xpr[e] = e < n * ds ? Xd[e] : make_float2(0.f, 0.f);
+    if (e >= npad / 2 * ds) return;
+    const int64_t m = e / ds;
+    const int q = (int)(e % ds);
+    const int64_t j0 = 2 * m, j1 = 2 * m + 1;
+    const float2 a = j0 < n ? Xd[j0 * ds + q] : make_float2(0.f, 0.f);
+    const float2 b = j1 < n ? Xd[j1 * ds + q] : make_float2(0.f, 0.f);
+    Xpr[e] = make_float4(a.x, b.x, a.y, b.y);
 }
 
 // max_j |p_jc| of the nc columns, as the bits of a non-negative double
@@ -1136,7 +1158,8 @@ static afn_status matvec_dfu(const float2 *Xd, int64_t n, int ds, int kernel, do
     int js;
     int64_t chunk_st;
     chunking_du(n, nstage, js, chunk_st);
-    dupoints_kernel<<<(unsigned)((npad * ds + 255) / 256), 256, 0, s>>>(Xd, n, ds, npad, Xpr);
+    dupoints_kernel<<<(unsigned)((npad / 2 * ds + 255) / 256), 256, 0, s>>>(
+        Xd, n, ds, npad, reinterpret_cast<float4 *>(Xpr));
     for (int c0 = 0; c0 < nrhs; c0 += DU_NR) {
         const int nc = std::min(DU_NR, nrhs - c0);
         const double *pp = p + (int64_t)c0 * n;

@@ -103,6 +103,27 @@ __device__ __forceinline__ void du_digits(dfl v, float (&d)[DU_DIG])
     a = du_round(__fadd_rn(r, rl), 0x1.8p-40f);       d[7] = a * 0x1p63f;
 }
 
+// du_digits for two values at once (packed f32x2, the same roundings)
+__device__ __forceinline__ f2_t du_round2(f2_t r, float c)
+{
+    return f2_sub(f2_add(r, f2_splat(c)), f2_splat(c));
+}
+
+__device__ __forceinline__ void du_digits2(dfl2 v, f2_t (&d)[DU_DIG])
+{
+    f2_t r = v.h, rl = v.l, a;
+    a = du_round2(r, 0x1.8p16f);  r = f2_sub(r, a); d[0] = f2_mul(a, f2_splat(0x1p7f));
+    a = du_round2(r, 0x1.8p8f);   r = f2_sub(r, a); d[1] = f2_mul(a, f2_splat(0x1p15f));
+    a = du_round2(r, 0x1.8p0f);   r = f2_sub(r, a); d[2] = f2_mul(a, f2_splat(0x1p23f));
+    two_sum2(r, rl, r, rl);
+    a = du_round2(r, 0x1.8p-8f);  r = f2_sub(r, a); d[3] = f2_mul(a, f2_splat(0x1p31f));
+    a = du_round2(r, 0x1.8p-16f); r = f2_sub(r, a); d[4] = f2_mul(a, f2_splat(0x1p39f));
+    a = du_round2(r, 0x1.8p-24f); r = f2_sub(r, a); d[5] = f2_mul(a, f2_splat(0x1p47f));
+    two_sum2(r, rl, r, rl);
+    a = du_round2(r, 0x1.8p-32f); r = f2_sub(r, a); d[6] = f2_mul(a, f2_splat(0x1p55f));
+    a = du_round2(f2_add(r, rl), 0x1.8p-40f);       d[7] = f2_mul(a, f2_splat(0x1p63f));
+}
+
 __device__ __forceinline__ uint32_t du_pack(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (low half) = lo
@@ -117,7 +138,9 @@ __device__ __forceinline__ int du_int(float x)
 
 // Row sums over the stages [s0, s1) of the prepared arrays:
 //   Xs:  the double-float points of the rows (n x DS);
-//   Xpr: per stage the DU_J staged points (n padded with zero points);
+//   Xpr: per stage the DU_J staged points (n padded with zero points) as
+//        packed pairs: points 2m, 2m + 1 and dimension q at float4 m DS + q =
+//        {h(2m), h(2m + 1), l(2m), l(2m + 1)};
 //   Pd:  per stage the digit tile of p (column n' = 32 t + c holds digit t of
 //        column c, du_tile_elem layout), zero beyond n and beyond nc columns;
 //   pexp: E_c per column.
@@ -292,19 +315,23 @@ __global__ void __launch_bounds__(DU_THREADS, 1)
             }
             // A buffer c & 1 was last read by the MMAs of block c - 2, whose
             // completion the fold of block c - 2 (previous iteration) awaited
-            const float2 *pts = reinterpret_cast<const float2 *>(stages + sb * SB);
+            const float4 *pts = reinterpret_cast<const float4 *>(stages + sb * SB);
             unsigned char *ab = abuf + (c & 1) * DU_ABUF + aoff;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t w[DU_DIG][2];
 #pragma unroll
                 for (int m2 = 0; m2 < 2; ++m2) {
-                    float d0[DU_DIG], d1[DU_DIG];
+                    // points jj and jj + 1 together (packed pairs of the staged tile)
+                    f2_t d2[DU_DIG];
                     const int jj = hf * 8 + h * 4 + m2 * 2;
-                    du_digits(df_kernel<KER>(df_dist2<DS>(xi, pts + jj * DS), T), d0);
-                    du_digits(df_kernel<KER>(df_dist2<DS>(xi, pts + (jj + 1) * DS), T), d1);
+                    du_digits2(df_kernel2<KER>(df_dist2_2<DS>(xi, pts + (jj / 2) * DS), T), d2);
 #pragma unroll
-                    for (int s = 0; s < DU_DIG; ++s) w[s][m2] = du_pack(d0[s], d1[s]);
+                    for (int s = 0; s < DU_DIG; ++s) {
+                        float a0, a1;
+                        f2_unpack(d2[s], a0, a1);
+                        w[s][m2] = du_pack(a0, a1);
+                    }
                 }
 #pragma unroll
                 for (int s = 0; s < DU_DIG; ++s)
