@@ -246,7 +246,6 @@ afn_status kernel_block(const double *Xa, int64_t na, const double *Xb, int64_t 
 // in place, lower; tiny < 0: error on a pivot <= 0; tiny >= 0: drop pivots <= tiny
 afn_status cholesky64(double *A, int64_t k, int *status, cudaStream_t s, double tiny);
 afn_status tri_inverse64(const double *L, int64_t k, double *Linv, double *LinvT, cudaStream_t s);
-afn_status tri_inverse32(const float *L, int64_t k, float *Linv, float *LinvT, cudaStream_t s);
 afn_status trsm_right_lt64(const double *L, int64_t k, double *B, int64_t m,
                            cudaStream_t s);   // B (m x k) <- B L^{-T}
 afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaStream_t s);

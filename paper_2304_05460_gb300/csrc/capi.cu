@@ -490,12 +490,18 @@ static afn_status build_impl(Handle *h, const double *points)
                 h->LinvT.release();
             }
         } else {
-            DevBuf L32;
-            AFN_TRY(L32.alloc(sizeof(float) * (size_t)(k * k)));
-            AFN_TRY(convert64to32(h->L.as<double>(), L32.as<float>(), k * k, s));
-            AFN_TRY(h->Linv32.alloc(sizeof(float) * (size_t)(k * k)));
-            AFN_TRY(h->LinvT32.alloc(sizeof(float) * (size_t)(k * k)));
-            AFN_TRY(tri_inverse32(L32.as<float>(), k, h->Linv32.as<float>(), h->LinvT32.as<float>(), s));
+            // L^{-1} in FP64 from the FP64 factor (L is ill-conditioned when K11 is), rounded
+            // once to FP32 for W and the apply
+            {
+                DevBuf Li, LiT;
+                AFN_TRY(Li.alloc(sizeof(double) * (size_t)(k * k)));
+                AFN_TRY(LiT.alloc(sizeof(double) * (size_t)(k * k)));
+                AFN_TRY(tri_inverse64(h->L.as<double>(), k, Li.as<double>(), LiT.as<double>(), s));
+                AFN_TRY(h->Linv32.alloc(sizeof(float) * (size_t)(k * k)));
+                AFN_TRY(h->LinvT32.alloc(sizeof(float) * (size_t)(k * k)));
+                AFN_TRY(convert64to32(Li.as<double>(), h->Linv32.as<float>(), k * k, s));
+                AFN_TRY(convert64to32(LiT.as<double>(), h->LinvT32.as<float>(), k * k, s));
+            }
             if (nr > 0) {
                 // W^T = K21 L^{-T}: the kernel block, then one tiled product with the
                 // triangular inverse (the same operator as the triangular solve)

@@ -506,10 +506,6 @@ afn_status tri_inverse64(const double *L, int64_t k, double *Linv, double *LinvT
     return tri_inverse<double>(L, k, Linv, LinvT, s);
 }
 
-afn_status tri_inverse32(const float *L, int64_t k, float *Linv, float *LinvT, cudaStream_t s)
-{
-    return tri_inverse<float>(L, k, Linv, LinvT, s);
-}
 
 // C (m x k) = A (m x k) U with U (k x k) upper triangular, FP64, row-major
 afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s)
