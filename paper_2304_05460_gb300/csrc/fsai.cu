@@ -44,56 +44,79 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
     if (tid < w && tid < WM) s[tid] = pat[i * w + tid];
     __syncthreads();
     const int m = m_s;
-    const int npair = m * (m + 1) / 2;
-    // Gram, lower triangle, each thread a strided set of pairs
-    constexpr int MAXP = (WM * (WM + 1) / 2 + FT - 1) / FT;
-    TW acc[MAXP];
+    // Gram, lower triangle, in 4 x 4 tiles: each thread a strided set of tile
+    // pairs (ta >= tb), 16 sums per pair so that each staged value feeds four
+    // products; every entry is still the sum over the landmarks in order
+    constexpr int NTL = WM / 4;
+    constexpr int MAXT = (NTL * (NTL + 1) / 2 + FT - 1) / FT;
+    const int nt = (m + 3) / 4;
+    const int ntt = nt * (nt + 1) / 2;
+    TW acc[MAXT][4][4];
+    int ta[MAXT], tb[MAXT];
 #pragma unroll
-    for (int q = 0; q < MAXP; ++q) acc[q] = 0;
-    int pa[MAXP], pb[MAXP];
+    for (int q = 0; q < MAXT; ++q) {
 #pragma unroll
-    for (int q = 0; q < MAXP; ++q) {
-        int p = tid + q * FT;
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[q][r][c] = 0;
+        const int p = tid + q * FT;
         int a = 0, b = 0;
-        if (p < npair) {
-            // p -> (a, b) with a >= b, row-major over the lower triangle
+        if (p < ntt) {
+            // p -> (a, b) with a >= b, row-major over the lower triangle of tiles
             a = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
             while ((a + 1) * (a + 2) / 2 <= p) ++a;
             while (a * (a + 1) / 2 > p) --a;
             b = p - a * (a + 1) / 2;
         }
-        pa[q] = a;
-        pb[q] = b;
+        ta[q] = a;
+        tb[q] = b;
     }
     for (int64_t k0 = 0; k0 < k; k0 += KC) {
         __syncthreads();
-        for (int e = tid; e < m * KC; e += FT) {
+        // rows m .. 4 nt - 1 of the tiles are zero
+        for (int e = tid; e < 4 * nt * KC; e += FT) {
             int a = e / KC, kk = e % KC;
             int64_t gk = k0 + kk;
-            ws[a * (KC + 1) + kk] = (gk < k) ? Wt[(int64_t)s[a] * k + gk] : (TW)0;
+            ws[a * (KC + 1) + kk] = (a < m && gk < k) ? Wt[(int64_t)s[a] * k + gk] : (TW)0;
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < MAXP; ++q) {
-            if (tid + q * FT < npair) {
-                const TW *wa = ws + pa[q] * (KC + 1);
-                const TW *wb = ws + pb[q] * (KC + 1);
-                TW v = acc[q];
-#pragma unroll 8
-                for (int kk = 0; kk < KC; ++kk) v += wa[kk] * wb[kk];
-                acc[q] = v;
+        for (int q = 0; q < MAXT; ++q) {
+            if (tid + q * FT < ntt) {
+                const TW *wa = ws + 4 * ta[q] * (KC + 1);
+                const TW *wb = ws + 4 * tb[q] * (KC + 1);
+#pragma unroll 4
+                for (int kk = 0; kk < KC; ++kk) {
+                    TW va[4], vb[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        va[r] = wa[r * (KC + 1) + kk];
+                        vb[r] = wb[r * (KC + 1) + kk];
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[q][r][c] += va[r] * vb[c];
+                }
             }
         }
     }
     // A = K22[s,s] + mu I - Gram  (lower triangle)
 #pragma unroll
-    for (int q = 0; q < MAXP; ++q) {
-        if (tid + q * FT < npair) {
-            int a = pa[q], b = pb[q];
-            double r2 = sqdist_exact(Xr + (int64_t)s[a] * d, Xr + (int64_t)s[b] * d, d);
-            double v = kernel64(r2, kernel, l);
-            if (a == b) v += mu;
-            A[a * (WM + 1) + b] = v - (double)acc[q];
+    for (int q = 0; q < MAXT; ++q) {
+        if (tid + q * FT < ntt) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int a = 4 * ta[q] + r, b = 4 * tb[q] + c;
+                    if (a < m && b <= a) {
+                        double r2 = sqdist_exact(Xr + (int64_t)s[a] * d, Xr + (int64_t)s[b] * d, d);
+                        double v = kernel64(r2, kernel, l);
+                        if (a == b) v += mu;
+                        A[a * (WM + 1) + b] = v - (double)acc[q][r][c];
+                    }
+                }
         }
     }
     __syncthreads();
