@@ -246,6 +246,8 @@ def _cmp(a, b, rtol):
     (300, 3, G, 0.2, 1e-3, 0, 10),          # k = 0: FSAI of K + mu I
     (300, 3, M32, 0.2, 1e-3, 300, 10),      # k = n: no Schur rows
     (200, 4, G, 0.3, 1e-2, 33, 1),          # w = 1: diagonal G
+    (1400, 3, G, 0.08, 1e-3, 1000, 4),      # k = 1000: batched and ragged blocks at every
+                                            # level of the recursive triangular inverse
 ])
 def test_build_parity_fp64(afn, n, d, ker, l, mu, k, w):
     X = inputs.uniform_points(n, d, 500 + n)
