@@ -131,8 +131,12 @@ typedef enum {
     AFN_KRYLOV_FP64 = 1,       /* the same reliable updates with FP64 vectors: x, r, z, p, q
                                   and their updates in FP64, only the matvec and the apply in
                                   FP32 (their inputs rounded to FP32, outputs widened) */
-    AFN_KRYLOV_RESTART = 2     /* restarted refinement: FP32 PCG on the scaled FP64 residual to
+    AFN_KRYLOV_RESTART = 2,    /* restarted refinement: FP32 PCG on the scaled FP64 residual to
                                   inner_tol, x updated in FP64, at most max_outer restarts */
+    AFN_KRYLOV_FP64_OPERATOR = 3  /* FP64 vectors and the FP64-accurate (double-float) matvec in
+                                  every iteration, only the preconditioner apply in FP32
+                                  (mixed-precision preconditioning); slower per iteration,
+                                  for comparison */
 } afn_krylov;
 
 typedef enum {

@@ -29,7 +29,7 @@ MATVEC_DF_TC, MATVEC_DF_CC = 4, 5   # ... with the sum over j on the tensor core
 LM_AUTO, LM_FPS, LM_UNIFORM = 0, 1, 2
 RANK_FIXED, RANK_ESTIMATE = 0, 1
 FACTORS_FP32, FACTORS_FP64 = 0, 1
-KRYLOV_FP32, KRYLOV_FP64, KRYLOV_RESTART = 0, 1, 2
+KRYLOV_FP32, KRYLOV_FP64, KRYLOV_RESTART, KRYLOV_FP64_OPERATOR = 0, 1, 2, 3
 
 
 class AfnError(RuntimeError):

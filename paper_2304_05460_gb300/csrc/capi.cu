@@ -582,7 +582,7 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
         set_error("bad flexible %d", o.flexible);
         return AFN_ERR_ARG;
     }
-    if (o.krylov < AFN_KRYLOV_FP32 || o.krylov > AFN_KRYLOV_RESTART) {
+    if (o.krylov < AFN_KRYLOV_FP32 || o.krylov > AFN_KRYLOV_FP64_OPERATOR) {
         set_error("bad krylov %d", o.krylov);
         return AFN_ERR_ARG;
     }

@@ -658,9 +658,10 @@ static afn_status mixed_reliable(Handle *h, Work &wk, int nrhs, double tol, int 
 // their updates and dots in FP64; only the two operators run in FP32, on
 // their inputs rounded to FP32 (p for the matvec, r for the apply), their
 // outputs widened back to FP64.  Rounding then enters the recurrences only
-// through the operators, not through the vector updates.
+// through the operators, not through the vector updates.  exact_operator:
+// the matvec too is the FP64-accurate one, so only the apply is FP32.
 static afn_status mixed_reliable64(Handle *h, Work &wk, int nrhs, double tol, int maxit,
-                                   double *drel, int *steps_out)
+                                   double *drel, int *steps_out, bool exact_operator)
 {
     cudaStream_t s = h->stream;
     const int64_t n = h->n, tot = n * nrhs;
@@ -685,9 +686,13 @@ static afn_status mixed_reliable64(Handle *h, Work &wk, int nrhs, double tol, in
     const int every = std::max(1, h->opt.check_every);
     int steps = 0;
     for (int it = 0; it < maxit + every; ++it) {
-        to32_kernel<<<g1(tot), 256, 0, s>>>(wk.p, wk.p32, tot);
-        AFN_TRY(mv32(h, wk.p32, nrhs, wk.q32, wk));
-        to64_kernel<<<g1(tot), 256, 0, s>>>(wk.q32, wk.q, tot);
+        if (exact_operator) {
+            AFN_TRY(mv64(h, wk.p, nrhs, wk.q, wk));
+        } else {
+            to32_kernel<<<g1(tot), 256, 0, s>>>(wk.p, wk.p32, tot);
+            AFN_TRY(mv32(h, wk.p32, nrhs, wk.q32, wk));
+            to64_kernel<<<g1(tot), 256, 0, s>>>(wk.q32, wk.q, tot);
+        }
         {
             Scope sc(&h->prof, K_BLAS1);
             launch_dot<double>(0, wk.p, wk.q, nullptr, nullptr, n, nrhs, M_ALPHA, cs, maxit, s);
@@ -769,8 +774,9 @@ afn_status pcg_solve(Handle *h, const double *b_perm, int nrhs, double tol, doub
         if (iters) AFN_CUDA(cudaMemcpyAsync(iters, wk.cs.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
     } else if (h->opt.krylov != AFN_KRYLOV_RESTART) {
         init_rel_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(wk.cs.bnorm, drel, nrhs);
-        if (h->opt.krylov == AFN_KRYLOV_FP64)
-            AFN_TRY(mixed_reliable64(h, wk, nrhs, tol, maxit, drel, &steps));
+        if (h->opt.krylov == AFN_KRYLOV_FP64 || h->opt.krylov == AFN_KRYLOV_FP64_OPERATOR)
+            AFN_TRY(mixed_reliable64(h, wk, nrhs, tol, maxit, drel, &steps,
+                                     h->opt.krylov == AFN_KRYLOV_FP64_OPERATOR));
         else
             AFN_TRY(mixed_reliable(h, wk, nrhs, tol, maxit, drel, &steps));
         AFN_CUDA(cudaMemcpyAsync(x_perm, wk.x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));

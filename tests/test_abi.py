@@ -94,7 +94,7 @@ def test_bad_matvec_precision_rejected_without_gpu():
 def test_bad_krylov_and_auto_rho_rejected_without_gpu():
     from paper_2304_05460_gb300 import afn
     X = np.zeros((4, 3))
-    for kw in (dict(krylov=3), dict(krylov=-1), dict(auto_rho=-0.5), dict(auto_rho=float("nan"))):
+    for kw in (dict(krylov=4), dict(krylov=-1), dict(auto_rho=-0.5), dict(auto_rho=float("nan"))):
         with pytest.raises(afn.AfnError) as e:
             afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, 2, **kw)
         assert e.value.status == afn.AFN_ERR_ARG
