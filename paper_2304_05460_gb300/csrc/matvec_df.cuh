@@ -41,23 +41,6 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b)
     return r;
 }
 
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
-{
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ dfl df_add(dfl a, dfl b)
-{
-    float s, e;
-    two_sum(a.h, b.h, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-    return fast_two_sum(s, e);
-}
-
 // constants of the exponential, set once per kernel launch from the host
 struct DfExpTable {
     float t_h[64], t_l[64];     // 2^(j/64)
@@ -65,90 +48,11 @@ struct DfExpTable {
     float log2e_h, log2e_l;      // log2 e
 };
 
-// 2^u for a double-float u <= 0 (0 below 2^-125, where the kernel value is
-// negligible next to the unit diagonal)
-__device__ __forceinline__ dfl df_exp2_neg(dfl u, const DfExpTable &T)
-{
-    dfl r{0.f, 0.f};
-    if (!(u.h > -125.f)) return r;
-    const float N = rintf(__fmul_rn(u.h, 64.f));
-    const int ni = (int)N;
-    const float gh = __fsub_rn(u.h, __fmul_rn(N, 0.015625f));   // exact (Sterbenz)
-    float s, e;
-    two_sum(gh, u.l, s, e);
-    const dfl g = fast_two_sum(s, e);
-    const int j = ni & 63;
-    const int m = (ni - j) >> 6;
-    const dfl y = df_mul(g, dfl{T.ln2_h, T.ln2_l});
-    // e^y - 1 = y + y^2/2 + y^3 (1/6 + y/24 + y^2/120 + y^3/720)
-    float q = __fmaf_rn(y.h, 1.f / 720.f, 1.f / 120.f);
-    q = __fmaf_rn(q, y.h, 1.f / 24.f);
-    q = __fmaf_rn(q, y.h, 1.f / 6.f);
-    const float y3 = __fmul_rn(__fmul_rn(y.h, y.h), y.h);
-    const float tail = __fmul_rn(q, y3);
-    const float p2 = __fmul_rn(y.h, y.h);
-    float p2e = __fmaf_rn(y.h, y.h, -p2);
-    p2e = __fmaf_rn(__fmul_rn(2.f, y.h), y.l, p2e);
-    dfl half_y2 = fast_two_sum(__fmul_rn(0.5f, p2), __fmul_rn(0.5f, p2e));
-    dfl em1 = df_add(half_y2, dfl{tail, 0.f});
-    em1 = df_add(y, em1);
-    const dfl ey = df_add(dfl{1.f, 0.f}, em1);
-    r = df_mul(dfl{T.t_h[j], T.t_l[j]}, ey);
-    const float sc = __int_as_float((m + 127) << 23);   // 2^m, m >= -126
-    r.h = __fmul_rn(r.h, sc);
-    r.l = __fmul_rn(r.l, sc);
-    return r;
-}
-
-// squared distance of prescaled double-float coordinates (row i in xi,
-// point j at xj), summed over the DS dimensions in order
-template <int DS>
-__device__ __forceinline__ dfl df_dist2(const dfl (&xi)[DS], const float2 *xj)
-{
-    float zh = 0.f, zc = 0.f;
-#pragma unroll
-    for (int q = 0; q < DS; ++q) {
-        const float2 b = xj[q];
-        float s, e;
-        two_sum(xi[q].h, -b.x, s, e);
-        e = __fadd_rn(e, __fsub_rn(xi[q].l, b.y));
-        const dfl dd = fast_two_sum(s, e);
-        const float p = __fmul_rn(dd.h, dd.h);
-        float pe = __fmaf_rn(dd.h, dd.h, -p);
-        pe = __fmaf_rn(__fmul_rn(2.f, dd.h), dd.l, pe);
-        float t;
-        two_sum(zh, p, zh, t);
-        zc = __fadd_rn(zc, __fadd_rn(t, pe));
-    }
-    return fast_two_sum(zh, zc);
-}
-
-// kernel value from the prescaled squared distance z:
-//   Gaussian (coordinates x sqrt(log2 e)/l):  2^-z
-//   Matern-3/2 (coordinates x sqrt(3)/l):     (1 + t) e^-t, t = sqrt(z)
-template <int KER>
-__device__ __forceinline__ dfl df_kernel(dfl z, const DfExpTable &T)
-{
-    if (KER == 0) return df_exp2_neg(dfl{-z.h, -z.l}, T);
-    dfl t{0.f, 0.f};
-    if (z.h > 0.f) {
-        // t = sqrt(z): one Newton step on the single-precision root in
-        // double-float (Karp and Markstein 1997)
-        const float t0 = __fsqrt_rn(z.h);
-        const float p = __fmul_rn(t0, t0);
-        const float pe = __fmaf_rn(t0, t0, -p);
-        const float rr = __fadd_rn(__fsub_rn(__fsub_rn(z.h, p), pe), z.l);
-        t = fast_two_sum(t0, __fdiv_rn(rr, __fmul_rn(2.f, t0)));
-    }
-    const dfl u = df_mul(t, dfl{T.log2e_h, T.log2e_l});
-    const dfl ex = df_exp2_neg(dfl{-u.h, -u.l}, T);
-    return df_mul(df_add(dfl{1.f, 0.f}, t), ex);
-}
-
-// ---- two pairs per instruction -------------------------------------------
-// The same operations on two independent values at once with Blackwell's
-// packed f32x2 add / sub / mul / fma (low half = first value): every rounding
-// is the scalar one, so each half equals the scalar result bit for bit.
+// ---- two values per instruction --------------------------------------------
+// Every operation below acts on two independent values at once with
+// Blackwell's packed f32x2 add / sub / mul / fma (low half = first value);
+// each half is rounded exactly as the scalar .rn operation would be, so the
+// halves are the scalar results bit for bit.
 struct dfl2 {
     f2_t h, l;
 };
@@ -196,7 +100,9 @@ __device__ __forceinline__ dfl2 df_add2(dfl2 a, dfl2 b)
     return fast_two_sum2(s, e);
 }
 
-// df_exp2_neg for two values
+// 2^u for double-float u <= 0, two values (0 below 2^-125, where the kernel
+// value is negligible next to the unit diagonal): -u = m + j/64 + g with
+// |g| <= 1/128, 2^u = 2^m 2^(j/64) e^(g ln 2)
 __device__ __forceinline__ dfl2 df_exp2_neg2(dfl2 u, const DfExpTable &T)
 {
     float uh0, uh1;
@@ -236,8 +142,9 @@ __device__ __forceinline__ dfl2 df_exp2_neg2(dfl2 u, const DfExpTable &T)
     return dfl2{f2_pack(rh0, rh1), f2_pack(rl0, rl1)};
 }
 
-// df_dist2 for two points j0, j1 whose coordinates come as packed pairs:
-// xj[q] = {h(j0), h(j1), l(j0), l(j1)}; xi is the same row point for both
+// squared distance of prescaled double-float coordinates, summed over the DS
+// dimensions in order, for the row point xi and two points j0, j1 whose
+// coordinates come as packed pairs: xj[q] = {h(j0), h(j1), l(j0), l(j1)}
 template <int DS>
 __device__ __forceinline__ dfl2 df_dist2_2(const dfl (&xi)[DS], const float4 *xj)
 {
@@ -259,6 +166,11 @@ __device__ __forceinline__ dfl2 df_dist2_2(const dfl (&xi)[DS], const float4 *xj
     return fast_two_sum2(zh, zc);
 }
 
+// kernel value from the prescaled squared distance z, two values:
+//   Gaussian (coordinates x sqrt(log2 e)/l):  2^-z
+//   Matern-3/2 (coordinates x sqrt(3)/l):     (1 + t) e^-t, t = sqrt(z) by one
+//   Newton step on the single-precision root in double-float (Karp and
+//   Markstein 1997)
 template <int KER>
 __device__ __forceinline__ dfl2 df_kernel2(dfl2 z, const DfExpTable &T)
 {

@@ -79,36 +79,16 @@ __device__ __forceinline__ void fence_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// nearest multiple of g = 2^(-7-8s) to r, with c = 1.5 * 2^23 * g (|r| < 2^22 g)
-__device__ __forceinline__ float du_round(float r, float c)
-{
-    return __fsub_rn(__fadd_rn(r, c), c);
-}
-
-// the eight base-256 digits of a double-float kernel value 0 <= v <= 1:
-// v = sum_s d[s] 2^(-7-8s) up to 2^-64; the low float is merged into the
-// remainder twice (after digits 2 and 5), where it can first reach a digit
-__device__ __forceinline__ void du_digits(dfl v, float (&d)[DU_DIG])
-{
-    float r = v.h, rl = v.l, a;
-    a = du_round(r, 0x1.8p16f);  r = __fsub_rn(r, a); d[0] = a * 0x1p7f;
-    a = du_round(r, 0x1.8p8f);   r = __fsub_rn(r, a); d[1] = a * 0x1p15f;
-    a = du_round(r, 0x1.8p0f);   r = __fsub_rn(r, a); d[2] = a * 0x1p23f;
-    two_sum(r, rl, r, rl);
-    a = du_round(r, 0x1.8p-8f);  r = __fsub_rn(r, a); d[3] = a * 0x1p31f;
-    a = du_round(r, 0x1.8p-16f); r = __fsub_rn(r, a); d[4] = a * 0x1p39f;
-    a = du_round(r, 0x1.8p-24f); r = __fsub_rn(r, a); d[5] = a * 0x1p47f;
-    two_sum(r, rl, r, rl);
-    a = du_round(r, 0x1.8p-32f); r = __fsub_rn(r, a); d[6] = a * 0x1p55f;
-    a = du_round(__fadd_rn(r, rl), 0x1.8p-40f);       d[7] = a * 0x1p63f;
-}
-
-// du_digits for two values at once (packed f32x2, the same roundings)
+// nearest multiple of g = 2^(-7-8s) to r, with c = 1.5 * 2^23 * g (|r| < 2^22 g),
+// two values
 __device__ __forceinline__ f2_t du_round2(f2_t r, float c)
 {
     return f2_sub(f2_add(r, f2_splat(c)), f2_splat(c));
 }
 
+// the eight base-256 digits of two double-float kernel values 0 <= v <= 1:
+// v = sum_s d[s] 2^(-7-8s) up to 2^-64; the low float is merged into the
+// remainder twice (after digits 2 and 5), where it can first reach a digit
 __device__ __forceinline__ void du_digits2(dfl2 v, f2_t (&d)[DU_DIG])
 {
     f2_t r = v.h, rl = v.l, a;
