@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT) matvec32p_kernel(const float *__restrict__
 // Xdup / Psp arrays; one partial per (chunk, column), summed in order by
 // matvec_finish.
 template <int DS, int NB, int KER>
-__global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? AFN_TC_MINB : 2)
+__global__ void __launch_bounds__(256, (2 * DS + 12 * NB + 24 <= 80) ? TC_MINB : 2)
     matvec32tca_kernel(const float *__restrict__ Xs, int64_t n, const f2_t *__restrict__ Xdup,
                        const uint32_t *__restrict__ Psp, float *__restrict__ part, int64_t chunk,
                        int *__restrict__ err)
@@ -531,11 +531,7 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
                      int64_t chunk, const TcPrep &tp, cudaStream_t s)
 {
     dim3 grid((unsigned)((n + TI - 1) / TI), (unsigned)js);
-#ifdef AFN_NO_TC
-    constexpr bool use_tc = false;   // tuning build: CUDA-core kernels only
-#else
     constexpr bool use_tc = true;
-#endif
     if constexpr (NR == 64) {
         // only the tcgen05 path takes 64-column pieces
         constexpr int DS = (D == 3 ? 4 : D);
@@ -632,11 +628,7 @@ afn_status matvec32(const float *Xs, int64_t n, int dp, int kernel, float mu, co
         }
     }
     for (int c0 = 0; c0 < nrhs;) {
-#ifdef AFN_NO_TC
-        int b = piece(nrhs - c0, 16);
-#else
         int b = piece(nrhs - c0, tp.umma ? piece_cap(nrhs - c0) : 32);
-#endif
         const float *pp = p + (int64_t)c0 * n;
         if (kernel == 0) launch32_d<0>(dp, b, Xs, n, pp, part, js, chunk, tp, s);
         else launch32_d<1>(dp, b, Xs, n, pp, part, js, chunk, tp, s);

@@ -22,38 +22,18 @@ namespace afn {
 // t = lane%4, A holds (g,t) (g+8,t) (g,t+4) (g+8,t+4); B holds (t,g) (t+4,g);
 // C holds (g,2t) (g,2t+1) (g+8,2t) (g+8,2t+1).
 // --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tf32_bits(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-#ifndef AFN_TC_MINB
-#define AFN_TC_MINB 3
-#endif
-#ifndef AFN_TC_FOLD
-#define AFN_TC_FOLD 2
-#endif
-#ifndef AFN_TC_KAHAN
-#define AFN_TC_KAHAN 1
-#endif
-static constexpr int TC_FOLD = AFN_TC_FOLD;        // blocks of 8 points per accumulator fold
+static constexpr int TC_MINB = 3;                  // resident CTAs per SM of the mma.sync tile
+static constexpr int TC_FOLD = 2;                  // blocks of 8 points per accumulator fold
 static_assert(TC_FOLD >= 1 && 8 % TC_FOLD == 0, "a fold chunk must not cross a staged tile");
-static constexpr bool TC_KAHAN = AFN_TC_KAHAN != 0;
+static constexpr bool TC_KAHAN = true;             // accumulator folds are Kahan sums
 
 // x = hi + lo with hi, lo tf32 (10-bit mantissa) values, each rounded to
 // nearest (ties away from zero): adding half a unit of the 13 dropped bits
 // and masking them is that rounding for finite inputs.
 __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
 {
-#ifdef AFN_TC_CVT_SPLIT
-    hi = tf32_bits(x);
-    lo = tf32_bits(x - __uint_as_float(hi));
-#else
     hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
     lo = (__float_as_uint(x - __uint_as_float(hi)) + 0x1000u) & 0xffffe000u;
-#endif
 }
 
 __device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
