@@ -171,6 +171,89 @@ __global__ void __launch_bounds__(NT) matvec32_kernel(const float *__restrict__ 
     }
 }
 
+// One right-hand side, two rows per thread: the rows i and i + 64 of a
+// 128-row CTA share every staged x_j and p_j, and their distances, kernel
+// arguments and sums are f32x2 pairs (each half rounded as the scalar
+// operation).  The staged tile holds each coordinate and p_j twice,
+// {v, v}, so a packed operand is one shared load.  Per row the arithmetic is
+// that of matvec32_kernel: d ascending for r^2, j ascending within a j-group,
+// a Kahan fold per tile, j-groups summed in order.
+static constexpr int TI2 = 2 * TI;   // rows per CTA of the two-row form
+
+template <int D, int KER>
+__global__ void __launch_bounds__(NT) matvec32r2_kernel(const float *__restrict__ Xs, int64_t n,
+                                                        const float *__restrict__ P,
+                                                        float *__restrict__ part, int64_t chunk)
+{
+    constexpr int DS = (D == 3) ? 4 : D;
+    constexpr int TILE = TJ * D + TJ;                 // f2_t entries: coordinates, then p
+    __shared__ __align__(16) f2_t sm2[TILE];
+    f2_t *xs = sm2;
+    f2_t *ps = sm2 + TJ * D;
+    const int ti = threadIdx.x % TI;
+    const int g = threadIdx.x / TI;
+    const int64_t i0 = (int64_t)blockIdx.x * TI2 + ti, i1 = i0 + TI;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk;
+    const int64_t j1 = min(n, j0 + chunk);
+
+    f2_t xi[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t)
+        xi[t] = f2_pack(i0 < n ? Xs[i0 * DS + t] : 0.f, i1 < n ? Xs[i1 * DS + t] : 0.f);
+    f2_t acc = 0ull, cmp = 0ull;
+    for (int64_t jt = j0; jt < j1; jt += TJ) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TJ * D; e += NT) {
+            const int jj = e / D, t = e % D;
+            const int64_t j = jt + jj;
+            const float v = j < j1 ? Xs[j * DS + t] : 0.f;
+            xs[e] = f2_pack(v, v);
+        }
+        for (int jj = threadIdx.x; jj < TJ; jj += NT) {
+            const int64_t j = jt + jj;
+            const float v = j < j1 ? P[j] : 0.f;
+            ps[jj] = f2_pack(v, v);
+        }
+        __syncthreads();
+        f2_t tac = 0ull;
+#pragma unroll 4
+        for (int jj = g * (TJ / JG); jj < (g + 1) * (TJ / JG); ++jj) {
+            const f2_t *xj = xs + jj * D;
+            f2_t r2 = 0ull;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const f2_t u = f2_sub(xi[t], xj[t]);
+                r2 = f2_fma(u, u, r2);
+            }
+            float ra, rb;
+            f2_unpack(r2, ra, rb);
+            tac = f2_fma(f2_pack(kernel32_scaled<KER>(ra), kernel32_scaled<KER>(rb)), ps[jj], tac);
+        }
+        const f2_t y = f2_sub(tac, cmp);
+        const f2_t t2 = f2_add(acc, y);
+        cmp = f2_sub(f2_sub(t2, acc), y);
+        acc = t2;
+    }
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(sm2);
+    float a0, a1;
+    f2_unpack(acc, a0, a1);
+    if (g > 0) {
+        red[((g - 1) * 2 + 0) * TI + ti] = a0;
+        red[((g - 1) * 2 + 1) * TI + ti] = a1;
+    }
+    __syncthreads();
+    if (g == 0) {
+        float s0 = a0, s1 = a1;
+        for (int q = 1; q < JG; ++q) {
+            s0 += red[((q - 1) * 2 + 0) * TI + ti];
+            s1 += red[((q - 1) * 2 + 1) * TI + ti];
+        }
+        if (i0 < n) part[(int64_t)blockIdx.y * n + i0] = s0;
+        if (i1 < n) part[(int64_t)blockIdx.y * n + i1] = s1;
+    }
+}
+
 // Packed variant for an even number of right-hand sides (NR in {2..32}):
 // coordinates, distances and the NR accumulators are f32x2 pairs, x_j and
 // p_j come from shared memory in 128-bit loads (p tile stored [j][c] with
@@ -558,7 +641,9 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
     } else if constexpr (NR >= 2) {
         matvec32p_kernel<(D == 3 ? 4 : D), NR, KER><<<grid, NT, 0, s>>>(Xs, n, P, n, part, chunk);
     } else {
-        matvec32_kernel<D, NR, KER><<<grid, NT, 0, s>>>(Xs, n, P, n, part, chunk);
+        // one right-hand side: two rows per thread
+        dim3 g2((unsigned)((n + TI2 - 1) / TI2), (unsigned)js);
+        matvec32r2_kernel<D, KER><<<g2, NT, 0, s>>>(Xs, n, P, part, chunk);
     }
 }
 
