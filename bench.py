@@ -734,7 +734,7 @@ def run_one_rhs(afn, s, Xd, Bd, stream, opts):
             "pcg_iters_max": iters,
             "roofline": {"bound": "alu", "achieved": ach, "peak": LANE_PEAK_TOPS, "unit": "Tops/s",
                          "frac": ach / LANE_PEAK_TOPS, "ops_per_pair": ops_pair,
-                         "kernel": "matvec32_kernel<D=8,NR=1,Gaussian> (CUDA cores)",
+                         "kernel": "matvec32r2_kernel<D=8,Gaussian> (CUDA cores, two rows per thread)",
                          "avg_launch_ms": avg, "launches": mv_cnt,
                          "mufu_bound_pairs_per_s": mufu_peak,
                          "pairs_per_s": float(n) * n / (avg / 1e3),
