@@ -248,6 +248,7 @@ def _cmp(a, b, rtol):
     (200, 4, G, 0.3, 1e-2, 33, 1),          # w = 1: diagonal G
     (1400, 3, G, 0.08, 1e-3, 1000, 4),      # k = 1000: batched and ragged blocks at every
                                             # level of the recursive triangular inverse
+    (1500, 3, M32, 0.2, 1e-3, 150, 100),    # w = 100 (the paper's FSAI-100): 128-wide tiles
 ])
 def test_build_parity_fp64(afn, n, d, ker, l, mu, k, w):
     X = inputs.uniform_points(n, d, 500 + n)
@@ -325,16 +326,18 @@ def test_build_maximin_schur_order(afn, ker, d, l, w):
     assert e.value.status == afn.AFN_ERR_ARG
 
 
-def test_build_mixed_close_to_oracle(afn):
+@pytest.mark.parametrize("w", [24, 100])
+def test_build_mixed_close_to_oracle(afn, w):
+    # w = 100: the FP32 FSAI build with the 128-wide Schur blocks
     X = inputs.uniform_points(1200, 3, 700)
-    ref = oracle.afn_build(X, G, 0.1, 1e-3, 120, 24)
-    h = afn.afn_build(X, G, 0.1, 1e-3, 120, 24, precision=afn.PREC_MIXED)
+    ref = oracle.afn_build(X, G, 0.1, 1e-3, 120, w)
+    h = afn.afn_build(X, G, 0.1, 1e-3, 120, w, precision=afn.PREC_MIXED)
     assert np.array_equal(afn.afn_get_perm(h), ref["perm"])
     pat, Gv = afn.afn_get_G(h)
     assert np.array_equal(pat, ref["pattern"])
     assert _cmp(afn.afn_get_L(h), ref["L"], 0) <= 1e-10      # Cholesky stays FP64
     assert _cmp(Gv, ref["G"], 0) <= 1e-2                      # FP32 Schur blocks
-    # W^T = K21 L^{-T} from the FP32 kernel block and the FP32 triangular inverse
+    # W^T = K21 L^{-T} from the FP32 kernel block and the triangular inverse (FP64, rounded)
     W = np.linalg.solve(ref["L"], ref["K12"]).T
     errw = _cmp(afn.afn_get_W(h), W, 0)
     assert errw <= 1e-3, errw
