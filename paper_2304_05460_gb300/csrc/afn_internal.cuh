@@ -252,6 +252,8 @@ afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaS
 // C (m x k) = A (m x k) U, U (k x k) upper triangular, FP32 row-major (tiled SGEMM)
 afn_status gemm_upper32(const float *A, int64_t m, int64_t k, const float *U, float *C, cudaStream_t s);
 afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s);
+// the same in double-float arithmetic on the FP32 pipes (double-float handles)
+afn_status gemm_upper_df(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s);
 afn_status kernel_block32(const float *Xa, int64_t na, const float *Xb, int64_t nb, int dp,
                           int kernel, float *out, int64_t ld, cudaStream_t s);
 afn_status convert64to32(const double *a, float *b, int64_t count, cudaStream_t s);
@@ -261,6 +263,10 @@ afn_status convert32to64(const float *a, double *b, int64_t count, cudaStream_t 
 afn_status fsai_build64(const double *Xr, int64_t nr, int d, KParams kp, const double *Wt,
                         int64_t k, const int32_t *pat, int w, double *G, int *status,
                         cudaStream_t s);
+// the same with the Gram in double-float arithmetic on the FP32 pipes (double-float handles)
+afn_status fsai_build_df(const double *Xr, int64_t nr, int d, KParams kp, const double *Wt,
+                         int64_t k, const int32_t *pat, int w, double *G, int *status,
+                         cudaStream_t s);
 afn_status fsai_build32(const double *Xr, int64_t nr, int d, KParams kp, const float *Wt,
                         int64_t k, const int32_t *pat, int w, double *G, int *status,
                         cudaStream_t s);

@@ -473,7 +473,12 @@ static afn_status build_impl(Handle *h, const double *points)
                 DevBuf K21;
                 AFN_TRY(K21.alloc(sizeof(double) * (size_t)(nr * k)));
                 AFN_TRY(kernel_block(Xr, nr, Xk, k, d, kp, 0.0, K21.as<double>(), k, s));
-                AFN_TRY(gemm_upper64(K21.as<double>(), nr, k, h->LinvT.as<double>(), h->Wt.as<double>(), s));
+                // FP64 handles in FP64; double-float handles in double-float arithmetic on the
+                // FP32 pipes (the same 48-bit accuracy their matvec has, far faster)
+                if (h->precision == AFN_PREC_DF)
+                    AFN_TRY(gemm_upper_df(K21.as<double>(), nr, k, h->LinvT.as<double>(), h->Wt.as<double>(), s));
+                else
+                    AFN_TRY(gemm_upper64(K21.as<double>(), nr, k, h->LinvT.as<double>(), h->Wt.as<double>(), s));
             }
             if (mixed) {
                 // FP64 factors rounded to FP32 for the apply of the mixed solves
@@ -528,7 +533,8 @@ static afn_status build_impl(Handle *h, const double *points)
         {
             Scope sc(&h->prof, K_FSAI);
             if (!mixed || f64fac)
-                AFN_TRY(fsai_build64(Xr, nr, d, kp, k > 0 ? h->Wt.as<double>() : nullptr, k,
+                AFN_TRY((h->precision == AFN_PREC_DF ? fsai_build_df : fsai_build64)(
+                    Xr, nr, d, kp, k > 0 ? h->Wt.as<double>() : nullptr, k,
                                      h->pat.as<int32_t>(), w, h->G.as<double>(), st, s));
             else
                 AFN_TRY(fsai_build32(Xr, nr, d, kp, h->Wt32.as<float>(), k, h->pat.as<int32_t>(), w,

@@ -507,6 +507,111 @@ afn_status tri_inverse64(const double *L, int64_t k, double *Linv, double *LinvT
 }
 
 
+// The same product with FP64 operands and result but double-float arithmetic
+// on the FP32 pipes (GB300 retires about 64 FP32 operations per FP64 one):
+// each operand is split on staging into hi + lo floats (hi = float(x), lo =
+// float(x - hi)), each product term is formed exactly by the FMA-based
+// TwoProduct of the hi parts plus the two cross terms (Dekker 1971), and
+// the running sum is a double-float (Knuth's TwoSum on the high parts, the
+// low parts added); the result is hi + lo in FP64.  Relative error about
+// K 2^-48 of sum |a b|, for the W products of double-float handles.
+static constexpr int DF_B = 64, DF_BK = 8;
+
+__global__ void __launch_bounds__(256) dfgemm_upper_kernel(const double *__restrict__ A, int64_t lda,
+                                                           const double *__restrict__ B, int64_t ldb,
+                                                           double *__restrict__ C, int64_t ldc,
+                                                           int64_t M, int64_t N, int64_t K)
+{
+    __shared__ __align__(16) float Ah[2][DF_BK][DF_B], Al[2][DF_BK][DF_B];
+    __shared__ __align__(16) float Bh[2][DF_BK][DF_B], Bl[2][DF_BK][DF_B];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * DF_B, n0 = (int64_t)blockIdx.x * DF_B;
+    const int64_t khi = min(K, n0 + DF_B);              // B upper triangular
+    const int am = tid / 4, ak = (tid % 4) * 2;
+    const int bk = tid / 32, bn = (tid % 32) * 2;
+    double ra[2], rb[2];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t gm = m0 + am, gk = k0 + ak + u;
+            ra[u] = (gm < M && gk < khi) ? A[gm * lda + gk] : 0.0;
+            const int64_t gq = k0 + bk, gp = n0 + bn + u;
+            rb[u] = (gq < khi && gp < N) ? B[gq * ldb + gp] : 0.0;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float ah = (float)ra[u], bh = (float)rb[u];
+            Ah[buf][ak + u][am] = ah;
+            Al[buf][ak + u][am] = (float)(ra[u] - (double)ah);
+            Bh[buf][bk][bn + u] = bh;
+            Bl[buf][bk][bn + u] = (float)(rb[u] - (double)bh);
+        }
+    };
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+    const int nt = (int)((khi + DF_BK - 1) / DF_BK);
+    if (nt > 0) {
+        fetch(0);
+        stash(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nt) fetch((int64_t)(t + 1) * DF_BK);
+#pragma unroll
+        for (int kk = 0; kk < DF_BK; ++kk) {
+            float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ah[i] = Ah[buf][kk][ty * 4 + i];
+                al[i] = Al[buf][kk][ty * 4 + i];
+                bh[i] = Bh[buf][kk][tx * 4 + i];
+                bl[i] = Bl[buf][kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = __fmul_rn(ah[i], bh[j]);
+                    float e = __fmaf_rn(ah[i], bh[j], -p);
+                    e = __fmaf_rn(ah[i], bl[j], e);
+                    e = __fmaf_rn(al[i], bh[j], e);
+                    const float s1 = __fadd_rn(sh[i][j], p);
+                    const float bb = __fsub_rn(s1, sh[i][j]);
+                    const float err = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+                    sh[i][j] = s1;
+                    sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(err, e));
+                }
+        }
+        if (t + 1 < nt) stash(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gp = n0 + tx * 4 + j;
+            if (gp < N) C[gm * ldc + gp] = (double)sh[i][j] + (double)sl[i][j];
+        }
+    }
+}
+
+afn_status gemm_upper_df(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s)
+{
+    if (m <= 0 || k <= 0) return AFN_OK;
+    dim3 g((unsigned)((k + DF_B - 1) / DF_B), (unsigned)((m + DF_B - 1) / DF_B));
+    dfgemm_upper_kernel<<<g, 256, 0, s>>>(A, k, U, k, C, k, m, k, k);
+    AFN_CUDA(cudaGetLastError());
+    return AFN_OK;
+}
+
 // C (m x k) = A (m x k) U with U (k x k) upper triangular, FP64, row-major
 afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s)
 {

@@ -9,6 +9,7 @@
 // run in shared memory in FP64.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "afn_device.cuh"
 #include "afn_internal.cuh"
@@ -18,17 +19,23 @@ namespace afn {
 static constexpr int KC = 32;    // landmarks per Gram chunk
 
 // FT threads per CTA (autotuned: 128 or 256 for w <= 64, 256 or 512 above;
-// every Gram entry and Cholesky step is the same sum whatever FT is)
-template <int WM, class TW, int FT>
+// every Gram entry and Cholesky step is the same sum whatever FT is).
+// GDF (FP64 W only): the Gram in double-float arithmetic on the FP32 pipes,
+// each staged W value split into hi + lo floats, each term by the FMA-based
+// TwoProduct and the sums double-float (about 48-bit accuracy, for the
+// double-float handles; GB300's FP64 pipe is far slower).
+template <int WM, class TW, int FT, bool GDF>
 __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr, int d, int kernel,
                                                   double l, double mu,
                                                   const TW *__restrict__ Wt, int64_t k,
                                                   const int32_t *__restrict__ pat, int w,
                                                   double *__restrict__ G, int *status)
 {
+    static_assert(!GDF || sizeof(TW) == 8, "the double-float Gram takes FP64 W");
+    using WS = std::conditional_t<GDF, float2, TW>;             // staged W value
     extern __shared__ __align__(16) unsigned char smraw[];
     double *A = reinterpret_cast<double *>(smraw);              // WM x (WM+1)
-    TW *ws = reinterpret_cast<TW *>(A + WM * (WM + 1));          // WM x (KC+1)
+    WS *ws = reinterpret_cast<WS *>(A + WM * (WM + 1));          // WM x (KC+1)
     __shared__ int32_t s[WM];
     __shared__ int m_s;
     __shared__ double piv;
@@ -51,14 +58,18 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
     constexpr int MAXT = (NTL * (NTL + 1) / 2 + FT - 1) / FT;
     const int nt = (m + 3) / 4;
     const int ntt = nt * (nt + 1) / 2;
-    TW acc[MAXT][4][4];
+    TW acc[GDF ? 1 : MAXT][4][4];                 // the Gram in TW
+    float acch[GDF ? MAXT : 1][4][4], accl[GDF ? MAXT : 1][4][4];   // or in double-float
     int ta[MAXT], tb[MAXT];
 #pragma unroll
     for (int q = 0; q < MAXT; ++q) {
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[q][r][c] = 0;
+            for (int c = 0; c < 4; ++c) {
+                if constexpr (GDF) acch[q][r][c] = accl[q][r][c] = 0.f;
+                else acc[q][r][c] = 0;
+            }
         const int p = tid + q * FT;
         int a = 0, b = 0;
         if (p < ntt) {
@@ -77,17 +88,23 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
         for (int e = tid; e < 4 * nt * KC; e += FT) {
             int a = e / KC, kk = e % KC;
             int64_t gk = k0 + kk;
-            ws[a * (KC + 1) + kk] = (a < m && gk < k) ? Wt[(int64_t)s[a] * k + gk] : (TW)0;
+            const TW v = (a < m && gk < k) ? Wt[(int64_t)s[a] * k + gk] : (TW)0;
+            if constexpr (GDF) {
+                const float h = (float)v;
+                ws[a * (KC + 1) + kk] = make_float2(h, (float)((double)v - (double)h));
+            } else {
+                ws[a * (KC + 1) + kk] = v;
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < MAXT; ++q) {
             if (tid + q * FT < ntt) {
-                const TW *wa = ws + 4 * ta[q] * (KC + 1);
-                const TW *wb = ws + 4 * tb[q] * (KC + 1);
+                const WS *wa = ws + 4 * ta[q] * (KC + 1);
+                const WS *wb = ws + 4 * tb[q] * (KC + 1);
 #pragma unroll 4
                 for (int kk = 0; kk < KC; ++kk) {
-                    TW va[4], vb[4];
+                    WS va[4], vb[4];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         va[r] = wa[r * (KC + 1) + kk];
@@ -96,7 +113,22 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[q][r][c] += va[r] * vb[c];
+                        for (int c = 0; c < 4; ++c) {
+                            if constexpr (GDF) {
+                                const float p = __fmul_rn(va[r].x, vb[c].x);
+                                float e = __fmaf_rn(va[r].x, vb[c].x, -p);
+                                e = __fmaf_rn(va[r].x, vb[c].y, e);
+                                e = __fmaf_rn(va[r].y, vb[c].x, e);
+                                const float sh = acch[q][r][c];
+                                const float s1 = __fadd_rn(sh, p);
+                                const float bb = __fsub_rn(s1, sh);
+                                const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+                                acch[q][r][c] = s1;
+                                accl[q][r][c] = __fadd_rn(accl[q][r][c], __fadd_rn(er, e));
+                            } else {
+                                acc[q][r][c] += va[r] * vb[c];
+                            }
+                        }
                 }
             }
         }
@@ -114,7 +146,10 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
                         double r2 = sqdist_exact(Xr + (int64_t)s[a] * d, Xr + (int64_t)s[b] * d, d);
                         double v = kernel64(r2, kernel, l);
                         if (a == b) v += mu;
-                        A[a * (WM + 1) + b] = v - (double)acc[q][r][c];
+                        double gram;
+                        if constexpr (GDF) gram = (double)acch[q][r][c] + (double)accl[q][r][c];
+                        else gram = (double)acc[q][r][c];
+                        A[a * (WM + 1) + b] = v - gram;
                     }
                 }
         }
@@ -167,14 +202,14 @@ __global__ void __launch_bounds__(FT) fsai_kernel(const double *__restrict__ Xr,
     if (tid == 0 && bad) atomicExch(status, DEV_NOT_SPD);
 }
 
-template <int WM, class TW, int FT>
+template <int WM, class TW, int FT, bool GDF>
 static afn_status launch_fsai_ft(const double *Xr, int64_t nr, int d, KParams kp, const TW *Wt,
                                  int64_t k, const int32_t *pat, int w, double *G, int *status,
                                  cudaStream_t s)
 {
     size_t smem = sizeof(double) * WM * (WM + 1) +
                   std::max(sizeof(TW) * WM * (KC + 1), sizeof(double) * WM);
-    auto kfn = fsai_kernel<WM, TW, FT>;
+    auto kfn = fsai_kernel<WM, TW, FT, GDF>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "fsai smem attribute");
@@ -189,34 +224,35 @@ static afn_status launch_fsai_ft(const double *Xr, int64_t nr, int d, KParams kp
 }
 
 // the FSAI rows with the autotuned block size (each run writes the same G)
-template <int WM, class TW>
+template <int WM, class TW, bool GDF>
 static afn_status launch_fsai(const double *Xr, int64_t nr, int d, KParams kp, const TW *Wt,
                               int64_t k, const int32_t *pat, int w, double *G, int *status,
                               cudaStream_t s)
 {
     constexpr int FA = WM <= 64 ? 128 : 256;
     char key[96];
-    snprintf(key, sizeof(key), "fsai/wm%d/%s/k2^%d/nr2^%d/%s", WM, sizeof(TW) == 8 ? "f64" : "f32",
-             log2_bucket(k), log2_bucket(nr), tune_device_tag().c_str());
+    snprintf(key, sizeof(key), "fsai/wm%d/%s/k2^%d/nr2^%d/%s", WM,
+             GDF ? "df" : sizeof(TW) == 8 ? "f64" : "f32", log2_bucket(k), log2_bucket(nr),
+             tune_device_tag().c_str());
     afn_status st = AFN_OK;
     auto run = [&](int c) {
-        st = c == 0 ? launch_fsai_ft<WM, TW, FA>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s)
-                    : launch_fsai_ft<WM, TW, 2 * FA>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+        st = c == 0 ? launch_fsai_ft<WM, TW, FA, GDF>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s)
+                    : launch_fsai_ft<WM, TW, 2 * FA, GDF>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
     };
     tune_run(key, 2, run, s, 1);
     return st;
 }
 
-template <class TW>
+template <class TW, bool GDF>
 static afn_status fsai_build(const double *Xr, int64_t nr, int d, KParams kp, const TW *Wt,
                              int64_t k, const int32_t *pat, int w, double *G, int *status,
                              cudaStream_t s)
 {
     if (nr <= 0) return AFN_OK;
     AFN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-    if (w <= 32) return launch_fsai<32, TW>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
-    if (w <= 64) return launch_fsai<64, TW>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
-    if (w <= 128) return launch_fsai<128, TW>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+    if (w <= 32) return launch_fsai<32, TW, GDF>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+    if (w <= 64) return launch_fsai<64, TW, GDF>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+    if (w <= 128) return launch_fsai<128, TW, GDF>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
     set_error("fsai: w=%d above 128 is not supported", w);
     return AFN_ERR_ARG;
 }
@@ -225,14 +261,21 @@ afn_status fsai_build64(const double *Xr, int64_t nr, int d, KParams kp, const d
                         int64_t k, const int32_t *pat, int w, double *G, int *status,
                         cudaStream_t s)
 {
-    return fsai_build<double>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+    return fsai_build<double, false>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+}
+
+afn_status fsai_build_df(const double *Xr, int64_t nr, int d, KParams kp, const double *Wt,
+                         int64_t k, const int32_t *pat, int w, double *G, int *status,
+                         cudaStream_t s)
+{
+    return fsai_build<double, true>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
 }
 
 afn_status fsai_build32(const double *Xr, int64_t nr, int d, KParams kp, const float *Wt,
                         int64_t k, const int32_t *pat, int w, double *G, int *status,
                         cudaStream_t s)
 {
-    return fsai_build<float>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
+    return fsai_build<float, false>(Xr, nr, d, kp, Wt, k, pat, w, G, status, s);
 }
 
 // ------------------------------------------------ CSR of G^T (gather form) --

@@ -276,6 +276,27 @@ def test_build_parity_fp64(afn, n, d, ker, l, mu, k, w):
 
 
 @pytest.mark.parametrize("n,d,ker,l,mu,k,w", [(2000, 3, G, 0.1, 1e-4, 200, 32),
+                                               (900, 2, M32, 0.15, 1e-3, 90, 20),
+                                               (1400, 3, G, 0.08, 1e-3, 1000, 4),
+                                               (1500, 3, M32, 0.2, 1e-3, 150, 100)])
+def test_build_parity_df(afn, n, d, ker, l, mu, k, w):
+    # double-float handles: FP64 Cholesky and triangular inverse, W = K21 L^{-T} and the FSAI
+    # Gram in double-float arithmetic on the FP32 pipes (about 48-bit accuracy)
+    X = inputs.uniform_points(n, d, 500 + n)
+    ref = oracle.afn_build(X, ker, l, mu, k, w)
+    h = afn.afn_build(X, ker, l, mu, k, w, precision=afn.PREC_DF)
+    assert afn.afn_get_build_info(h).precision == afn.PREC_DF
+    assert np.array_equal(afn.afn_get_perm(h), ref["perm"])
+    assert _cmp(afn.afn_get_L(h), ref["L"], 0) <= 1e-10
+    W = np.linalg.solve(ref["L"], ref["K12"]).T
+    assert _cmp(afn.afn_get_W(h), W, 0) <= 1e-10
+    pat, Gv = afn.afn_get_G(h)
+    assert np.array_equal(pat, ref["pattern"])
+    assert _cmp(Gv, ref["G"], 0) <= 1e-10
+    afn.afn_free(h)
+
+
+@pytest.mark.parametrize("n,d,ker,l,mu,k,w", [(2000, 3, G, 0.1, 1e-4, 200, 32),
                                                (3001, 8, M32, 2.0, 1e-2, 300, 64)])
 def test_build_mixed_fp64_factors(afn, n, d, ker, l, mu, k, w):
     # factors = FP64: a mixed handle's W and G are built as for an FP64 handle (G within
