@@ -156,14 +156,26 @@ def _ptr(a):
 
 
 def _f64_rowmajor(a):
+    """n x d row-major float64 points (a 2-D array)."""
     if _is_torch(a):
         import torch
-        return a.to(torch.float64).contiguous()
-    return np.ascontiguousarray(a, dtype=np.float64)
+        t = a.to(torch.float64).contiguous()
+    else:
+        t = np.ascontiguousarray(a, dtype=np.float64)
+    if t.ndim != 2:
+        raise ValueError("points must have shape (n, d), got %s" % (tuple(t.shape),))
+    return t
 
 
-def _f64_colmajor(a):
-    """n x m column-major float64 (as a contiguous m x n transpose buffer)."""
+def _f64_colmajor(a, n=None, what="block"):
+    """n x m column-major float64 (as a contiguous m x n transpose buffer).  With
+    ``n`` given, a block with another number of rows is refused: the library
+    reads n x m values from the buffer and cannot see its size."""
+    nd = a.dim() if _is_torch(a) else np.ndim(a)
+    if nd not in (1, 2):
+        raise ValueError("%s must have shape (n,) or (n, m)" % what)
+    if n is not None and int(a.shape[0]) != int(n):
+        raise ValueError("%s has %d rows, expected n = %d" % (what, int(a.shape[0]), int(n)))
     if _is_torch(a):
         import torch
         t = a.to(torch.float64)
@@ -244,9 +256,7 @@ def afn_free(h: Handle):
 def afn_solve(h: Handle, rhs, tol):
     """PCG with the AFN preconditioner.  rhs: (n,) or (n, nrhs); returns
     (x, info) with info = dict(iters, relres, outer_steps, converged, solve_ms)."""
-    B, nrhs = _f64_colmajor(rhs)
-    if int(B.shape[-1]) != h.n:
-        raise ValueError("rhs has %d rows, handle has n=%d" % (B.shape[-1], h.n))
+    B, nrhs = _f64_colmajor(rhs, h.n, "rhs")
     out = _empty_like_kind(B, tuple(B.shape), np.float64)
     its = (C.c_int32 * nrhs)()
     rel = (C.c_double * nrhs)()
@@ -303,7 +313,7 @@ def afn_get_W(h: Handle):
 def afn_apply_precond(h: Handle, r):
     """M^{-1} r (Alg. 3); r in PERMUTED order, (n,) or (n, nrhs).  FP64 handles
     apply in FP64, mixed handles run the FP32 apply of their solves."""
-    R, nrhs = _f64_colmajor(r)
+    R, nrhs = _f64_colmajor(r, h.n, "r")
     out = np.empty(R.shape, dtype=np.float64)
     pr, kr = _ptr(R)
     _check(_lib.afn_apply_precond(h.ptr, pr, nrhs, _ptr(out)[0]))
@@ -372,7 +382,7 @@ def afn_kernel_matvec(points, kernel, l, mu, p, precision=PREC_FP64, stream=None
     """(K + mu I) p, matrix-free; p (n,) or (n, nrhs)."""
     X = _f64_rowmajor(points)
     n, d = int(X.shape[0]), int(X.shape[1])
-    Pm, nrhs = _f64_colmajor(p)
+    Pm, nrhs = _f64_colmajor(p, n, "p")
     out = _empty_like_kind(Pm, tuple(Pm.shape), np.float64)
     px, kx = _ptr(X)
     pp, kp = _ptr(Pm)
@@ -516,9 +526,7 @@ def afn_solve_batched(b: Batch, rhs, tol):
     cols = []
     nr = []
     for i, r in enumerate(rhs):
-        Bc, m = _f64_colmajor(r)
-        if int(Bc.shape[-1]) != b.n[i]:
-            raise ValueError("rhs %d has %d rows, system has n=%d" % (i, Bc.shape[-1], b.n[i]))
+        Bc, m = _f64_colmajor(r, b.n[i], "rhs %d" % i)
         cols.append(Bc.reshape(-1))
         nr.append(m)
     if _is_torch(cols[0]):
@@ -618,7 +626,7 @@ class Server:
         """system: dict(points, kernel, l, mu, k_max, fsai_nnz); rhs (n,) or
         (n, nrhs).  Returns the request id."""
         X = _f64_rowmajor(system["points"])
-        Bc, m = _f64_colmajor(rhs)
+        Bc, m = _f64_colmajor(rhs, X.shape[0], "rhs")
         px, kx = _ptr(X)
         pb, kb = _ptr(Bc)
         sy = afn_system(px, int(X.shape[0]), int(X.shape[1]), int(system["kernel"]),

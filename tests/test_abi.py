@@ -142,3 +142,31 @@ def test_noalloc_binding_refuses_bad_tensors_before_any_launch():
             afn.afn_kernel_matvec_noalloc(pts, afn.GAUSSIAN, 1.0, 1e-2, p, q)
         if msg:
             assert msg in str(e.value), (msg, str(e.value))
+
+
+def test_binding_refuses_blocks_of_the_wrong_size_before_any_launch():
+    # the library reads n x nrhs values from a right-hand-side block and cannot see the
+    # buffer's size, so the binding refuses a block whose rows differ from n (and
+    # points or blocks that are not 2-D / 1-D) before calling it
+    from paper_2304_05460_gb300 import afn
+    X = np.zeros((10, 3))
+    for p in (np.zeros(9), np.zeros((11, 2)), np.zeros((10, 2, 2))):
+        with pytest.raises(ValueError):
+            afn.afn_kernel_matvec(X, afn.GAUSSIAN, 1.0, 1e-2, p)
+    with pytest.raises(ValueError):
+        afn.afn_kernel_matvec(np.zeros(10), afn.GAUSSIAN, 1.0, 1e-2, np.zeros(10))
+    with pytest.raises(ValueError):
+        afn.afn_build(np.zeros((2, 5, 3)), afn.GAUSSIAN, 1.0, 1e-2, 2, 2)
+
+    class FakeHandle:
+        ptr, n = None, 10
+    for r in (np.zeros(9), np.zeros((12, 1))):
+        with pytest.raises(ValueError):
+            afn.afn_solve(FakeHandle(), r, 1e-6)
+        with pytest.raises(ValueError):
+            afn.afn_apply_precond(FakeHandle(), r)
+
+    class FakeBatch:
+        ptr, nsys, n = None, 2, [10, 20]
+    with pytest.raises(ValueError):
+        afn.afn_solve_batched(FakeBatch(), [np.zeros(10), np.zeros(19)], 1e-6)
