@@ -179,8 +179,8 @@ void afn_default_options(afn_options *opt);
  *   uniform sampling; L = chol(K11 + mu I); W = L^{-1} K12; FSAI pattern of
  *   each Schur row = its fsai_nnz-1 nearest lower-numbered neighbours plus
  *   itself (Sec. 3.1); G = FSAI of the Schur complement (Alg. 1).
- * kernel: afn_kernel.  l > 0, mu > 0, k_max >= 0, fsai_nnz >= 1 (clamped to
- * n - k).  opt may be NULL (defaults).  On success *out owns all device state.
+ * kernel: afn_kernel.  l > 0, mu > 0, k_max >= 0, 1 <= fsai_nnz <= 128
+ * (clamped to n - k).  opt may be NULL (defaults).  On success *out owns all device state.
  * Errors: AFN_ERR_ARG, AFN_ERR_OOM, AFN_ERR_NOT_SPD, AFN_ERR_TIMEOUT, AFN_ERR_CUDA.
  */
 afn_status afn_build(const double *points, int64_t n, int32_t d, int32_t kernel, double l,
@@ -375,7 +375,7 @@ typedef struct {
     int32_t kernel;         /* afn_kernel */
     double l, mu;           /* > 0 */
     int32_t k_max;          /* landmarks (clamped to [0, n]; Alg. 4 when opt.rank_mode = 1) */
-    int32_t fsai_nnz;       /* w, nonzeros per row of G including the diagonal */
+    int32_t fsai_nnz;       /* w, nonzeros per row of G including the diagonal (1..128) */
 } afn_system;
 
 typedef struct afn_batch afn_batch;

@@ -571,7 +571,8 @@ afn_status create_handle(const double *points, int64_t n, int d, int kernel, dou
 {
     *out = nullptr;
     if (!points || n < 1 || d < 1 || d > 16 || (kernel != 0 && kernel != 1) || !(l > 0) ||
-        !std::isfinite(l) || !(mu > 0) || !std::isfinite(mu) || k_max < 0 || fsai_nnz < 1) {
+        !std::isfinite(l) || !(mu > 0) || !std::isfinite(mu) || k_max < 0 || fsai_nnz < 1 ||
+        fsai_nnz > 128) {
         set_error("afn_build: invalid argument (n=%lld d=%d kernel=%d l=%g mu=%g k_max=%d w=%d)",
                   (long long)n, d, kernel, l, mu, k_max, fsai_nnz);
         return AFN_ERR_ARG;

@@ -66,6 +66,10 @@ def test_argument_checks_without_gpu():
     with pytest.raises(afn.AfnError) as e:
         afn.afn_build(X, 5, 1.0, 1e-3, 2, 2)                  # unknown kernel
     assert e.value.status == afn.AFN_ERR_ARG
+    for w in (0, 129):                                       # FSAI width outside 1..128
+        with pytest.raises(afn.AfnError) as e:
+            afn.afn_build(X, afn.GAUSSIAN, 1.0, 1e-3, 2, w)
+        assert e.value.status == afn.AFN_ERR_ARG
 
 
 def test_default_options():
