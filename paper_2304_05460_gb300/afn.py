@@ -171,7 +171,9 @@ def _f64_colmajor(a, n=None, what="block"):
     """n x m column-major float64 (as a contiguous m x n transpose buffer).  With
     ``n`` given, a block with another number of rows is refused: the library
     reads n x m values from the buffer and cannot see its size."""
-    nd = a.dim() if _is_torch(a) else np.ndim(a)
+    if not _is_torch(a):
+        a = np.asarray(a, dtype=np.float64)
+    nd = a.dim() if _is_torch(a) else a.ndim
     if nd not in (1, 2):
         raise ValueError("%s must have shape (n,) or (n, m)" % what)
     if n is not None and int(a.shape[0]) != int(n):
