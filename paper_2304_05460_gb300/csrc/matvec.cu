@@ -614,7 +614,6 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
                      int64_t chunk, const TcPrep &tp, cudaStream_t s)
 {
     dim3 grid((unsigned)((n + TI - 1) / TI), (unsigned)js);
-    constexpr bool use_tc = true;
     if constexpr (NR == 64) {
         // only the tcgen05 path takes 64-column pieces
         constexpr int DS = (D == 3 ? 4 : D);
@@ -623,7 +622,7 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
         launch_u_any<DS, 8, KER>(Xs, n, reinterpret_cast<float *>(tp.Xdup), tp.Psp, part, tp.jsu,
                                  tp.chunk_st, tp.npad, tp.err, s);
         return;
-    } else if constexpr (NR >= 16 && use_tc) {
+    } else if constexpr (NR >= 16) {
         if (tp.umma) {
             constexpr int DS = (D == 3 ? 4 : D);
             const int64_t tot = tp.npad * NR;
@@ -633,7 +632,7 @@ static void launch32(const float *Xs, int64_t n, const float *P, float *part, in
             return;
         }
     }
-    if constexpr (NR >= 8 && use_tc) {
+    if constexpr (NR >= 8) {
         constexpr int DS = (D == 3 ? 4 : D);
         const int64_t tot = tp.npad * NR;
         psplit_kernel<NR / 8><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, n, n, tp.npad, tp.Psp);
