@@ -157,13 +157,23 @@ class Clocks:
 FP64_ITERS = {0.5: 8, 1.0: 227, 2.0: 801, 4.0: 362}
 
 
-def oracle_sample(n, nrhs, budget_s=20.0, iters_hint=None):
+# sizes of the oracle's bounded sample: "step" for each step of the reference arm (about 2 s
+# on 16 host cores), "baseline" for the in-bench CPU baseline (about 10 s): FPS steps timed,
+# landmarks of the timed Cholesky, FSAI rows with their literal Schur blocks, pattern rows of
+# the timed KNN, matvec rows
+SAMPLE_SIZES = {"step": dict(fps=400, kc=1200, fsai=8, knn=2000, mv=16),
+                "baseline": dict(fps=2000, kc=2000, fsai=96, knn=4000, mv=1024)}
+
+
+def oracle_sample(n, nrhs, size="step", iters_hint=None):
     """Time the FP64 oracle on a bounded sample of the workload (the l = 1
-    system's build pieces and sampled matvec rows) and scale to one step of the
-    workload: one build per length-scale plus each system's PCG iterations.
-    Returns (solves_per_s, detail, cores, per-piece seconds)."""
+    system's build pieces and sampled matvec rows, sized by SAMPLE_SIZES[size])
+    and scale to one step of the workload: one build per length-scale plus each
+    system's PCG iterations.  Returns (solves_per_s, detail, cores, per-piece
+    seconds)."""
     import oracle
     from paper_2304_05460_gb300 import inputs
+    z = SAMPLE_SIZES[size]
     s = workload(n, nrhs)
     X = s.X
     l = 1.0
@@ -172,19 +182,19 @@ def oracle_sample(n, nrhs, budget_s=20.0, iters_hint=None):
     t0 = time.perf_counter()
     k, r, br = oracle.rank_estimate(X, 0, l, MU, m=min(n, 1000), seed=SEED, k_max=KMAX)
     t["rank"] = time.perf_counter() - t0
-    # FPS: the first 400 of the k steps, scaled (each step is one O(n d) pass)
-    ks = min(k, 400)
+    # FPS: the first steps of the k, scaled (each step is one O(n d) pass)
+    ks = min(k, z["fps"])
     t0 = time.perf_counter()
     oracle.fps(X, ks, 0)
     t["fps"] = (time.perf_counter() - t0) * k / ks
     # Cholesky of K11 + mu I on the first kc landmarks, scaled by (k/kc)^3
-    kc = min(k, 1200)
+    kc = min(k, z["kc"])
     idx = np.arange(kc)
     A = oracle.kernel_matrix(X[idx], X[idx], 0, l) + MU * np.eye(kc)
     t0 = time.perf_counter()
     Lc = oracle.cholesky(A)
     t["chol"] = (time.perf_counter() - t0) * (k / kc) ** 3
-    # FSAI rows: 8 Schur rows with their literal Schur blocks, scaled to nr rows
+    # FSAI rows with their literal Schur blocks (full patterns), scaled to nr rows
     nr = n - k
     Xp = np.concatenate([X[:k], X[k:]])
     Lk = None
@@ -193,17 +203,19 @@ def oracle_sample(n, nrhs, budget_s=20.0, iters_hint=None):
     else:
         Ak = oracle.kernel_matrix(X[:k], X[:k], 0, l) + MU * np.eye(k)
         Lk = np.linalg.cholesky(Ak)      # factor only feeds the timed row solves below
-    pat, _ = oracle.knn_pattern(Xp[k:k + 2000], W)
-    rows = np.arange(1990, 1998)
+    kr = min(nr, z["knn"])
+    pat, _ = oracle.knn_pattern(Xp[k:k + kr], W)
+    rows = np.arange(max(kr - 2 - z["fsai"], 0), kr - 2)
     t0 = time.perf_counter()
-    oracle.fsai_rows(Xp, 0, l, MU, k, W, Lk, np.concatenate([pat, np.full((nr - 2000, W), -1, np.int32)]), rows)
+    oracle.fsai_rows(Xp, 0, l, MU, k, W, Lk,
+                     np.concatenate([pat, np.full((nr - kr, W), -1, np.int32)]), rows)
     t["fsai"] = (time.perf_counter() - t0) * nr / len(rows)
-    # KNN: rows 0..2000 cost ~ sum i; scale to nr rows (quadratic)
+    # KNN: rows 0..kr cost ~ sum i; scale to nr rows (quadratic)
     t0 = time.perf_counter()
-    oracle.knn_pattern(Xp[k:k + 2000], W)
-    t["knn"] = (time.perf_counter() - t0) * (nr / 2000.0) ** 2
-    # one PCG iteration ~ one matvec with nrhs columns: 16 sampled rows scaled
-    rowsm = np.arange(16)
+    oracle.knn_pattern(Xp[k:k + kr], W)
+    t["knn"] = (time.perf_counter() - t0) * (nr / float(kr)) ** 2
+    # one PCG iteration ~ one matvec with nrhs columns: sampled rows scaled to n
+    rowsm = np.arange(min(n, z["mv"]))
     P = inputs.rhs(n, nrhs, 5)
     t0 = time.perf_counter()
     oracle.matvec_rows(X, 0, l, MU, P, rowsm)
@@ -213,11 +225,12 @@ def oracle_sample(n, nrhs, budget_s=20.0, iters_hint=None):
     build = sum(t.values())
     t["pcg"] = t_mv * sum(its)
     total = build * len(LS) + t["pcg"]
-    detail = ("FP64 oracle, l=1 system: rank estimate in full; FPS 400 of %d steps; Cholesky "
-              "of %d of %d landmarks (x(k/kc)^3); 8 FSAI rows of %d; KNN rows 0..2000 "
-              "(x(nr/2000)^2); 16 matvec rows x %d RHS (x n); scaled to one step (the build "
+    detail = ("FP64 oracle, l=1 system: rank estimate in full; FPS %d of %d steps; Cholesky "
+              "of %d of %d landmarks (x(k/kc)^3); %d FSAI rows of %d; KNN rows 0..%d "
+              "(x(nr/%d)^2); %d matvec rows x %d RHS (x n); scaled to one step (the build "
               "once per system, PCG iterations %s for l = %s as the FP64-accurate GPU path "
-              "counts them) = %.1f s" % (k, kc, k, nr, nrhs, its, list(LS), total))
+              "counts them) = %.1f s" % (ks, k, kc, k, len(rows), nr, kr, kr, len(rowsm), nrhs,
+                                        its, list(LS), total))
     return len(LS) * nrhs / total, detail, cores, t
 
 
@@ -746,8 +759,8 @@ def run_one_rhs(afn, s, Xd, Bd, stream, opts):
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands on the host cores.  Each
     step (warm-up steps included) is one bounded sample of the workload (the
-    l = 1 system's build pieces and sampled matvec rows, about 10 s of CPU
-    work); `ms_per_step` is the measured time of a timed step, `value` the
+    l = 1 system's build pieces and sampled matvec rows, SAMPLE_SIZES["step"]:
+    about 2 s on 16 host cores); `ms_per_step` is the measured time of a timed step, `value` the
     sample's throughput scaled to the workload's solves (median over the timed
     steps).  Under torchrun only rank 0 runs."""
     rank = int(os.environ.get("RANK", "0"))
@@ -989,7 +1002,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, detail, cores, parts = oracle_sample(args.n, args.nrhs)
+        v, detail, cores, parts = oracle_sample(args.n, args.nrhs, "baseline")
         cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": detail}
 
     fp64 = None
