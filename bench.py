@@ -162,7 +162,7 @@ FP64_ITERS = {0.5: 8, 1.0: 227, 2.0: 801, 4.0: 362}
 # landmarks of the timed Cholesky, FSAI rows with their literal Schur blocks, pattern rows of
 # the timed KNN, matvec rows
 SAMPLE_SIZES = {"step": dict(fps=400, kc=1200, fsai=8, knn=2000, mv=16),
-                "baseline": dict(fps=2000, kc=2000, fsai=96, knn=4000, mv=1024)}
+                "baseline": dict(fps=2000, kc=2000, fsai=128, knn=4000, mv=1536)}
 
 
 def oracle_sample(n, nrhs, size="step", iters_hint=None):
