@@ -91,93 +91,15 @@ __global__ void matvec_finish(const T *__restrict__ part, int js, int nrc, int64
 
 // ------------------------------------------------------------------ FP32 --
 // Xs: n x DS floats (DS = 4 when D == 3, else D), prescaled (kernel32_scaled).
-template <int D, int NR, int KER>
-__global__ void __launch_bounds__(NT) matvec32_kernel(const float *__restrict__ Xs, int64_t n,
-                                                      const float *__restrict__ P, int64_t ldp,
-                                                      float *__restrict__ part, int64_t chunk)
-{
-    constexpr int DS = (D == 3) ? 4 : D;
-    constexpr int TILE = TJ * DS + NR * TJ;
-    constexpr int RED = (JG - 1) * TI * NR;
-    constexpr int SM = TILE > RED ? TILE : RED;
-    __shared__ __align__(16) float sm[SM];
-    float *xs = sm;
-    float *ps = sm + TJ * DS;
-    const int ti = threadIdx.x % TI;
-    const int g = threadIdx.x / TI;
-    const int64_t i = (int64_t)blockIdx.x * TI + ti;
-    const int64_t j0 = (int64_t)blockIdx.y * chunk;
-    const int64_t j1 = min(n, j0 + chunk);
-
-    float xi[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) xi[t] = (i < n) ? Xs[i * DS + t] : 0.f;
-    // two-level accumulation: a tile partial (TJ/JG terms) is folded into the
-    // running sum with Kahan compensation, so the FP32 rounding of a row sum
-    // grows like sqrt(TJ/JG) instead of sqrt(n / (JG * chunks)).
-    float acc[NR], cmp[NR];
-#pragma unroll
-    for (int c = 0; c < NR; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
-
-    for (int64_t jt = j0; jt < j1; jt += TJ) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < TJ * DS; e += NT) {
-            int64_t j = jt + e / DS;
-            xs[e] = (j < j1) ? Xs[jt * DS + e] : 0.f;
-        }
-        for (int e = threadIdx.x; e < NR * TJ; e += NT) {
-            int c = e / TJ, jj = e % TJ;
-            int64_t j = jt + jj;
-            ps[c * TJ + jj] = (j < j1) ? P[c * ldp + j] : 0.f;
-        }
-        __syncthreads();
-        float tac[NR];
-#pragma unroll
-        for (int c = 0; c < NR; ++c) tac[c] = 0.f;
-#pragma unroll 4
-        for (int jj = g * (TJ / JG); jj < (g + 1) * (TJ / JG); ++jj) {
-            const float *xj = xs + jj * DS;
-            float r2 = 0.f;
-#pragma unroll
-            for (int t = 0; t < D; ++t) {
-                float u = xi[t] - xj[t];
-                r2 = fmaf(u, u, r2);
-            }
-            float kv = kernel32_scaled<KER>(r2);
-#pragma unroll
-            for (int c = 0; c < NR; ++c) tac[c] = fmaf(kv, ps[c * TJ + jj], tac[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            float y = tac[c] - cmp[c];
-            float t = acc[c] + y;
-            cmp[c] = (t - acc[c]) - y;
-            acc[c] = t;
-        }
-    }
-    __syncthreads();
-    if (g > 0) {
-#pragma unroll
-        for (int c = 0; c < NR; ++c) sm[((g - 1) * NR + c) * TI + ti] = acc[c];
-    }
-    __syncthreads();
-    if (g == 0 && i < n) {
-#pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            float s = acc[c];
-            for (int q = 1; q < JG; ++q) s += sm[((q - 1) * NR + c) * TI + ti];
-            part[((int64_t)blockIdx.y * NR + c) * n + i] = s;
-        }
-    }
-}
 
 // One right-hand side, two rows per thread: the rows i and i + 64 of a
 // 128-row CTA share every staged x_j and p_j, and their distances, kernel
 // arguments and sums are f32x2 pairs (each half rounded as the scalar
 // operation).  The staged tile holds each coordinate and p_j twice,
-// {v, v}, so a packed operand is one shared load.  Per row the arithmetic is
-// that of matvec32_kernel: d ascending for r^2, j ascending within a j-group,
-// a Kahan fold per tile, j-groups summed in order.
+// {v, v}, so a packed operand is one shared load.  Per row: r^2 by FMAs over
+// d ascending, the j-group's partial over j ascending, folded into the running
+// sum with Kahan compensation once per staged tile (so the FP32 rounding of a
+// row sum grows like sqrt(TJ/JG), not sqrt(n/JG)), j-groups summed in order.
 static constexpr int TI2 = 2 * TI;   // rows per CTA of the two-row form
 
 template <int D, int KER>
