@@ -19,18 +19,6 @@ __device__ __forceinline__ double sqdist_exact(const double *x, const double *y,
     return s;
 }
 
-// Strided variant: x has stride sx, y stride sy between coordinates.
-__device__ __forceinline__ double sqdist_exact_s(const double *x, int64_t sx, const double *y,
-                                                 int64_t sy, int d)
-{
-    double s = 0.0;
-    for (int t = 0; t < d; ++t) {
-        double u = __dsub_rn(x[t * sx], y[t * sy]);
-        s = __dadd_rn(s, __dmul_rn(u, u));
-    }
-    return s;
-}
-
 // Kernel value from a squared distance, FP64 (Gaussian eq. (gaussianf);
 // Matern-3/2 of Sec. 5).  Written as the definition: exp(-r^2 / l^2) and
 // (1 + sqrt3 r / l) exp(-sqrt3 r / l).

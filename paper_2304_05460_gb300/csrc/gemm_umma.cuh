@@ -35,13 +35,6 @@ template <int NR> struct GStage {
     static constexpr int BYTES = 2 * AB + 2 * BB;
 };
 
-// element (row r, K-element kk) of a 128 x GKU tile in the K-major core-matrix
-// layout: core matrices of 8 rows x 4 elements, consecutive along K
-__host__ __device__ inline int64_t gu_tile_word(int r, int kk)
-{
-    return (int64_t)(r / 8) * (GKU / 4) * 32 + (kk / 4) * 32 + (r % 8) * 4 + (kk % 4);
-}
-
 // part[(y NR + c) M + i] = sum over the CTA's stages of A[i, :] B[:, c] for the
 // 128 rows of row tile blockIdx.x; Atl: the tiled operand, row tiles of
 // nks stages each (4096 words a stage); Bk: the split vector block, per stage
