@@ -435,11 +435,16 @@ def dense_solve(X, kernel, l, mu, b):
 
 
 def true_relres(X, kernel, l, mu, x, b):
-    """||b - (K + mu I) x||_2 / ||b||_2 per column, in FP64."""
+    """||b - (K + mu I) x||_2 / ||b||_2 per column, in FP64 (the relative
+    residual of the stopping test, Sec. 5).  A zero column b has the solution
+    x = 0: its value is 0 when the residual is zero and +inf otherwise."""
     x = np.asarray(x, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     r = b.reshape(b.shape[0], -1) - matvec(X, kernel, l, mu, x.reshape(x.shape[0], -1)).reshape(b.shape[0], -1)
-    out = np.linalg.norm(r, axis=0) / np.linalg.norm(b.reshape(b.shape[0], -1), axis=0)
+    nr = np.linalg.norm(r, axis=0)
+    nb = np.linalg.norm(b.reshape(b.shape[0], -1), axis=0)
+    out = np.where(nr == 0.0, 0.0, np.inf)
+    np.divide(nr, nb, out=out, where=nb > 0)
     return out
 
 

@@ -375,6 +375,22 @@ def test_pcg_afn_beats_cg_and_multi_rhs():
     assert np.all(oracle.true_relres(X, G, 0.15, 1e-4, x, B) <= 1e-6)
 
 
+def test_true_relres_special_values():
+    # x = 0 leaves r = b (relative residual exactly 1); the dense solve leaves rounding only;
+    # a zero column b has the solution 0 (value 0) and any other x is wrong (value inf)
+    X = pts(40, 2, 35)
+    A = np.exp(-((X[:, None, :] - X[None, :, :]) ** 2).sum(-1) / 0.3 ** 2) + 1e-2 * np.eye(40)
+    B = inputs.rhs(40, 3, 36)
+    B[:, 2] = 0.0
+    x = np.linalg.solve(A, B)
+    rel = oracle.true_relres(X, G, 0.3, 1e-2, x, B)
+    assert np.all(rel[:2] < 1e-12) and rel[2] == 0.0
+    rel0 = oracle.true_relres(X, G, 0.3, 1e-2, np.zeros_like(B), B)
+    assert np.array_equal(rel0, np.array([1.0, 1.0, 0.0]))
+    x[0, 2] = 1e-3
+    assert oracle.true_relres(X, G, 0.3, 1e-2, x, B)[2] == np.inf
+
+
 # -------------------------------------------------------- eigen / Alg. 4 ---
 def test_tridiagonalize_and_sturm_against_eigvalsh():
     X = pts(80, 3, 34)
