@@ -32,7 +32,7 @@ def nvcc() -> str:
 
 
 def _flags():
-    extra = os.environ.get("AFN_NVCC_FLAGS", "").split()   # tuning: e.g. -DAFN_TC_FOLD=2
+    extra = os.environ.get("AFN_NVCC_FLAGS", "").split()   # extra nvcc flags, e.g. -Xptxas -v
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
                    "-Xptxas", "-warn-spills"] + extra
 

@@ -161,7 +161,7 @@ afn_status sync_status(Handle *h, const char *what);   // sync + read device sta
 
 // pointer kind
 bool is_device_ptr(const void *p);
-// AFN_PREC_AUTO threshold on rho (AFN_AUTO_RHO in the environment, default 0.3)
+// AFN_PREC_AUTO threshold on rho (afn_options.auto_rho, default 0.3)
 double auto_rho_limit(const afn_options &o);
 
 // the body of afn_build: validate, build on stream s, return a new handle

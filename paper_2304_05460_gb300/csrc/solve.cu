@@ -8,9 +8,11 @@
 //  * Mixed handles: one FP32 PCG sequence with reliable updates (see
 //    mixed_reliable): FP32 matvec / apply / vectors, FP64 scalars, x in FP64,
 //    and the residual replaced by the FP64 residual b - (K + mu I) x whenever
-//    the recursive one has dropped by inner_tol.  (AFN_REFINE=restart selects
-//    the earlier restarted refinement: FP32 inner PCG to inner_tol, then
-//    x += d and a new FP64 residual.)
+//    the recursive one has dropped by inner_tol.  afn_options.krylov selects
+//    the variants: FP64 Krylov vectors with only the matvec and the apply in
+//    FP32 (AFN_KRYLOV_FP64), the same with the FP64-accurate matvec as well
+//    (AFN_KRYLOV_FP64_OPERATOR), or the restarted refinement (AFN_KRYLOV_RESTART:
+//    FP32 inner PCG to inner_tol, then x += d and a new FP64 residual).
 //
 // Scalars (rho, alpha, beta, norms) live on the device in FP64 per column.
 // Each dot product is a two-level reduction whose last block sums the
