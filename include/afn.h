@@ -394,9 +394,11 @@ typedef struct {
 
 /*
  * Builds the AFN preconditioners (Alg. 2, the factors of afn_build) of nsys
- * independent systems, several at a time on separate streams.  The batch
- * runs the mixed-precision path only: opt->precision must be AFN_PREC_MIXED
- * (AFN_ERR_ARG otherwise).  opt applies to every system (landmark policy,
+ * independent systems, several at a time on separate streams.  opt->precision
+ * applies to every system as in afn_build (AFN_PREC_AUTO picks MIXED or DF per
+ * system); mixed systems are later solved together, DF and FP64 ones one at
+ * a time beside them.  opt->precond must be AFN_PRECOND_AFN (AFN_ERR_ARG
+ * otherwise).  opt applies to every system (landmark policy,
  * rank mode, seed, max_iter, inner_tol = delta of the reliable updates,
  * check_every = PCG iterations per captured CUDA graph launch, stream for
  * the solves: NULL creates a private stream).  AFN_BUILD_THREADS in the
@@ -408,12 +410,14 @@ afn_status afn_build_batched(const afn_system *systems, int32_t nsys, const afn_
                              afn_batch **out);
 
 /*
- * Solves every system of the batch for its nrhs[s] right-hand sides by the
- * mixed-precision PCG of afn_solve (Alg. 5 with the apply of Alg. 3; FP32
- * matvec/apply, FP64 scalars, FP64 residual replacements; stop when the FP64
- * residual ||b - (K + mu I) x|| <= tol ||b||, at most max_iter iterations a
- * column), all systems advancing together: each step of an iteration is one
- * launch over the work of every system that still has an active column.
+ * Solves every system of the batch for its nrhs[s] right-hand sides.  The
+ * mixed systems run the mixed-precision PCG of afn_solve (Alg. 5 with the
+ * apply of Alg. 3; FP32 matvec/apply, FP64 scalars, FP64 residual
+ * replacements; stop when the FP64 residual ||b - (K + mu I) x|| <= tol ||b||,
+ * at most max_iter iterations a column), all advancing together: each step of
+ * an iteration is one launch over the work of every mixed system that still
+ * has an active column.  DF and FP64 systems are solved as by afn_solve, one
+ * at a time on host threads, concurrently with the group.
  * rhs and x_out (host or device) hold the systems' n_s x nrhs[s] column-major
  * blocks one after the other, in original point order; iters and relres (host,
  * may be NULL) get sum(nrhs) entries in the same column order.  A system's

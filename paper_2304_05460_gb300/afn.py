@@ -484,7 +484,8 @@ class Batch:
 
 def afn_build_batched(systems, opt: afn_options | None = None, **kw):
     """Builds every system of ``systems`` (dicts with keys points, kernel, l,
-    mu, k_max, fsai_nnz) with the mixed-precision options ``opt``."""
+    mu, k_max, fsai_nnz) with the options ``opt`` (precision AUTO unless
+    given: MIXED or DF per system)."""
     if opt is None:
         kw.setdefault("precision", PREC_AUTO)
         opt = options(**kw)
