@@ -52,8 +52,11 @@ typedef enum {
     AFN_PREC_FP64 = 0,         /* everything in FP64 */
     AFN_PREC_MIXED = 1,        /* FP32 matvec / apply / FSAI build + FP64 Cholesky, dots,
                                   scalars and FP64 residual replacements (reliable updates) */
-    AFN_PREC_DF = 2,           /* FP64 PCG, factors and apply; the matvec FP64-accurate in
-                                  double-float on the FP32 pipes (matvec_df) */
+    AFN_PREC_DF = 2,           /* FP64 PCG and apply; FP64-accurate factors (Cholesky and
+                                  triangular inverse in FP64, W and the FSAI Gram in
+                                  double-float on the FP32 pipes); the matvec FP64-accurate
+                                  in double-float (its sum over j exact on the tensor cores
+                                  from 8 columns and 16384 points) */
     AFN_PREC_AUTO = 3          /* per system at build time: MIXED when
                                   rho = 2^-24 max_i sum_j K_ij / mu <= 0.3 (the FP32 matvec
                                   error stays small next to mu; the option auto_rho
@@ -140,8 +143,9 @@ typedef enum {
 } afn_krylov;
 
 typedef enum {
-    AFN_FACTORS_FP32 = 0,      /* K12 from the FP32 points, W = L^{-1} K12 by an FP32 triangular
-                                  solve, FSAI Schur blocks with an FP32 Gram (Alg. 1) */
+    AFN_FACTORS_FP32 = 0,      /* L^{-1} formed in FP64 and rounded once to FP32; K12 from the
+                                  FP32 points and W = L^{-1} K12 by an FP32 product; FSAI Schur
+                                  blocks with an FP32 Gram (Alg. 1) */
     AFN_FACTORS_FP64 = 1       /* W, the triangular inverses and G built in FP64 as for an FP64
                                   handle (G within the FP64 parity bound of the oracle's), then
                                   rounded to FP32 for the apply */
@@ -222,8 +226,9 @@ afn_status afn_get_G(const afn_handle *h, int32_t *pattern, double *values);
 afn_status afn_get_W(const afn_handle *h, double *Wt);
 /* s = M^{-1} r for nrhs columns (Alg. 3), vectors in PERMUTED order, FP64 in
  * and out.  FP64 handles apply in FP64; mixed handles run the FP32 apply of
- * their solves (r rounded to FP32; with the handle's option apply_tc = 1 and
- * a multiple of 16 columns the W products run on the tensor cores).
+ * their solves (r rounded to FP32; with the handle's option apply_tc = 1 or
+ * 2, the default, and a multiple of 16 columns the W products run on the
+ * tensor cores).
  * AFN_ERR_TIMEOUT if a staged copy or MMA did not complete. */
 afn_status afn_apply_precond(afn_handle *h, const double *r, int32_t nrhs, double *s);
 
@@ -246,8 +251,9 @@ int64_t afn_launch_count(void);
 void afn_release_cached_memory(void);
 
 /* Limit, in nanoseconds, of the bounded device-side waits of the tensor-core
- * (tcgen05) kernels: the FP32 kernel matvec with 16 or 32 columns a piece
- * and the tensor-core W products of the FP32 apply.  A wait that runs past
+ * (tcgen05) kernels: the FP32 kernel matvec with 16, 32 or 64 columns a
+ * piece, the tensor-core sum of the double-float matvec and the tensor-core
+ * W products of the FP32 apply (tf32 and BF16).  A wait that runs past
  * it (a staged copy or an MMA that has not completed) raises the kernel's
  * abort flag; the kernel then still waits, up to 2 s, for the copies and
  * MMAs it has in flight, releases its tensor memory and returns, and the
