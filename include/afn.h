@@ -448,7 +448,8 @@ typedef struct {
     int64_t memory_budget;  /* device bytes for admitted requests; 0 = half the free memory */
     int32_t max_active;     /* admitted requests at once; 0 = no limit besides memory */
     int32_t build_threads;  /* host threads (each with a stream) building requests; 0 = 8 */
-    afn_options opt;        /* solve options for every request; precision must be MIXED */
+    afn_options opt;        /* build and solve options for every request; precond AFN;
+                               precision AUTO by default (MIXED or DF per request) */
 } afn_server_config;
 
 typedef struct {
@@ -473,7 +474,7 @@ typedef struct {
 } afn_server_stats;
 
 /* defaults: budget 0 (half the free memory), no count limit, 8 build
- * threads, afn_default_options with precision = AFN_PREC_MIXED */
+ * threads, afn_default_options with precision = AFN_PREC_AUTO */
 void afn_server_default_config(afn_server_config *cfg);
 
 /*
@@ -482,9 +483,10 @@ void afn_server_default_config(afn_server_config *cfg);
  * admitted in arrival order while the sum of the admitted requests' device
  * footprints stays within the budget (a request larger than the budget runs
  * when nothing else is admitted); each is built (Alg. 2) on a build thread's
- * own stream, then joins the group of running PCG solves (the solve of
- * afn_solve_batched, one launch per step for all requests) at its next graph
- * launch and leaves it when its columns have stopped; its device memory is
+ * own stream; a mixed request then joins the group of running PCG solves
+ * (the solve of afn_solve_batched, one launch per step for all requests) at
+ * its next graph launch and leaves it when its columns have stopped, a DF or
+ * FP64 request is solved on its build thread as by afn_solve; its device memory is
  * then released and its result kept in host memory until afn_server_result.
  * A request's solution is the same whatever other requests run beside it.
  * Errors: AFN_ERR_ARG (bad config), AFN_ERR_CUDA.
