@@ -298,8 +298,9 @@ void afn_tune_clear(void);
  * points n x d row-major FP64; p, q n x nrhs column-major FP64.  precision:
  * AFN_PREC_FP64 computes in FP64; AFN_PREC_MIXED evaluates pairs in FP32
  * (points and p rounded to FP32, FP32 accumulation) and returns FP64;
- * AFN_PREC_DF computes FP64-accurate values (kernel values to about 1e-14
- * relative on the FP32 pipes) -- the kernel of the DF solves and of the
+ * AFN_PREC_DF computes FP64-accurate values (kernel values in double-float
+ * on the FP32 pipes, within 2e-14 absolute; Gaussian values above 2^-100
+ * within 2e-14 relative) -- the kernel of the DF solves and of the
  * mixed solves' FP64 residual b - (K + mu I) x: with at least 8 columns and
  * 16384 points the sum over j runs exactly on the tensor cores (both
  * operands split into BF16 base-256 digits, integer products accumulated

@@ -11,7 +11,10 @@
 // 64 table values 2^(j/64) and ln 2 carried as double-floats rounded from
 // the host's FP64 values, and e^y = 1 + y + y^2/2 + y^3 P(y) from its Taylor
 // series (|y| < 0.0055, so the cubic tail needs single precision only).
-// Relative error of a kernel value is about 1e-14; sums are double-float.
+// 2^-z is within 2e-14 relative while it is above 2^-100 (below that the low
+// word is subnormal and only the absolute error stays below 1e-44), the
+// Matern value within 2e-14 absolute, the squared distance within 5e-14
+// relative; sums are double-float.
 #pragma once
 
 #include <stdint.h>
