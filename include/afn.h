@@ -282,7 +282,9 @@ afn_status afn_tune_set_cache(const char *path);
 /* The recorded choice for key; AFN_ERR_ARG when there is none. */
 afn_status afn_tune_get(const char *key, int32_t *choice);
 /* Record a choice (key: printable, no spaces, at most 200 characters;
- * choice >= 0); the library uses it from then on.  Errors: AFN_ERR_ARG. */
+ * choice >= 0); the library uses it from then on.  A choice outside the
+ * key's candidates (here or in a loaded file) is ignored: the key is tuned
+ * again and the entry replaced.  Errors: AFN_ERR_ARG. */
 afn_status afn_tune_put(const char *key, int32_t choice);
 /* Entries in the cache; the key of entry index (sorted order) copied into
  * buf (len bytes, NUL-terminated) and its choice returned, -1 past the end. */

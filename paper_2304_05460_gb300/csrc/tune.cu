@@ -127,8 +127,10 @@ void tune_store(const std::string &key, int choice)
 int tune_pick(const std::string &key, int ncand, const std::function<void(int)> &run,
               cudaStream_t s, int fallback)
 {
+    // a recorded choice outside the candidates (a hand-edited cache file, a
+    // key reused with fewer candidates) is ignored and the key tuned again
     int choice = fallback;
-    if (tune_lookup(key, &choice)) return choice;
+    if (tune_lookup(key, &choice) && choice >= 0 && choice < ncand) return choice;
     // no timing inside a stream capture: the default, without recording it
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -174,7 +176,7 @@ void tune_run(const std::string &key, int ncand, const std::function<void(int)> 
               cudaStream_t s, int fallback)
 {
     int choice = fallback;
-    if (tune_lookup(key, &choice)) {
+    if (tune_lookup(key, &choice) && choice >= 0 && choice < ncand) {
         run(choice);
         return;
     }
@@ -191,7 +193,7 @@ void tune_run(const std::string &key, int ncand, const std::function<void(int)> 
     {
         std::lock_guard<std::mutex> lk(c.mu);
         auto f = c.m.find(key);          // decided by another thread meanwhile
-        if (f != c.m.end()) {
+        if (f != c.m.end() && f->second >= 0 && f->second < ncand) {
             cand = -2;
             choice = f->second;
         } else {

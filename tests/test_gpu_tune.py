@@ -81,6 +81,46 @@ def test_grouped_grid_sizes_bit_identical(afn):
             assert np.array_equal(a, c_)
 
 
+def test_out_of_range_recorded_choice_is_ignored(afn):
+    # a cache entry naming no candidate (a hand-edited file, say) is not used: the key is
+    # tuned again, the entry replaced by a valid choice, and the results stay the same
+    afn.afn_tune_clear()                        # only this test's keys from here on
+    systems, rhs = [], []
+    for i, (n, d) in enumerate([(800, 3), (1100, 6)]):
+        X = inputs.normal_points(n, d, 111 + i)
+        systems.append(dict(points=X, kernel=afn.GAUSSIAN, l=1.0 * np.sqrt(d), mu=1e-2,
+                            k_max=n // 4, fsai_nnz=16))
+        rhs.append(inputs.rhs(n, 8, 113 + i))
+    b = afn.afn_build_batched(systems, precision=afn.PREC_MIXED)
+    xs0, _ = afn.afn_solve_batched(b, rhs, 1e-6)
+    afn.afn_batch_free(b)
+    keys = _keys(afn, "gmv32/") + _keys(afn, "gapply/")
+    assert keys
+    for k in keys:
+        afn.afn_tune_put(k, 7)                  # three candidates: 0, 1, 2
+    b = afn.afn_build_batched(systems, precision=afn.PREC_MIXED)
+    xs, _ = afn.afn_solve_batched(b, rhs, 1e-6)
+    afn.afn_batch_free(b)
+    for a, c in zip(xs0, xs):
+        assert np.array_equal(a, c)
+    for k in keys:
+        assert 0 <= afn.afn_tune_get(k) < 3
+    X = inputs.normal_points(3000, 8, 115)
+    P = inputs.rhs(3000, 32, 116)
+    q0 = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.PREC_MIXED)
+    for _ in range(3):                          # the key of this shape decided
+        afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.PREC_MIXED)
+    mk = _keys(afn, "mv32u/ds8/nb4/ker0/n2^11/")  # n = 3000
+    assert mk, afn.afn_tune_entries()
+    for k in mk:
+        afn.afn_tune_put(k, 9)                  # two candidates: 0, 1
+    for _ in range(4):
+        q = afn.afn_kernel_matvec(X, afn.GAUSSIAN, 2.0, 1e-2, P, precision=afn.PREC_MIXED)
+        assert np.array_equal(q, q0)
+    for k in mk:
+        assert 0 <= afn.afn_tune_get(k) < 2
+
+
 def test_online_tuning_from_concurrent_threads(afn):
     # several host threads, each on its own stream, make the first calls of one
     # tuning key at the same time: one of them records the choice while the
