@@ -6,8 +6,9 @@ N(0, I_8), Gaussian kernel, mu = 1e-2, landmark count estimated by Alg. 4 and
 capped at 4000, FSAI with 64 nonzeros per row, 32 right-hand sides
 b ~ N(0, 1), tol 1e-6.  One step = build + solve for each length-scale
 l in {0.5, 1, 2, 4} (4 systems x 32 right-hand sides = 128 solves), mixed
-precision (FP32 matvec / apply / FSAI build, FP64 Cholesky, dots and
-residual-correction loop).  The inputs (50,000 x 8 points, 50,000 x 32 RHS,
+precision (FP32 matvec / apply / FSAI Gram, FP64 Cholesky and triangular
+inverse, FP64 dots and scalars, residual replacements by the FP64-accurate
+double-float matvec).  The inputs (50,000 x 8 points, 50,000 x 32 RHS,
 12.8 MB) are created once and stay resident in HBM; every step builds the
 factors anew and the solve streams W^T (46,000 x 4,000 FP32 = 736 MB per
 system) many times per step, far more than L2 (129 MB), so no L2 flush is
