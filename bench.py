@@ -408,6 +408,16 @@ def serving_fp64_baseline(afn, count, fp64_sample):
                        "sample; an estimate: iteration counts are not proportional to n^2"}
 
 
+def fifo_latencies_ms(arrivals_s, service_s):
+    """Latencies (ms) of requests served one at a time in arrival order: each
+    starts when it has arrived and the previous one has finished."""
+    free, out = 0.0, []
+    for t, sv in zip(arrivals_s, service_s):
+        free = max(free, t) + sv
+        out.append((free - t) * 1e3)
+    return np.array(out)
+
+
 def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None, fp64=None):
     """The serving workload: `count` requests of the Poisson stream (n
     log-uniform in [1e3, 1e5], d in {3, 8, 16}, N(0,I) points, Gaussian or
@@ -503,12 +513,8 @@ def run_serving(afn, count, rate, fp64_sample, rank=0, world=1, dist=None, fp64=
         if rate > 0 and world == 1:
             # the same arrivals served one at a time by the FP64 path (FIFO), with each
             # request's service time estimated as s_per_n2 x n^2 from the timed sample
-            free, fl = 0.0, []
-            for r in reqs:
-                start = max(free, r["t"])
-                free = start + fp64["s_per_n2"] * float(r["n"]) ** 2
-                fl.append((free - r["t"]) * 1e3)
-            fl = np.sort(np.array(fl))
+            fl = np.sort(fifo_latencies_ms([r["t"] for r in reqs],
+                                           [fp64["s_per_n2"] * float(r["n"]) ** 2 for r in reqs]))
             out["fp64_fifo_estimate"] = {
                 "latency_p50_ms": float(np.percentile(fl, 50)),
                 "latency_p99_ms": float(np.percentile(fl, 99)),

@@ -83,3 +83,4 @@ def test_single_process_time_is_local():
     import bench
     assert bench.job_time_ms(42.0, None, "cpu") == 42.0
     assert bench.job_throughput(10, 1, 500.0) == pytest.approx(20.0)
+
