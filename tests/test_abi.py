@@ -174,3 +174,35 @@ def test_binding_refuses_blocks_of_the_wrong_size_before_any_launch():
         ptr, nsys, n = None, 2, [10, 20]
     with pytest.raises(ValueError):
         afn.afn_solve_batched(FakeBatch(), [np.zeros(10), np.zeros(19)], 1e-6)
+
+
+def test_header_is_c99_and_the_library_links_from_c(tmp_path):
+    # a C caller: the header compiles as strict C99, the program links against the
+    # library by name, and an argument error comes back as a status (no GPU work)
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2304_05460_gb300 import build
+    libdir = os.path.dirname(build.build())
+    src = tmp_path / "caller.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "afn.h"\n'
+        "int main(void) {\n"
+        "    afn_options o;\n"
+        "    afn_handle *h = 0;\n"
+        "    double pts[6] = {0};\n"
+        "    afn_status st;\n"
+        "    afn_default_options(&o);\n"
+        "    st = afn_build(pts, 2, 3, AFN_GAUSSIAN, -1.0, 1e-2, 1, 1, &o, &h);\n"
+        '    printf("%d %d %s\\n", (int)st, (int)o.max_iter, afn_last_error());\n'
+        "    return (st == AFN_ERR_ARG && h == 0) ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "caller"
+    cc = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                         "-I", HEADER_DIR, str(src), "-L", libdir, "-lafn",
+                         "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, (run.stdout, run.stderr)
+    assert run.stdout.startswith("1 500 ") and "invalid argument" in run.stdout
