@@ -206,3 +206,35 @@ def test_header_is_c99_and_the_library_links_from_c(tmp_path):
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert run.returncode == 0, (run.stdout, run.stderr)
     assert run.stdout.startswith("1 500 ") and "invalid argument" in run.stdout
+
+
+def test_null_handles_are_refused_or_ignored_without_gpu():
+    # the frees are NULL-safe; every other entry point returns AFN_ERR_ARG for a NULL
+    # handle or output before it touches the device
+    from paper_2304_05460_gb300 import afn
+    lib = afn.lib()
+    lib.afn_free(None)
+    lib.afn_batch_free(None)
+    lib.afn_server_destroy(None)
+    assert lib.afn_batch_build_ms(None) == 0.0
+    bi = afn.afn_build_info()
+    si = afn.afn_solve_info()
+    buf = (ctypes.c_double * 4)()
+    cnt = ctypes.c_int32(0)
+    checks = [
+        lambda: lib.afn_get_build_info(None, ctypes.byref(bi)),
+        lambda: lib.afn_get_perm(None, buf),
+        lambda: lib.afn_get_L(None, buf),
+        lambda: lib.afn_get_W(None, buf),
+        lambda: lib.afn_solve(None, buf, 1, 1e-6, buf, ctypes.byref(si)),
+        lambda: lib.afn_apply_precond(None, buf, 1, buf),
+        lambda: lib.afn_reset_kernel_stats(None),
+        lambda: lib.afn_batch_build_info(None, 0, ctypes.byref(bi)),
+        lambda: lib.afn_solve_batched(None, buf, None, 1e-6, buf, None, None, None),
+        lambda: lib.afn_server_poll(None, None, 0, ctypes.byref(cnt), 0),
+        lambda: lib.afn_server_result(None, 0, buf, None, None, None),
+        lambda: lib.afn_server_get_stats(None, None),
+    ]
+    for i, f in enumerate(checks):
+        assert f() == afn.AFN_ERR_ARG, i
+        assert afn.last_error(), i
