@@ -238,3 +238,16 @@ def test_null_handles_are_refused_or_ignored_without_gpu():
     for i, f in enumerate(checks):
         assert f() == afn.AFN_ERR_ARG, i
         assert afn.last_error(), i
+
+
+def test_server_config_checked_without_gpu():
+    from paper_2304_05460_gb300 import afn
+    for kw in (dict(precision=9), dict(precond=afn.PRECOND_NYSTROM), dict(memory_budget=-1),
+               dict(max_active=-2), dict(build_threads=-1)):
+        with pytest.raises(afn.AfnError) as e:
+            afn.Server(**kw)
+        assert e.value.status == afn.AFN_ERR_ARG, kw
+    cfg = afn.afn_server_config()
+    afn.lib().afn_server_default_config(ctypes.byref(cfg))
+    assert cfg.opt.precision == afn.PREC_AUTO and cfg.build_threads == 8
+    assert cfg.memory_budget == 0 and cfg.max_active == 0
