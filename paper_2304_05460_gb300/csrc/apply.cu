@@ -8,6 +8,12 @@
 // Every product is a streamed pass over one stored operand, so the apply is
 // bound by HBM bandwidth: W^T (nr x k) is read twice, L^{-1} and L^{-T} once,
 // G twice.  Vectors are n x nrhs column-major (ld = n) in permuted order.
+// The two W products of mixed handles run, for a multiple of 16 columns, on
+// the tensor cores: on a BF16 image of W with the vectors split into three
+// BF16 terms (gemm_bf16.cuh, apply_tc = 2, the default) or three-pass tf32 on
+// the FP32 W (gemm_umma.cuh, apply_tc = 1); otherwise, and with apply_tc = 0,
+// on the CUDA cores (the gemm_kernel tiles of gemm_tile.cuh; pieces of at
+// most 4 columns by rowmul_kernel / colmul_kernel below).
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
