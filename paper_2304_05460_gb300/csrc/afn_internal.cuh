@@ -248,7 +248,6 @@ afn_status cholesky64(double *A, int64_t k, int *status, cudaStream_t s, double 
 afn_status tri_inverse64(const double *L, int64_t k, double *Linv, double *LinvT, cudaStream_t s);
 afn_status trsm_right_lt64(const double *L, int64_t k, double *B, int64_t m,
                            cudaStream_t s);   // B (m x k) <- B L^{-T}
-afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaStream_t s);
 // C (m x k) = A (m x k) U, U (k x k) upper triangular, FP32 row-major (tiled SGEMM)
 afn_status gemm_upper32(const float *A, int64_t m, int64_t k, const float *U, float *C, cudaStream_t s);
 afn_status gemm_upper64(const double *A, int64_t m, int64_t k, const double *U, double *C, cudaStream_t s);

@@ -1,7 +1,14 @@
 // dense.cu -- dense pieces of the AFN build (Alg. 2):
 //   * kernel blocks K(X_a, X_b) (K11 + mu I, K12),
 //   * the blocked right-looking Cholesky of K11 + mu I in FP64,
-//   * the blocked solve B <- B L^{-T} (gives W^T = K12^T L^{-T} and L^{-T}),
+//   * L^{-1} by recursive doubling in FP64: 64 x 64 diagonal blocks inverted
+//     by substitution, then per level the lower-left block -C^{-1} B A^{-1} of
+//     every 2b-block as batched triangular GEMMs (rounded once to FP32 for
+//     mixed handles),
+//   * W^T = K12^T L^{-T} as one tiled GEMM that skips the triangular
+//     operand's zero tiles (FP64, FP32, or double-float on the FP32 pipes for
+//     DF handles),
+//   * the blocked solve B <- B L^{-T} (the Nystrom factor B = K(X, X_S) L^{-T}),
 // all on row-major storage.
 #include <algorithm>
 #include <cmath>
@@ -293,10 +300,6 @@ afn_status trsm_right_lt64(const double *L, int64_t k, double *B, int64_t m, cud
     return trsm_right_lt<double>(L, k, B, m, s);
 }
 
-afn_status trsm_right_lt32(const float *L, int64_t k, float *B, int64_t m, cudaStream_t s)
-{
-    return trsm_right_lt<float>(L, k, B, m, s);
-}
 
 
 template <class T>
