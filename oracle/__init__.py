@@ -531,6 +531,8 @@ def fsai_rows(Xp, kernel, l, mu, k, w, Lo, pattern, rows):
     out = np.zeros((rows.shape[0], w))
     st = lib.orc_fsai_rows(_p(Xp), Xp.shape[0], Xp.shape[1], _kid(kernel), float(l), float(mu),
                            int(k), int(w), _p(Lo), _p(pat), _p(rows), rows.shape[0], _p(out))
+    if st == 1:
+        raise ValueError("oracle fsai_rows: k, w or a row index out of range")
     if st:
         raise np.linalg.LinAlgError("oracle fsai_rows: not SPD")
     return out

@@ -1115,11 +1115,15 @@ void orc_matvec_rows(const double *X, int64_t n, int d, int kernel, double l, do
 /* FSAI rows of Alg. 1 on the Schur complement for selected Schur rows, with
  * the pattern given (nr x w) and K12 columns formed on the fly from the
  * permuted points Xp (landmarks first).  Same literal Schur block as
- * orc_afn_build.  G out: nrows x w.  Returns 0 or 3. */
+ * orc_afn_build.  G out: nrows x w.  Returns 0, 1 (a size or row index
+ * out of range) or 3. */
 int orc_fsai_rows(const double *Xp, int64_t n, int d, int kernel, double l, double mu, int64_t k,
                   int w, const double *L, const int32_t *pat, const int64_t *rows, int64_t nrows,
                   double *Gout)
 {
+    if (k < 0 || k > n || w < 1 || d < 1) return 1;
+    for (int64_t q = 0; q < nrows; ++q)
+        if (rows[q] < 0 || rows[q] >= n - k) return 1;
     const double *Xk = Xp, *Xr = Xp + k * d;
     int bad = 0;
 #pragma omp parallel

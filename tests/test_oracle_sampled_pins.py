@@ -67,3 +67,13 @@ def test_knn_rows_rejects_out_of_range():
     X = inputs.uniform_points(10, 2, 1)
     with pytest.raises(ValueError):
         oracle.knn_rows(X, 3, [10])
+
+
+def test_fsai_rows_rejects_out_of_range():
+    X = inputs.uniform_points(12, 2, 2)
+    L = np.eye(4)
+    pat = np.full((8, 3), -1, np.int32)
+    pat[:, 0] = np.arange(8)
+    for rows, k in (([8], 4), ([-1], 4), ([0], 13)):
+        with pytest.raises(ValueError):
+            oracle.fsai_rows(X, oracle.GAUSSIAN, 0.5, 1e-2, k, 3, L, pat, rows)
