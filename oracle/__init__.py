@@ -501,6 +501,8 @@ def matvec_rows(X, kernel, l, mu, p, rows):
     X = _f64(X)
     P = np.asfortranarray(np.asarray(p, dtype=np.float64).reshape(X.shape[0], -1))
     rows = np.ascontiguousarray(rows, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= X.shape[0]):
+        raise ValueError("matvec_rows: row index out of range")
     out = np.empty((rows.shape[0], P.shape[1]), order="F")
     lib.orc_matvec_rows(_p(X), X.shape[0], X.shape[1], _kid(kernel), float(l), float(mu), _p(P),
                         P.shape[1], _p(rows), rows.shape[0], _p(out))

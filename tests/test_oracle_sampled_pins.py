@@ -77,3 +77,10 @@ def test_fsai_rows_rejects_out_of_range():
     for rows, k in (([8], 4), ([-1], 4), ([0], 13)):
         with pytest.raises(ValueError):
             oracle.fsai_rows(X, oracle.GAUSSIAN, 0.5, 1e-2, k, 3, L, pat, rows)
+
+
+def test_matvec_rows_rejects_out_of_range():
+    X = inputs.uniform_points(10, 2, 3)
+    for rows in ([10], [-1]):
+        with pytest.raises(ValueError):
+            oracle.matvec_rows(X, oracle.GAUSSIAN, 0.5, 1e-2, np.ones(10), rows)
